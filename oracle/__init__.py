@@ -1,0 +1,35 @@
+"""Plain FP64 CPU oracle for the network density-of-states method.
+
+TEST INFRASTRUCTURE ONLY.  Nothing on the product path may import this
+package: only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg
+of ``bench.py`` use it.  It shares no code with the CUDA library
+(``paper_1905_09758_gb300``): it re-derives every quantity from the paper's
+definitions, in float64, with numpy/scipy primitives (a sort, a sparse
+matrix-vector product, a dense symmetric eigensolver) as its only building
+blocks.
+
+Every function cites the passage it follows (Dong, Benson, Bindel, "Network
+Density of States", KDD 2019).  Readings of passages that are silent or
+garbled are stated where they are used.
+
+Parity status of each function (what pins it, see ``tests/test_oracle_*.py``):
+
+* ``splitmix64`` / ``probes``      -- pinned to the generator's published outputs.
+* ``build_csr``                    -- pinned to brute-force adjacency sets.
+* ``dense_h``, ``exact_moments``,
+  ``exact_ldos``                   -- pinned to closed-form spectra (K_n, C_n,
+                                      K_{1,n}, K_{a,b}, bipartite symmetry,
+                                      tr T_1 and tr T_2 identities).
+* ``kpm_direct``, ``kpm_doubled``  -- pinned to the exact moments (identity
+                                      probes give tr T_m(H) exactly) and to each
+                                      other.
+* ``twin_classes``, ``project_probes``
+                                   -- pinned by stars, K_{a,b}, eigenvalue counts
+                                      at 0 and the spectrum of P^T H P.
+* ``jackson``, ``bin_integrals``,
+  ``histogram``                    -- pinned by g_0 = 1, kernel positivity,
+                                      unit mass, and independent quadrature.
+* ``mlp_*``                        -- pinned by central finite differences.
+"""
+from .kpm import *  # noqa: F401,F403
+from .kpm import __all__  # noqa: F401

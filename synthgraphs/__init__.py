@@ -1,0 +1,248 @@
+"""Seeded synthetic graph generators.
+
+These produce the edge lists that both the CPU oracle and the CUDA library
+consume.  They hold none of the density-of-states arithmetic: each function
+returns plain ``(src, dst, n_nodes)`` int64 edge lists (undirected edges, one
+entry per sampled pair; duplicates and self-loops may occur and are left for the
+CSR builder to remove) and is deterministic for a given seed.
+
+The graph models follow the ones the paper works with:
+
+* Erdos-Renyi G(n, p) -- every unordered pair independently with probability p
+  (random-graph background of §2.1).
+* Chung-Lu expected-degree graphs with a power-law weight sequence, standing
+  in for the heavy-tailed SNAP networks of §5 (Table 1 sizes).
+* Barabasi-Albert preferential attachment with m edges per new node (§5.3,
+  "Model Verification").
+* Twin-leaf injection: pairs of degree-1 leaves hung on a common host, the
+  lambda = 0 motif of §3.4 (Fig. 3a).
+
+Recipes (the parameters of each model) are stated in each function's
+docstring.  All randomness comes from ``numpy.random.Generator(PCG64(seed))``.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+__all__ = [
+    "erdos_renyi",
+    "chung_lu",
+    "barabasi_albert",
+    "add_twin_leaves",
+    "cycle",
+    "complete",
+    "star",
+    "complete_bipartite",
+    "path",
+    "batch_graphs",
+]
+
+
+def _rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(int(seed)))
+
+
+def _pair_from_linear(idx: np.ndarray, n: int):
+    """Map linear indices of the strict upper triangle (row-major) to (u, v), u < v."""
+    idx = idx.astype(np.int64)
+    # row u starts at offset(u) = u*(2n-u-1)/2
+    nn = 2 * n - 1
+    u = np.floor((nn - np.sqrt(np.maximum(nn * nn - 8.0 * idx, 0.0))) / 2.0).astype(np.int64)
+    u = np.clip(u, 0, n - 2)
+
+    def off(x):
+        return x * (2 * n - x - 1) // 2
+
+    # fix floating point off-by-one in both directions
+    for _ in range(3):
+        too_big = off(u) > idx
+        u = np.where(too_big, u - 1, u)
+        too_small = off(u + 1) <= idx
+        u = np.where(too_small, u + 1, u)
+    v = idx - off(u) + u + 1
+    return u, v
+
+
+def erdos_renyi(n: int, p: float, seed: int):
+    """G(n, p): each of the n(n-1)/2 unordered pairs is an edge with probability p.
+
+    Sampled by geometric skipping over the row-major strict upper triangle, so
+    the cost is proportional to the number of edges.  Returns unique pairs u < v.
+    """
+    n = int(n)
+    total = n * (n - 1) // 2
+    if n < 2 or p <= 0.0:
+        return np.zeros(0, np.int64), np.zeros(0, np.int64), n
+    rng = _rng(seed)
+    expect = total * p
+    chunk = int(expect + 6.0 * math.sqrt(expect + 1.0) + 16)
+    pos = []
+    last = -1
+    while True:
+        gaps = rng.geometric(p, size=chunk).astype(np.int64)
+        cs = last + np.cumsum(gaps)
+        keep = cs[cs < total]
+        pos.append(keep)
+        if keep.size < cs.size:
+            break
+        last = int(cs[-1])
+    lin = np.concatenate(pos) if pos else np.zeros(0, np.int64)
+    u, v = _pair_from_linear(lin, n)
+    return u, v, n
+
+
+def chung_lu(n: int, gamma: float, mean_degree: float, seed: int, i0: float = 10.0):
+    """Chung-Lu style power-law graph (fast endpoint-sampling variant).
+
+    Node weights w_i = (i + i0)^(-1/(gamma-1)), i = 0..n-1, scaled so their
+    mean is ``mean_degree`` (so hubs have the low ids).  round(n*mean_degree/2)
+    edges are drawn, each endpoint independently with probability proportional
+    to w.  Self-loops and repeated pairs are kept in the list (the CSR builder
+    removes them), so realised degrees are slightly below the weights; nodes
+    with no edge stay isolated.
+    """
+    rng = _rng(seed)
+    i = np.arange(n, dtype=np.float64)
+    w = (i + i0) ** (-1.0 / (gamma - 1.0))
+    w *= mean_degree * n / w.sum()
+    m = int(round(n * mean_degree / 2.0))
+    cdf = np.cumsum(w)
+    cdf /= cdf[-1]
+    src = np.searchsorted(cdf, rng.random(m), side="right").astype(np.int64)
+    dst = np.searchsorted(cdf, rng.random(m), side="right").astype(np.int64)
+    np.minimum(src, n - 1, out=src)
+    np.minimum(dst, n - 1, out=dst)
+    return src, dst, n
+
+
+def barabasi_albert(n: int, m: int, seed: int):
+    """Barabasi-Albert preferential attachment.
+
+    Seed graph: the clique K_{m+1} on nodes 0..m.  Each later node t attaches to
+    m distinct earlier nodes, each drawn with probability proportional to its
+    current degree (uniform draws from the list of edge endpoints, redrawing
+    repeats).  Returns unique pairs.
+    """
+    n, m = int(n), int(m)
+    if n <= m + 1:
+        return complete(n)
+    rng = _rng(seed)
+    n_edges = m * (m + 1) // 2 + (n - m - 1) * m
+    src = np.empty(n_edges, np.int64)
+    dst = np.empty(n_edges, np.int64)
+    ends = np.empty(2 * n_edges, np.int64)
+    e = 0
+    for a in range(m + 1):
+        for b in range(a + 1, m + 1):
+            src[e], dst[e] = a, b
+            ends[2 * e], ends[2 * e + 1] = a, b
+            e += 1
+    n_ends = 2 * e
+    # draw uniform numbers in batches to keep Python overhead bounded
+    buf = rng.random(4 * m + 8)
+    bpos = 0
+    for t in range(m + 1, n):
+        chosen = []
+        while len(chosen) < m:
+            if bpos >= buf.size:
+                buf = rng.random(4 * m + 8)
+                bpos = 0
+            c = int(ends[int(buf[bpos] * n_ends)])
+            bpos += 1
+            if c not in chosen:
+                chosen.append(c)
+        for c in chosen:
+            src[e], dst[e] = t, c
+            ends[n_ends], ends[n_ends + 1] = t, c
+            n_ends += 2
+            e += 1
+    return src, dst, n
+
+
+def add_twin_leaves(src, dst, n: int, n_hosts: int, seed: int):
+    """Hang two new degree-1 leaves on each of ``n_hosts`` hosts.
+
+    Hosts are drawn without replacement from the nodes that have at least one
+    edge in (src, dst) that is not a self-loop.  The two leaves of host h get
+    the ids n + 2k and n + 2k + 1 (k = the host's draw index).  Each pair is an
+    instance of the lambda = 0 twin motif (§3.4, Fig. 3a).  Returns the
+    extended edge list and the new node count n + 2*n_hosts.
+    """
+    rng = _rng(seed)
+    src = np.asarray(src, np.int64)
+    dst = np.asarray(dst, np.int64)
+    live = np.zeros(n, bool)
+    nl = src != dst
+    live[src[nl]] = True
+    live[dst[nl]] = True
+    cand = np.nonzero(live)[0]
+    hosts = rng.choice(cand, size=int(n_hosts), replace=False).astype(np.int64)
+    leaves = n + np.arange(2 * n_hosts, dtype=np.int64)
+    new_src = np.concatenate([src, np.repeat(hosts, 2)])
+    new_dst = np.concatenate([dst, leaves])
+    return new_src, new_dst, n + 2 * int(n_hosts)
+
+
+# ---------------------------------------------------------------------------
+# small deterministic graphs with closed-form spectra (for pins)
+# ---------------------------------------------------------------------------
+
+def cycle(n: int):
+    """Cycle C_n (n >= 3)."""
+    u = np.arange(n, dtype=np.int64)
+    return u, (u + 1) % n, n
+
+
+def path(n: int):
+    """Path P_n."""
+    u = np.arange(n - 1, dtype=np.int64)
+    return u, u + 1, n
+
+
+def complete(n: int):
+    """Complete graph K_n."""
+    u, v = np.triu_indices(n, 1)
+    return u.astype(np.int64), v.astype(np.int64), n
+
+
+def star(n_leaves: int):
+    """Star K_{1,n}: hub 0, leaves 1..n."""
+    v = np.arange(1, n_leaves + 1, dtype=np.int64)
+    return np.zeros(n_leaves, np.int64), v, n_leaves + 1
+
+
+def complete_bipartite(a: int, b: int):
+    """K_{a,b}: parts {0..a-1} and {a..a+b-1}."""
+    u, v = np.meshgrid(np.arange(a), np.arange(a, a + b), indexing="ij")
+    return u.ravel().astype(np.int64), v.ravel().astype(np.int64), a + b
+
+
+def batch_graphs(count: int, seed: int, n_min: int = 200, n_max: int = 20000):
+    """A batch of uneven graphs for the many-small-graphs workload.
+
+    Graph g draws N uniform in [n_min, n_max] and a model uniformly from
+    {Erdos-Renyi, Barabasi-Albert with m in [2, 15], Chung-Lu with exponent in
+    [2.1, 3.0]}; Erdos-Renyi and Chung-Lu draw a mean degree uniform in [4, 30].
+    Yields (src, dst, n, description) per graph.
+    """
+    rng = _rng(seed)
+    for g in range(count):
+        n = int(rng.integers(n_min, n_max + 1))
+        kind = int(rng.integers(0, 3))
+        gseed = int(rng.integers(0, 2**62))
+        if kind == 0:
+            md = float(rng.uniform(4.0, 30.0))
+            s, d, nn = erdos_renyi(n, md / max(n - 1, 1), gseed)
+            desc = f"er(n={n},mean_deg={md:.2f})"
+        elif kind == 1:
+            m = int(rng.integers(2, 16))
+            s, d, nn = barabasi_albert(n, m, gseed)
+            desc = f"ba(n={n},m={m})"
+        else:
+            gam = float(rng.uniform(2.1, 3.0))
+            md = float(rng.uniform(4.0, 30.0))
+            s, d, nn = chung_lu(n, gam, md, gseed)
+            desc = f"cl(n={n},gamma={gam:.2f},mean_deg={md:.2f})"
+        yield s, d, nn, desc

@@ -1,0 +1,193 @@
+"""Oracle pins: twin-motif classes, probe projection, Jackson damping and the
+spectral histogram (CPU only)."""
+import numpy as np
+import pytest
+from scipy import integrate
+
+import oracle
+import synthgraphs as sg
+
+
+def _p_matrix(class_id):
+    ids = np.unique(class_id)
+    p = np.zeros((class_id.size, ids.size))
+    for k, c in enumerate(ids):
+        mem = class_id == c
+        p[mem, k] = 1.0 / np.sqrt(mem.sum())
+    return p
+
+
+def test_star_is_one_twin_class():
+    g = oracle.build_csr(*sg.star(6))
+    cid, removed = oracle.twin_classes(g)
+    assert removed == 5
+    assert list(cid) == [0, 1, 1, 1, 1, 1, 1]
+
+
+def test_complete_bipartite_two_classes():
+    g = oracle.build_csr(*sg.complete_bipartite(3, 4))
+    cid, removed = oracle.twin_classes(g)
+    assert removed == 3 + 4 - 2
+    assert list(cid) == [0, 0, 0, 3, 3, 3, 3]
+
+
+def test_adjacent_nodes_are_never_twins():
+    # in K_n every pair is adjacent; open neighbourhoods all differ
+    g = oracle.build_csr(*sg.complete(5))
+    cid, removed = oracle.twin_classes(g)
+    assert removed == 0 and list(cid) == list(range(5))
+
+
+def test_twins_remove_zero_eigenvalues_and_projection_spectrum():
+    src, dst, n = sg.chung_lu(300, 2.3, 4.0, 31)
+    src, dst, n = sg.add_twin_leaves(src, dst, n, 20, 32)
+    g = oracle.build_csr(src, dst, n)
+    cid, removed = oracle.twin_classes(g)
+    assert removed >= 20
+    lam, _ = oracle.exact_eigs(g)
+    assert np.sum(np.abs(lam) < 1e-9) >= removed
+    p = _p_matrix(cid)
+    assert np.allclose(p.T @ p, np.eye(p.shape[1]), atol=1e-12)
+    hr = p.T @ oracle.dense_h(g) @ p
+    lam_r = np.linalg.eigvalsh(hr)
+    # spec(P^T H P) = spec(H) minus `removed` copies of 0
+    zeros = np.nonzero(np.abs(lam) < 1e-9)[0]
+    keep = np.ones(lam.size, bool)
+    keep[zeros[:removed]] = False
+    assert lam_r.size == g.n - removed
+    assert np.allclose(np.sort(lam_r), np.sort(lam[keep]), atol=1e-9)
+
+
+def test_projection_is_class_mean_and_matches_ppt():
+    src, dst, n = sg.star(4)
+    src = np.concatenate([src, [5, 5]])
+    dst = np.concatenate([dst, [6, 7]])
+    g = oracle.build_csr(src, dst, 8)
+    cid, _ = oracle.twin_classes(g)
+    z = oracle.probes(5, g.old_id, 9)
+    zr = oracle.project_probes(z, cid)
+    p = _p_matrix(cid)
+    assert np.allclose(zr, p @ (p.T @ z), atol=1e-14)
+    assert np.allclose(oracle.project_probes(zr, cid), zr)
+
+
+def test_filtered_moments_estimate_reduced_trace():
+    src, dst, n = sg.chung_lu(250, 2.4, 5.0, 41)
+    src, dst, n = sg.add_twin_leaves(src, dst, n, 15, 42)
+    g = oracle.build_csr(src, dst, n)
+    cid, removed = oracle.twin_classes(g)
+    r = g.n - removed
+    p = _p_matrix(cid)
+    lam_r = np.linalg.eigvalsh(p.T @ oracle.dense_h(g) @ p)
+    d_r = oracle.exact_moments(lam_r, 8)
+    # identity-like probes: columns of P P^T give tr(P^T T_m(H) P) exactly
+    z = p @ p.T
+    mu, _ = oracle.kpm_direct(g, z, 8)
+    assert np.allclose(mu / r, d_r, atol=1e-11)
+
+
+def test_jackson_coefficients_properties():
+    for m in (2, 10, 100, 500):
+        g = oracle.jackson(m)
+        assert abs(g[0] - 1.0) < 1e-15
+        assert abs(g[1] - np.cos(np.pi / (m + 1))) < 1e-14
+        assert np.all(np.diff(g) < 0) and g[-1] > 0
+    # the damped kernel K(x, y) = g_0 + 2 sum g_m T_m(x) T_m(y) is nonnegative
+    g = oracle.jackson(40)
+    x = np.cos(np.linspace(0, np.pi, 301))
+    t = oracle.cheb_values(x, 40)
+    k = g[0] + 2.0 * np.einsum("m,mi,mj->ij", g[1:], t[1:], t[1:])
+    assert k.min() > -1e-10
+
+
+@pytest.mark.parametrize("m", [0, 1, 2, 7, 30])
+def test_bin_integrals_against_quadrature(m):
+    nb = 10
+    i_cf = oracle.bin_integrals(m + 1, nb)[m]
+    e = oracle.bin_edges(nb)
+    for b in range(nb):
+        a, c = e[b], e[b + 1]
+        f = lambda x: np.cos(m * np.arccos(x)) / np.pi  # noqa: E731
+        if b == 0:
+            val, _ = integrate.quad(lambda x: f(x) / np.sqrt(1 - x), a, c, weight="alg", wvar=(-0.5, 0.0))
+        elif b == nb - 1:
+            val, _ = integrate.quad(lambda x: f(x) / np.sqrt(1 + x), a, c, weight="alg", wvar=(0.0, -0.5))
+        else:
+            val, _ = integrate.quad(lambda x: f(x) / np.sqrt(1 - x * x), a, c)
+        assert abs(val - i_cf[b]) < 1e-9
+
+
+def test_histogram_unit_mass_and_positive_with_exact_moments():
+    src, dst, n = sg.barabasi_albert(400, 3, 6)
+    g = oracle.build_csr(src, dst, n)
+    lam, _ = oracle.exact_eigs(g)
+    for mm in (20, 100, 300):
+        d = oracle.exact_moments(lam, mm)
+        h = oracle.histogram(d, 50)
+        assert abs(h.sum() - 1.0) < 1e-12
+        assert h.min() > -1e-12
+    # without damping the sum is still d_0 but Gibbs ringing can go negative
+    h0 = oracle.histogram(oracle.exact_moments(lam, 100), 50, kernel="none")
+    assert abs(h0.sum() - 1.0) < 1e-12
+
+
+def test_histogram_independent_evaluation():
+    # h_b = (1/N) sum_i integral_bin K_M(x, lambda_i) w(x) dx, evaluated by quadrature
+    src, dst, n = sg.erdos_renyi(40, 0.15, 3)
+    g = oracle.build_csr(src, dst, n)
+    lam, _ = oracle.exact_eigs(g)
+    mm, nb = 12, 8
+    h = oracle.histogram(oracle.exact_moments(lam, mm), nb)
+    gj = oracle.jackson(mm)
+    e = oracle.bin_edges(nb)
+
+    def dens(theta):  # density in theta = arccos x, where dx / (pi sqrt(1-x^2)) = dtheta / pi
+        x = np.cos(theta)
+        s = 0.0
+        for lm in lam:
+            tl = np.cos(np.arange(mm) * np.arccos(np.clip(lm, -1, 1)))
+            tx = np.cos(np.arange(mm) * theta)
+            s += gj[0] + 2.0 * np.dot(gj[1:] * tl[1:], tx[1:])
+        return s / (lam.size * np.pi) + 0.0 * x
+
+    for b in range(nb):
+        val, _ = integrate.quad(dens, np.arccos(e[b + 1]), np.arccos(e[b]), limit=200)
+        assert abs(val - h[b]) < 1e-9
+
+
+def test_point_mass_histogram_edges():
+    h = oracle.point_mass_histogram([0.0, -1.0, 1.0, 0.3], [1, 1, 1, 1], 4)
+    # 0.0 is an interior edge of 4 bins over [-1, 1]: split between bins 1 and 2
+    assert np.allclose(h, [1.0, 0.5, 0.5 + 1.0, 1.0])
+    h = oracle.point_mass_histogram([0.0], [1.0], 5)
+    assert np.allclose(h, [0, 0, 1, 0, 0])
+
+
+def test_jackson_error_decreases_with_moments():
+    src, dst, n = sg.chung_lu(600, 2.5, 6.0, 14)
+    g = oracle.build_csr(src, dst, n)
+    lam, _ = oracle.exact_eigs(g)
+    cid, removed = oracle.twin_classes(g)
+    h_ex = oracle.exact_histogram(lam, 20)
+    errs = [oracle.l1(oracle.histogram(oracle.exact_moments(lam, mm), 20), h_ex) for mm in (25, 100, 400)]
+    assert errs[0] > errs[1] > errs[2]
+
+
+def test_filtered_density_recovers_spectrum_better():
+    # the lambda = 0 spike of twin leaves, filtered and added back as a point mass,
+    # lowers the L1 error at a fixed moment count (§3.4, Fig. 4)
+    src, dst, n = sg.chung_lu(500, 2.3, 4.0, 51)
+    src, dst, n = sg.add_twin_leaves(src, dst, n, 60, 52)
+    g = oracle.build_csr(src, dst, n)
+    lam, _ = oracle.exact_eigs(g)
+    cid, removed = oracle.twin_classes(g)
+    r = g.n - removed
+    p = _p_matrix(cid)
+    lam_r = np.linalg.eigvalsh(p.T @ oracle.dense_h(g) @ p)
+    nb, mm = 40, 60
+    h_ex = oracle.exact_histogram(lam, nb)
+    h_plain = oracle.histogram(oracle.exact_moments(lam, mm), nb)
+    h_filt = (r / g.n) * oracle.histogram(oracle.exact_moments(lam_r, mm), nb)
+    h_filt += oracle.point_mass_histogram([0.0], [removed / g.n], nb)
+    assert abs(h_filt.sum() - 1.0) < 1e-12
+    assert oracle.l1(h_filt, h_ex) < oracle.l1(h_plain, h_ex)
