@@ -1,0 +1,382 @@
+"""Benchmark of the KPM network-DOS hot path on one GB300 (or N replicas).
+
+Workload (the Chung-Lu configuration): a Chung-Lu power-law graph, exponent
+2.5, mean degree 20, 1,000,000 nodes, plus 50,000 hosts that each receive two
+new degree-1 leaves (twin pairs, the lambda = 0 motif) -> 1,100,000 nodes,
+~2.0e7 stored nonzeros.  M = 500 moments, Nz = 64 Rademacher probes, FP32
+probe blocks, FP64 moment reductions.
+
+One step = the whole path on that graph: CSR build from the device-resident
+edge list, twin-motif filter, filtered DOS moments (doubling: 250 fused
+Chebyshev steps), LDOS moments (499 fused steps, N x M FP32 output), and the
+damped 200-bin densities (filtered DOS, and DOS from the LDOS run).
+
+Metric: algorithmic HBM GB/s of the fused Chebyshev steps, whole-job:
+    sum over the step's Chebyshev launches of B_launch / step time,
+    B_launch = 4 nnz + 8 (N + 1) + 4 N + 3 N Nz 4 (+ 4 N for LDOS)
+(the CSR once, the degree vector, read V_{k-1}, read V_k, write V_{k+1},
+the LDOS column).  The time includes the non-Chebyshev parts of the step.
+
+--impl reference times the CPU oracle (test infrastructure) on the host cores
+on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Chebyshev-step SpMM HBM GB/s; s to DOS at L1 err≤1e-2 vs plain KPM"
+WORKLOAD = {
+    "workload": "chung_lu_1M_twins_50k",
+    "graph": "Chung-Lu gamma=2.5 mean_deg=20 N=1,000,000 + 50,000 twin-leaf pairs (N=1,100,000)",
+    "M": 500,
+    "Nz": 64,
+    "probe_storage": "fp32",
+    "moment_reduction": "fp64",
+    "parts": "csr_build + twin_filter + dos_moments(filtered, doubled) + ldos_moments(N x M) + 2 densities",
+    "l2": "working set > L2 (probe blocks 282 MB each, LDOS output 2.2 GB); no flush needed",
+    "seed": 2025,
+}
+N_BASE, GAMMA, MEAN_DEG, N_TWIN_HOSTS = 1_000_000, 2.5, 20.0, 50_000
+M, NZ, BINS = 500, 64, 200
+
+
+def make_edges(seed: int):
+    import synthgraphs as sg
+
+    src, dst, n = sg.chung_lu(N_BASE, GAMMA, MEAN_DEG, seed)
+    return sg.add_twin_leaves(src, dst, n, N_TWIN_HOSTS, seed + 1)
+
+
+def step_bytes(n: int, nnz: int, nz: int, ldos: bool) -> float:
+    b = 4.0 * nnz + 8.0 * (n + 1) + 4.0 * n + 3.0 * n * nz * 4
+    return b + (4.0 * n if ldos else 0.0)
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+
+    import paper_1905_09758_gb300 as nd
+    from paper_1905_09758_gb300.build import build
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    if rank == 0:
+        build()
+    if dist is not None:
+        dist.barrier()
+    nd.lib()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    # every rank runs an independent replica (weak scaling; seeds differ per rank)
+    seed = WORKLOAD["seed"] + 1000 * rank
+    src_np, dst_np, n_nodes = make_edges(seed)
+    src_h = torch.from_numpy(src_np).pin_memory()
+    dst_h = torch.from_numpy(dst_np).pin_memory()
+    src_d, dst_d = src_h.to(dev), dst_h.to(dev)
+
+    g0 = nd.dos_build_csr(src_d, dst_d, n_nodes)
+    info = g0.info()
+    n, nnz = info["n"], info["nnz"]
+    plan = nd.dos_get_plan(g0, NZ)
+    del g0
+    c_buf = torch.empty((M, n), dtype=torch.float32, device=dev)
+    c_host = torch.empty((M, n), dtype=torch.float32).pin_memory()
+    small_host = torch.empty(2 * M + 2 * BINS, dtype=torch.float64).pin_memory()
+
+    def one_step(host_io: bool):
+        if host_io:
+            g = nd.dos_build_csr(src_h, dst_h, n_nodes)  # H2D copy inside the call
+        else:
+            g = nd.dos_build_csr(src_d, dst_d, n_nodes)
+        f = nd.dos_motif_filter(g)
+        d_f = nd.dos_moments(g, M, NZ, seed, filter=f)
+        c, d_l = nd.ldos_moments(g, M, NZ, seed + 7, C_out=c_buf)
+        h_f = nd.density_with_spikes(d_f, g, BINS, filter=f)
+        h_l = nd.density_with_spikes(d_l, g, BINS)
+        if host_io:
+            c_host.copy_(c, non_blocking=True)
+            small = torch.cat([d_f, d_l, h_f, h_l])
+            small_host.copy_(small, non_blocking=True)
+        return g, f, h_f
+
+    bytes_dos = step_bytes(n, nnz, NZ, False) * (M // 2)
+    bytes_ldos = step_bytes(n, nnz, NZ, True) * (M - 1)
+    bytes_step = bytes_dos + bytes_ldos
+
+    for _ in range(args.warmup):
+        one_step(False)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    nd.dos_profile_enable(True)
+    nd.dos_profile_read(reset=True)
+    launches0 = nd.dos_launch_count()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        one_step(False)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    launches = nd.dos_launch_count() - launches0
+    step_ms_total, step_launches = nd.dos_profile_read(reset=True)
+    nd.dos_profile_enable(False)
+    clocks = sampler.stop()
+
+    # end to end through the public API: host edge list in, results back to host
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(max(1, args.steps // 2)):
+        one_step(True)
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / max(1, args.steps // 2)
+
+    if dist is not None:
+        t = torch.tensor([ms, e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, e2e_s = float(t[0]), float(t[1])
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    ms_step = ms / args.steps
+    value = world * bytes_step / (ms_step * 1e-3) / 1e9
+    peak, peak_kind = load_peaks()
+    per_launch_bytes = (bytes_dos + bytes_ldos) / ((M // 2) + (M - 1))
+    avg_launch_ms = step_ms_total / max(1, step_launches)
+    achieved = per_launch_bytes / (avg_launch_ms * 1e-3) / 1e9
+    out = {
+        "metric": METRIC,
+        "value": round(value, 2),
+        "unit": "GB/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_step, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": dict(WORKLOAD, n_compact=n, nnz=nnz, plan=plan, parallelism=f"replicas{world}"),
+        "roofline": {
+            "bound": "hbm",
+            "kernel": "k_cheb_step (fused Chebyshev step, DOS and LDOS launches)",
+            "achieved": round(achieved, 1),
+            "peak": peak,
+            "peak_kind": f"{peak_kind} hbm_gbs",
+            "unit": "GB/s",
+            "frac": round(achieved / peak, 4),
+            "traffic": None,
+            "bytes_per_launch": round(per_launch_bytes),
+            "avg_launch_ms": round(avg_launch_ms, 5),
+            "launches": step_launches,
+            "share_of_step": round(step_ms_total / ms, 4) if ms > 0 else None,
+        },
+        "e2e": {
+            "value": round(world * bytes_step / e2e_s / 1e9, 2),
+            "unit": "GB/s",
+            "h2d_bytes_per_step": int(src_h.numel() * 8 * 2),
+            "d2h_bytes_per_step": int(c_host.numel() * 4 + small_host.numel() * 8),
+            "s_per_step": round(e2e_s, 4),
+        },
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(src_np, dst_np, n_nodes, budget_s=args.cpu_seconds)
+    print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+def cpu_baseline(src, dst, n_nodes, budget_s: float = 20.0, seed: int = 2025) -> dict:
+    """Time the oracle's direct LDOS recurrence (the dominant kernel's work) on
+    the same graph for as many Chebyshev steps as fit in ``budget_s``."""
+    import oracle
+
+    ref = oracle.build_csr(src, dst, n_nodes)
+    h = oracle.h_sparse(ref)
+    z = oracle.probes(seed, ref.old_id, NZ)
+    v_prev, v = z, h @ z
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        v_prev, v = v, 2.0 * (h @ v) - v_prev
+        _ = (z * v).sum(axis=1) / NZ
+        steps += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    gbs = steps * step_bytes(ref.n, ref.nnz, NZ, True) / dt / 1e9
+    return {
+        "value": round(gbs, 3),
+        "unit": "GB/s",
+        "cores": 1,
+        "kind": "oracle",
+        "sample": f"{steps} LDOS Chebyshev steps (FP64 scipy CSR x dense, Nz={NZ}) on the full graph, "
+                  f"{dt:.1f} s; same algorithmic bytes per step as the GPU",
+    }
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    src, dst, n_nodes = make_edges(WORKLOAD["seed"])
+    import oracle
+
+    ref = oracle.build_csr(src, dst, n_nodes)
+    h = oracle.h_sparse(ref)
+    z = oracle.probes(WORKLOAD["seed"], ref.old_id, NZ)
+    per = step_bytes(ref.n, ref.nnz, NZ, True)
+    n_chunk = max(1, int(args.ref_steps_per_sample))
+    times = []
+    for it in range(args.warmup + args.steps):
+        v_prev, v = z, h @ z
+        t0 = time.perf_counter()
+        for _ in range(n_chunk):
+            v_prev, v = v, 2.0 * (h @ v) - v_prev
+            _ = (z * v).sum(axis=1) / NZ
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    value = args.steps * n_chunk * per / tot / 1e9
+    sample = f"{n_chunk} LDOS Chebyshev steps per bench step on the full graph (FP64 scipy, 1 thread)"
+    out = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": round(value, 3),
+        "unit": "GB/s",
+        "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(1e3 * tot / args.steps, 1),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": dict(WORKLOAD, n_compact=ref.n, nnz=ref.nnz),
+        "cpu_baseline": {"value": round(value, 3), "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--ref-steps-per-sample", type=int, default=3)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,228 @@
+/*
+ * netdos.h -- C ABI of the GB300 network density-of-states library.
+ *
+ * The library computes the stochastic Chebyshev (kernel polynomial method,
+ * KPM) moments of the normalized adjacency H = D^{-1/2} A D^{-1/2} of an
+ * undirected graph, the per-node (local / pointwise) moments, the twin-motif
+ * filter and the damped spectral histogram, following Dong, Benson, Bindel,
+ * "Network Density of States", KDD 2019 (§2.1 graph operators, §2.2 DOS and
+ * LDOS, §3.1 KPM, §3.4 motif filtering, §4.1 Jackson damping).
+ *
+ * Conventions for every entry point:
+ *  - Return value: DOS_OK (0) or a dos_status code; nothing aborts and no C++
+ *    exception crosses the ABI.  dos_last_error() returns a thread-local text
+ *    for the last failure on the calling thread.
+ *  - Pointers marked [device] are CUDA device pointers owned by the caller;
+ *    [host] are host pointers owned by the caller.  Handles (dos_graph_t,
+ *    dos_filter_t) are owned by the library and released by *_destroy.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Work is enqueued on that stream; calls that return scalars to
+ *    the host synchronise it.  A handle must not be used from two streams
+ *    concurrently.
+ *  - Node numbering: the library compacts away nodes without edges (their
+ *    eigenvalue is 0, see dos_density's spikes).  "Compact id" i in [0, N)
+ *    is the i-th non-isolated node in increasing original id; old_id[i] is
+ *    its original id.  All per-node outputs use compact ids.
+ *  - Probes are Rademacher: entry (i, j) for the node with original id o is
+ *    +1 if bit (j & 63) of SplitMix64(seed)[((j >> 6) << 32) | o] is 0, else
+ *    -1, where SplitMix64(seed)[n] = mix(seed + (n + 1) * 0x9E3779B97F4A7C15)
+ *    (Steele, Lea, Flood, OOPSLA 2014).  The paper's probes are i.i.d. with
+ *    mean 0 and variance 1 (§3.1); these are such probes.
+ */
+#ifndef NETDOS_H
+#define NETDOS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dos_graph_s* dos_graph_t;
+typedef struct dos_filter_s* dos_filter_t;
+
+enum dos_status {
+  DOS_OK = 0,
+  DOS_EINVAL = 1,    /* invalid argument (ids out of range, M < 1, Nz < 1, ...) */
+  DOS_ENOMEM = 2,    /* device allocation failed */
+  DOS_ECUDA = 3,     /* a CUDA runtime call failed; see dos_last_error() */
+  DOS_ETIMEOUT = 4,  /* a bounded device wait gave up */
+  DOS_EOVERFLOW = 5  /* size beyond the int32 / int64 index range of a path */
+};
+
+/* Storage precision of the probe blocks T_m(H) Z.  Arithmetic is FP32 and
+ * the moment reductions are FP64 in every mode. */
+enum dos_prec { DOS_FP32 = 0, DOS_BF16 = 1, DOS_FP16 = 2 };
+
+/* Damping of the Chebyshev series in dos_density. */
+enum dos_kernel { DOS_KERNEL_NONE = 0, DOS_KERNEL_JACKSON = 1 };
+
+/* Flags of dos_build_csr. */
+enum dos_build_flags {
+  DOS_INPUT_HOST = 1 /* src/dst are host pointers; the library copies them */
+};
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int dos_version(void);
+
+/* Thread-local text describing the last failed call on this thread ("" if none). */
+const char* dos_last_error(void);
+
+/*
+ * dos_build_csr -- undirected edge list -> CSR of A, degrees, D^{-1/2}.
+ * Paper: §2.1 (A, D and the normalized adjacency D^{-1/2} A D^{-1/2}).
+ *   src, dst   [device, or host with DOS_INPUT_HOST] int64[n_edges]: edge
+ *              endpoints, original ids in [0, n_nodes).  Each entry is one
+ *              undirected edge; repeated pairs collapse to one edge of
+ *              weight 1 and self-loops (u == v) are dropped.
+ *   n_edges    >= 0.   n_nodes in [0, 2^31 - 1].
+ *   out        receives the graph handle (device memory owned by the library).
+ * Column indices are int32 and row offsets int64, so nnz (2 x undirected
+ * edges) may exceed 2^31; n_edges <= 2^40.
+ * Errors: DOS_EINVAL (negative sizes, endpoint out of range -- detected on
+ * the device and reported after a stream sync), DOS_ENOMEM, DOS_ECUDA.
+ * Synchronises `stream` (the node count is needed on the host).
+ */
+int dos_build_csr(const int64_t* src, const int64_t* dst, int64_t n_edges,
+                  int64_t n_nodes, uint32_t flags, void* stream,
+                  dos_graph_t* out);
+
+/* Sizes of a built graph [host outputs; any may be NULL]: N = non-isolated
+ * nodes, nnz = stored nonzeros (2 x undirected edges), n_isolated = nodes
+ * dropped for having no edge, n_original = n_nodes given to dos_build_csr. */
+int dos_graph_info(dos_graph_t g, int64_t* n, int64_t* nnz,
+                   int64_t* n_isolated, int64_t* n_original);
+
+/*
+ * dos_graph_export -- copy the CSR (compact ids) to caller buffers [device].
+ *   row_ptr int64[N+1], col int32[nnz] (ascending within each row),
+ *   deg int32[N], inv_sqrt_deg double[N] = 1/sqrt(deg) (IEEE, correctly
+ *   rounded), inv_sqrt_deg32 float[N] = (float) of that, old_id int32[N].
+ *   Any pointer may be NULL to skip that array.  Stream-ordered.
+ */
+int dos_graph_export(dos_graph_t g, int64_t* row_ptr, int32_t* col,
+                     int32_t* deg, double* inv_sqrt_deg,
+                     float* inv_sqrt_deg32, int32_t* old_id, void* stream);
+
+void dos_graph_destroy(dos_graph_t g);
+
+/*
+ * dos_motif_filter -- find the lambda = 0 twin motif classes.
+ * Paper: §3.4 (Fig. 3a: nodes with identical neighbourhoods give localized
+ * eigenvectors with eigenvalue 0; detection by hashing; filtering by the
+ * projected probes Z_r = P P^T Z).  Classes are the exact relation the hash
+ * detects: nodes i != j of degree >= 1 with N(i) = N(j) as sets; hash
+ * collisions are resolved by comparing neighbour lists, so the result is
+ * deterministic and exact.
+ *   out  receives the filter handle.  Synchronises `stream`.
+ * Errors: DOS_EINVAL (g NULL), DOS_ENOMEM, DOS_ECUDA.
+ */
+int dos_motif_filter(dos_graph_t g, void* stream, dos_filter_t* out);
+
+/* Filter summary [host outputs; any may be NULL]: removed = sum over classes
+ * of (size - 1) = number of eigenvalues at 0 the filter takes out,
+ * n_classes = classes of size >= 2, r = N - removed. */
+int dos_filter_info(dos_filter_t f, int64_t* removed, int64_t* n_classes,
+                    int64_t* r);
+
+/* class_id [device] int32[N]: the smallest compact id in each node's class
+ * (a node's own id if it has no twin).  Stream-ordered. */
+int dos_filter_export(dos_filter_t f, int32_t* class_id, void* stream);
+
+void dos_filter_destroy(dos_filter_t f);
+
+/*
+ * dos_moments -- stochastic DOS moments d_0 .. d_{M-1}.
+ * Paper: §3.1, Eq. (6) (Chebyshev recurrence on H), Eq. (9) (d_m = tr T_m(H)
+ * / N) and Eq. (11) (trace estimator with Nz probes).  The recurrence runs
+ * floor(M/2) sparse products: with V_k = T_k(H) Z, per probe
+ *   mu_{2k}   = 2 <V_k, V_k>     - <V_0, V_0>
+ *   mu_{2k+1} = 2 <V_{k+1}, V_k> - <V_1, V_0>.
+ *   f       NULL for plain probes, or a filter from dos_motif_filter on the
+ *           same graph: then Z is replaced by Z_r = P P^T Z (class means,
+ *           §3.4) and the moments are those of the reduced operator P^T H P.
+ *   M >= 1, Nz >= 1, prec a dos_prec.
+ *   d_out   [device] double[M]: d_m = mu_m / (r * Nz), r = N without a
+ *           filter, r = N - removed with one.
+ * Scratch: two probe blocks of N x Nz elements of the storage precision and a
+ * small FP64 partial-sum array, allocated stream-ordered on `stream` and
+ * released before return.  Stream-ordered (does not synchronise).
+ * Errors: DOS_EINVAL, DOS_ENOMEM, DOS_ECUDA.
+ */
+int dos_moments(dos_graph_t g, dos_filter_t f, int M, int Nz, uint64_t seed,
+                int prec, double* d_out, void* stream);
+
+/*
+ * ldos_moments -- per-node (pointwise) moments, and the DOS moments from them.
+ * Paper: §2.2 Eq. (2) (LDOS), Eq. (10) (d_mk = T_m(H)_kk), Eq. (12) (diagonal
+ * estimator E[z o Hz] = diag H).  Direct recurrence, M - 1 sparse products:
+ *   C[m][k] = (1/Nz) sum_j z_kj (T_m(H) z_j)_k.
+ *   C_out  [device] float[M * N], MOMENT-MAJOR: C_out[m * N + k] is moment m
+ *          of compact node k (i.e. a column-major N x M matrix).
+ *   d_out  [device] double[M] or NULL: d_m = (1/(N Nz)) sum_k sum_j
+ *          z_kj (T_m(H) z_j)_k, the same estimator as dos_moments without a
+ *          filter, from the direct recurrence.
+ * Probes are never projected here (a projected probe would estimate the
+ * diagonal of P P^T T_m(H) P P^T instead).  Scratch as for dos_moments.
+ * Errors: DOS_EINVAL, DOS_ENOMEM, DOS_ECUDA.
+ */
+int ldos_moments(dos_graph_t g, int M, int Nz, uint64_t seed, int prec,
+                 float* C_out, double* d_out, void* stream);
+
+/*
+ * dos_density -- damped spectral histogram from moments.
+ * Paper: §2.2 (spectral histogram on equal bins), Eq. (7)-(8) (dual Chebyshev
+ * basis, expansion of the DOS), §4.1 (Jackson damping; the factors are the
+ * Jackson kernel of the KPM literature for M terms:
+ * g_m = [(M-m+1) cos(pi m/(M+1)) + sin(pi m/(M+1)) cot(pi/(M+1))]/(M+1)).
+ *   d        [device] double[M] moments d_0 .. d_{M-1}.
+ *   n_bins   B >= 1 equal bins over [-1, 1].
+ *   kernel   DOS_KERNEL_JACKSON or DOS_KERNEL_NONE (g_m = 1).
+ *   scale    multiplies the series part (use r / N_total with a filter and
+ *            N / N_total when isolated nodes are counted; 1.0 otherwise).
+ *   spikes   [host] double[2 * n_spikes] pairs (lambda, mass) added as point
+ *            masses (a point on an interior bin edge splits evenly between
+ *            the two bins; +-1 go to the end bins); NULL if n_spikes == 0.
+ *            n_spikes <= 16.
+ *   hist_out [device] double[B]: bin b gets
+ *            scale * (g_0 d_0 I_0b + 2 sum_{m>=1} g_m d_m I_mb) + spikes,
+ *            I_mb = integral over bin b of T_m(x) / (pi sqrt(1 - x^2)) dx.
+ * Stream-ordered.  Errors: DOS_EINVAL.
+ */
+int dos_density(const double* d, int M, int n_bins, int kernel, double scale,
+                const double* spikes, int n_spikes, double* hist_out,
+                void* stream);
+
+/* ---------------------------------------------------------------------
+ * Tuning and instrumentation (not part of the method).
+ * --------------------------------------------------------------------- */
+
+/* Planner override: force the probe tile width t (a power of two in [4, 64]
+ * that is a multiple of 16 bytes of the storage type; 0 = automatic) and the
+ * neighbour slots per light row (1, 2 or 4; 0 = automatic) of later
+ * dos_moments / ldos_moments calls.  Process-wide.  Errors: DOS_EINVAL. */
+int dos_set_plan(int tile_width, int slots);
+
+/* The plan dos_moments / ldos_moments would use for (g, Nz, prec): tile
+ * width t, neighbour slots, number of tiles T = ceil(Nz / t) and the step
+ * grid's x extent [host outputs; any may be NULL]. */
+int dos_get_plan(dos_graph_t g, int Nz, int prec, int* tile_width, int* slots,
+                 int* tiles, int* grid_x);
+
+/* Number of kernels this library has launched since load (all threads). */
+int64_t dos_launch_count(void);
+
+/* Enable (1) / disable (0) CUDA-event timing of the Chebyshev step kernels.
+ * While enabled, every step launch is bracketed by events on its own stream. */
+int dos_profile_enable(int on);
+
+/* Total device time (ms) and launch count of the step kernels recorded since
+ * the last reset; synchronises on the recorded events.  reset != 0 clears. */
+int dos_profile_read(double* total_ms, int64_t* launches, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NETDOS_H */

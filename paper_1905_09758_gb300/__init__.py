@@ -1,0 +1,31 @@
+"""GB300-native network density of states (KPM Chebyshev moments).
+
+Python face of the CUDA library ``libnetdos.so`` (C ABI: include/netdos.h).
+The functions carry the ABI's names; see ``_binding`` for their arguments.
+"""
+from ._binding import (  # noqa: F401
+    DOS_EINVAL,
+    DOS_ENOMEM,
+    DOS_OK,
+    DosError,
+    Filter,
+    Graph,
+    density_with_spikes,
+    dos_build_csr,
+    dos_density,
+    dos_filter_export,
+    dos_filter_info,
+    dos_get_plan,
+    dos_graph_export,
+    dos_graph_info,
+    dos_launch_count,
+    dos_moments,
+    dos_motif_filter,
+    dos_profile_enable,
+    dos_profile_read,
+    dos_set_plan,
+    dos_version,
+    header_functions,
+    ldos_moments,
+    lib,
+)

@@ -1,0 +1,326 @@
+"""ctypes binding of libnetdos.so (include/netdos.h).
+
+Argument marshalling only: every computation runs in the CUDA library.  Torch
+is used for device memory and the current CUDA stream.  There is no fallback:
+if the library is missing or a call fails, an exception is raised.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libnetdos.so")
+HEADER_PATH = os.path.join(os.path.dirname(_PKG), "include", "netdos.h")
+
+DOS_OK, DOS_EINVAL, DOS_ENOMEM, DOS_ECUDA, DOS_ETIMEOUT, DOS_EOVERFLOW = range(6)
+PREC = {"fp32": 0, "bf16": 1, "fp16": 2}
+KERNEL = {"none": 0, "jackson": 1}
+DOS_INPUT_HOST = 1
+
+_STATUS_NAMES = {
+    DOS_EINVAL: "DOS_EINVAL",
+    DOS_ENOMEM: "DOS_ENOMEM",
+    DOS_ECUDA: "DOS_ECUDA",
+    DOS_ETIMEOUT: "DOS_ETIMEOUT",
+    DOS_EOVERFLOW: "DOS_EOVERFLOW",
+}
+
+
+class DosError(RuntimeError):
+    """A netdos call returned a status other than DOS_OK."""
+
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+_vp, _i64, _i32, _u32, _u64, _dbl = C.c_void_p, C.c_int64, C.c_int, C.c_uint32, C.c_uint64, C.c_double
+_P64 = C.POINTER(C.c_int64)
+_PI = C.POINTER(C.c_int)
+
+_SIGNATURES = {
+    "dos_version": ([], _i32),
+    "dos_last_error": ([], C.c_char_p),
+    "dos_build_csr": ([_vp, _vp, _i64, _i64, _u32, _vp, C.POINTER(_vp)], _i32),
+    "dos_graph_info": ([_vp, _P64, _P64, _P64, _P64], _i32),
+    "dos_graph_export": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp], _i32),
+    "dos_graph_destroy": ([_vp], None),
+    "dos_motif_filter": ([_vp, _vp, C.POINTER(_vp)], _i32),
+    "dos_filter_info": ([_vp, _P64, _P64, _P64], _i32),
+    "dos_filter_export": ([_vp, _vp, _vp], _i32),
+    "dos_filter_destroy": ([_vp], None),
+    "dos_moments": ([_vp, _vp, _i32, _i32, _u64, _i32, _vp, _vp], _i32),
+    "ldos_moments": ([_vp, _i32, _i32, _u64, _i32, _vp, _vp, _vp], _i32),
+    "dos_density": ([_vp, _i32, _i32, _i32, _dbl, _vp, _i32, _vp, _vp], _i32),
+    "dos_launch_count": ([], _i64),
+    "dos_profile_enable": ([_i32], _i32),
+    "dos_profile_read": ([C.POINTER(C.c_double), _P64, _i32], _i32),
+    "dos_set_plan": ([_i32, _i32], _i32),
+    "dos_get_plan": ([_vp, _i32, _i32, _PI, _PI, _PI, _PI], _i32),
+}
+
+
+def lib():
+    """Load libnetdos.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(
+                f"{LIB_PATH} is missing: build it with paper_1905_09758_gb300.build.build() "
+                "(there is no non-CUDA implementation)"
+            )
+        handle = C.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGNATURES.items():
+            f = getattr(handle, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = handle
+    return _lib
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/netdos.h."""
+    txt = open(HEADER_PATH).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b((?:dos|ldos)_[a-z0-9_]+)\s*\(", txt)))
+
+
+def _check(status: int):
+    if status != DOS_OK:
+        msg = lib().dos_last_error()
+        raise DosError(status, msg.decode() if msg else "")
+
+
+def _stream(stream=None) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _ptr(t: torch.Tensor | None) -> int | None:
+    return None if t is None else t.data_ptr()
+
+
+def _need_cuda(t: torch.Tensor, dtype, name: str, numel: int | None = None):
+    if not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA {dtype} tensor")
+    if numel is not None and t.numel() < numel:
+        raise ValueError(f"{name} needs at least {numel} elements")
+
+
+# ---------------------------------------------------------------------------
+# handles
+# ---------------------------------------------------------------------------
+class Graph:
+    """Owned dos_graph_t handle."""
+
+    def __init__(self, handle: int):
+        self._h = C.c_void_p(handle)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        n, nnz, iso, orig = (C.c_int64() for _ in range(4))
+        _check(lib().dos_graph_info(self._h, C.byref(n), C.byref(nnz), C.byref(iso), C.byref(orig)))
+        return {"n": n.value, "nnz": nnz.value, "n_isolated": iso.value, "n_original": orig.value}
+
+    @property
+    def n(self) -> int:
+        return self.info()["n"]
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            lib().dos_graph_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Filter:
+    """Owned dos_filter_t handle (keeps its graph alive)."""
+
+    def __init__(self, handle: int, graph: Graph):
+        self._h = C.c_void_p(handle)
+        self.graph = graph
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        rem, ncl, r = (C.c_int64() for _ in range(3))
+        _check(lib().dos_filter_info(self._h, C.byref(rem), C.byref(ncl), C.byref(r)))
+        return {"removed": rem.value, "n_classes": ncl.value, "r": r.value}
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            lib().dos_filter_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------
+# entry points (same names as the C ABI)
+# ---------------------------------------------------------------------------
+def dos_version() -> int:
+    return lib().dos_version()
+
+
+def dos_build_csr(src: torch.Tensor, dst: torch.Tensor, n_nodes: int, stream=None) -> Graph:
+    """Edge list (int64 tensors, CUDA or host) -> Graph.  Host tensors are copied by the library."""
+    if src.dtype != torch.int64 or dst.dtype != torch.int64 or src.shape != dst.shape:
+        raise ValueError("src and dst must be int64 tensors of equal shape")
+    src, dst = src.contiguous(), dst.contiguous()
+    if src.is_cuda != dst.is_cuda:
+        raise ValueError("src and dst must be on the same device")
+    flags = 0 if src.is_cuda else DOS_INPUT_HOST
+    out = C.c_void_p()
+    _check(lib().dos_build_csr(_ptr(src), _ptr(dst), src.numel(), int(n_nodes), flags, _stream(stream),
+                               C.byref(out)))
+    return Graph(out.value)
+
+
+def dos_graph_info(g: Graph) -> dict:
+    return g.info()
+
+
+def dos_graph_export(g: Graph, stream=None) -> dict:
+    """CSR arrays (compact ids) as CUDA tensors."""
+    info = g.info()
+    n, nnz = info["n"], info["nnz"]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    out = {
+        "row_ptr": torch.empty(n + 1, dtype=torch.int64, device=dev),
+        "col": torch.empty(nnz, dtype=torch.int32, device=dev),
+        "deg": torch.empty(n, dtype=torch.int32, device=dev),
+        "inv_sqrt_deg": torch.empty(n, dtype=torch.float64, device=dev),
+        "inv_sqrt_deg32": torch.empty(n, dtype=torch.float32, device=dev),
+        "old_id": torch.empty(n, dtype=torch.int32, device=dev),
+    }
+    _check(lib().dos_graph_export(g.handle, *(_ptr(out[k]) for k in
+                                              ("row_ptr", "col", "deg", "inv_sqrt_deg", "inv_sqrt_deg32", "old_id")),
+                                  _stream(stream)))
+    return out
+
+
+def dos_motif_filter(g: Graph, stream=None) -> Filter:
+    out = C.c_void_p()
+    _check(lib().dos_motif_filter(g.handle, _stream(stream), C.byref(out)))
+    return Filter(out.value, g)
+
+
+def dos_filter_info(f: Filter) -> dict:
+    return f.info()
+
+
+def dos_filter_export(f: Filter, stream=None) -> torch.Tensor:
+    n = f.graph.n
+    cid = torch.empty(n, dtype=torch.int32, device=torch.device("cuda", torch.cuda.current_device()))
+    _check(lib().dos_filter_export(f.handle, _ptr(cid), _stream(stream)))
+    return cid
+
+
+def dos_moments(g: Graph, M: int, Nz: int, seed: int, prec: str = "fp32", filter: Filter | None = None,
+                d_out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """DOS moments d_0..d_{M-1} (float64 CUDA tensor)."""
+    if d_out is None:
+        d_out = torch.empty(M, dtype=torch.float64, device=torch.device("cuda", torch.cuda.current_device()))
+    _need_cuda(d_out, torch.float64, "d_out", M)
+    _check(lib().dos_moments(g.handle, None if filter is None else filter.handle, int(M), int(Nz),
+                             int(seed) & (2**64 - 1), PREC[prec], _ptr(d_out), _stream(stream)))
+    return d_out
+
+
+def ldos_moments(g: Graph, M: int, Nz: int, seed: int, prec: str = "fp32", C_out: torch.Tensor | None = None,
+                 d_out: torch.Tensor | None = None, want_d: bool = True, stream=None):
+    """Per-node moments C (float32, shape (M, N): C[m, k] = moment m of compact node k) and,
+    if want_d, the DOS moments from the same recurrence."""
+    n = g.n
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if C_out is None:
+        C_out = torch.empty((M, n), dtype=torch.float32, device=dev)
+    _need_cuda(C_out, torch.float32, "C_out", M * n)
+    if d_out is None and want_d:
+        d_out = torch.empty(M, dtype=torch.float64, device=dev)
+    if d_out is not None:
+        _need_cuda(d_out, torch.float64, "d_out", M)
+    _check(lib().ldos_moments(g.handle, int(M), int(Nz), int(seed) & (2**64 - 1), PREC[prec], _ptr(C_out),
+                              _ptr(d_out), _stream(stream)))
+    return C_out, d_out
+
+
+def dos_density(d: torch.Tensor, n_bins: int, kernel: str = "jackson", scale: float = 1.0, spikes=(),
+                hist_out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Damped histogram over n_bins equal bins of [-1, 1] (float64 CUDA tensor).
+    spikes: iterable of (lambda, mass) point masses."""
+    _need_cuda(d, torch.float64, "d")
+    if hist_out is None:
+        hist_out = torch.empty(n_bins, dtype=torch.float64, device=d.device)
+    _need_cuda(hist_out, torch.float64, "hist_out", n_bins)
+    sp = [float(x) for pair in spikes for x in pair]
+    arr = (C.c_double * max(1, len(sp)))(*sp)
+    _check(lib().dos_density(_ptr(d), d.numel(), int(n_bins), KERNEL[kernel], float(scale),
+                             arr if sp else None, len(sp) // 2, _ptr(hist_out), _stream(stream)))
+    return hist_out
+
+
+def dos_launch_count() -> int:
+    return int(lib().dos_launch_count())
+
+
+def dos_profile_enable(on: bool = True):
+    _check(lib().dos_profile_enable(1 if on else 0))
+
+
+def dos_profile_read(reset: bool = True):
+    """(total ms, launches) of the Chebyshev step kernels since the last reset."""
+    ms, n = C.c_double(), C.c_int64()
+    _check(lib().dos_profile_read(C.byref(ms), C.byref(n), 1 if reset else 0))
+    return ms.value, n.value
+
+
+def dos_set_plan(tile_width: int = 0, slots: int = 0):
+    _check(lib().dos_set_plan(int(tile_width), int(slots)))
+
+
+def dos_get_plan(g: Graph, Nz: int, prec: str = "fp32") -> dict:
+    t, p, tiles, gx = (C.c_int() for _ in range(4))
+    _check(lib().dos_get_plan(g.handle, int(Nz), PREC[prec], C.byref(t), C.byref(p), C.byref(tiles), C.byref(gx)))
+    return {"tile_width": t.value, "slots": p.value, "tiles": tiles.value, "grid_x": gx.value}
+
+
+# ---------------------------------------------------------------------------
+# assembly of a filtered density (host arithmetic on three scalars)
+# ---------------------------------------------------------------------------
+def density_with_spikes(d: torch.Tensor, g: Graph, n_bins: int, filter: Filter | None = None,
+                        count_isolated: bool = True, kernel: str = "jackson", stream=None) -> torch.Tensor:
+    """Histogram of the whole graph from moments d of the (filtered) operator.
+
+    With a twin filter, d are the moments of P^T H P (r = N - removed
+    eigenvalues); the removed eigenvalues sit at 0 (§3.4).  Nodes without edges
+    contribute eigenvalue 0 too.  The series part is scaled by r / N_total and
+    the zero eigenvalues are added as one point mass at 0.
+    """
+    info = g.info()
+    n_total = info["n"] + (info["n_isolated"] if count_isolated else 0)
+    removed = filter.info()["removed"] if filter is not None else 0
+    r = info["n"] - removed
+    zeros = removed + (info["n_isolated"] if count_isolated else 0)
+    spikes = [(0.0, zeros / n_total)] if zeros else []
+    return dos_density(d, n_bins, kernel=kernel, scale=r / n_total, spikes=spikes, stream=stream)

@@ -1,0 +1,332 @@
+// dos_moments / ldos_moments: host driver of the stochastic Chebyshev
+// recurrence (§3.1).  Plans the probe tiling, allocates the two probe blocks,
+// runs the init kernel, floor(M/2) (DOS) or M-1 (LDOS) fused step launches
+// and the deterministic FP64 reduction of the moment partials.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "kpm_kernels.cuh"
+
+namespace netdos {
+
+// class probe sums for the twin filter: csum[slot][j] = sum over members of z_j
+// (integer-valued, so the float atomics are exact in any order)
+__global__ void __launch_bounds__(256) k_class_sums(const int32_t* __restrict__ orig, const int32_t* __restrict__ slot,
+                                                    int64_t n, int nz, int nz_pad, uint64_t seed,
+                                                    float* __restrict__ csum) {
+  const int words = (nz + 63) / 64;
+  const int64_t total = n * words;
+  for (int64_t c = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; c < total;
+       c += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t p = c / words;
+    const int w = static_cast<int>(c % words);
+    const int sl = slot[p];
+    if (sl < 0) continue;
+    const uint64_t word = probe_word(seed, static_cast<uint32_t>(orig[p]), static_cast<uint32_t>(w));
+    const int jend = min(nz, 64 * (w + 1));
+    for (int j = 64 * w; j < jend; ++j)
+      atomicAdd(&csum[static_cast<size_t>(sl) * nz_pad + j], ((word >> (j & 63)) & 1ull) ? -1.f : 1.f);
+  }
+}
+
+// raw[s] = sum of partial[s * width + i], i < width, in a fixed order
+__global__ void __launch_bounds__(256) k_reduce_partials(const double* __restrict__ partial, int64_t width,
+                                                         double* __restrict__ raw) {
+  __shared__ double sh[256];
+  const int s = blockIdx.x;
+  double a = 0.0;
+  for (int64_t i = threadIdx.x; i < width; i += blockDim.x) a += partial[static_cast<size_t>(s) * width + i];
+  sh[threadIdx.x] = a;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) raw[s] = sh[0];
+}
+
+// raw dot slots -> normalised moments d_m = mu_m / norm.
+// DOS (doubled): raw[0] = <V0,V0>, step k: raw[1+2k] = <V_{k+1},V_{k+1}>,
+// raw[2+2k] = <V_{k+1},V_k>.  LDOS (direct): raw[m] = mu_m.
+__global__ void k_moments_from_raw(const double* __restrict__ raw, int M, int doubled, double norm,
+                                   double* __restrict__ d) {
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) {
+    double mu;
+    if (!doubled) {
+      mu = raw[m];
+    } else if (m == 0) {
+      mu = raw[0];
+    } else if (m == 1) {
+      mu = raw[2];
+    } else if ((m & 1) == 0) {
+      const int k = m / 2 - 1;
+      mu = 2.0 * raw[1 + 2 * k] - raw[0];
+    } else {
+      const int k = (m - 1) / 2;
+      mu = 2.0 * raw[2 + 2 * k] - raw[2];
+    }
+    d[m] = mu / norm;
+  }
+}
+
+__global__ void k_fill_f32(float* __restrict__ p, int64_t n, float v) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    p[i] = v;
+}
+
+
+static int g_force_t = 0;  // 0 = planner's choice
+static int g_force_p = 0;
+
+static int elem_size(int prec) { return prec == DOS_FP32 ? 4 : 2; }
+
+template <typename T>
+static int occupancy_for(const Plan& plan) {
+  return step_occupancy<T>(plan);
+}
+
+static int occupancy(int prec, const Plan& plan) {
+  switch (prec) {
+    case DOS_BF16:
+      return occupancy_for<__nv_bfloat16>(plan);
+    case DOS_FP16:
+      return occupancy_for<__half>(plan);
+    default:
+      return occupancy_for<float>(plan);
+  }
+}
+
+// Probe tiling.  A tile of t probe columns is what concurrently running CTAs
+// gather from, so t is chosen so that one tile of U_k (n * t elements) fits
+// in a share of L2 when possible; among the tilings that fit, the one with
+// the least modelled traffic per step (T re-reads of the CSR + three probe
+// blocks including padding) wins.
+int make_plan(const Graph* G, int Nz, int prec, Plan* out) {
+  const int es = elem_size(prec);
+  const int V = 16 / es;
+  const int qmax = prec == DOS_FP32 ? 16 : 8;
+  const double budget = 80.0e6;
+  const double n = static_cast<double>(G->n), nnz = static_cast<double>(G->nnz);
+  bool have = false, have_fit = false;
+  double best = 0.0;
+  Plan pl;
+  for (int q = 1; q <= qmax; q *= 2) {
+    const int t = q * V;
+    if (g_force_t && t != g_force_t) continue;
+    const int tiles = (Nz + t - 1) / t;
+    const int nz_pad = tiles * t;
+    const double bytes = tiles * (4.0 * nnz + 8.0 * (n + 1) + 8.0 * n) + 3.0 * n * nz_pad * es;
+    const bool fits = n * t * es <= budget;
+    bool take = false;
+    if (!have) take = true;
+    else if (fits && !have_fit) take = true;
+    else if (fits == have_fit && bytes < best) take = true;
+    if (take) {
+      have = true;
+      have_fit = fits;
+      best = bytes;
+      pl.t = t;
+      pl.q = q;
+      pl.tiles = tiles;
+      pl.nz_pad = nz_pad;
+    }
+  }
+  if (!have) return fail(DOS_EINVAL, "no tile width matches the forced plan");
+  // neighbour slots per light row from the light rows' mean degree
+  const double light_rows = std::max(1.0, n - static_cast<double>(G->n_heavy));
+  const double avg = nnz / std::max(1.0, n) * (n / light_rows);
+  int p = 1;
+  while (p < 4 && pl.q * p * 2 <= 32 && avg >= 8.0 * p) p *= 2;
+  if (g_force_p) {
+    if (g_force_p != 1 && g_force_p != 2 && g_force_p != 4) return fail(DOS_EINVAL, "slots must be 1, 2 or 4");
+    if (pl.q * g_force_p > 32) return fail(DOS_EINVAL, "slots * lanes per row exceeds a warp");
+    p = g_force_p;
+  }
+  pl.p = p;
+  const int sms = num_sms();
+  const int occ = occupancy(prec, pl);
+  pl.heavy_ctas = static_cast<int>(std::min<int64_t>(G->n_heavy, 4LL * sms));
+  const int64_t light_n = G->n - G->n_heavy;
+  const int64_t rows_per_cta = static_cast<int64_t>(kStepWarps) * (32 / (pl.q * pl.p));
+  int64_t light = (light_n + rows_per_cta - 1) / rows_per_cta;
+  light = std::min<int64_t>(light, static_cast<int64_t>(occ) * sms);
+  if (light < 1) light = 1;
+  pl.gx = pl.heavy_ctas + static_cast<int>(light);
+  *out = pl;
+  return DOS_OK;
+}
+
+template <typename T>
+static int run_steps(const Graph* G, const Filter* F, const Plan& plan, int M, int Nz, uint64_t seed, int mode,
+                     double* d_out, float* C_out, cudaStream_t s) {
+  constexpr int V = VecT<T>::N;
+  const int64_t n = G->n;
+  const int steps = mode == kModeDos ? M / 2 : M - 1;
+  const int n_dots = mode == kModeDos ? 2 : 1;
+  const int64_t width = static_cast<int64_t>(plan.tiles) * plan.gx;
+  const int64_t n_raw = 1 + static_cast<int64_t>(steps) * n_dots;
+  const size_t elems = static_cast<size_t>(n) * plan.nz_pad;
+
+  T *ua = nullptr, *ub = nullptr;
+  double *partial = nullptr, *raw = nullptr;
+  float* csum = nullptr;
+  int st = DOS_OK;
+  const auto cleanup = [&]() {
+    dfree(ua, s);
+    dfree(ub, s);
+    dfree(partial, s);
+    dfree(raw, s);
+    dfree(csum, s);
+  };
+  if ((st = dalloc_t(&ua, elems, s)) || (st = dalloc_t(&ub, elems, s)) ||
+      (st = dalloc_t(&partial, static_cast<size_t>(n_raw) * width, s)) || (st = dalloc_t(&raw, n_raw, s))) {
+    cleanup();
+    return st;
+  }
+  const auto cu = [&](cudaError_t e, const char* what) {
+    if (e != cudaSuccess && st == DOS_OK) st = cuda_fail(e, what, __FILE__, __LINE__);
+  };
+  cu(cudaMemsetAsync(partial, 0, sizeof(double) * width, s), "cudaMemsetAsync");
+
+  InitParams ip{};
+  ip.orig = G->p_orig;
+  ip.compact = G->p_compact;
+  ip.s32 = G->s32;
+  ip.u0 = ua;
+  ip.n = n;
+  ip.t = plan.t;
+  ip.nz = Nz;
+  ip.nz_pad = plan.nz_pad;
+  ip.seed = seed;
+  ip.partial = partial;
+  if (F && F->n_classes > 0 && st == DOS_OK) {
+    if ((st = dalloc_t(&csum, static_cast<size_t>(F->n_classes) * plan.nz_pad, s)) == DOS_OK) {
+      cu(cudaMemsetAsync(csum, 0, sizeof(float) * F->n_classes * plan.nz_pad, s), "cudaMemsetAsync");
+      const int64_t work = n * ((Nz + 63) / 64);
+      const unsigned g = static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, 8LL * num_sms())));
+      k_class_sums<<<g, 256, 0, s>>>(G->p_orig, F->p_slot, n, Nz, plan.nz_pad, seed, csum);
+      count_launch();
+      cu(cudaGetLastError(), "k_class_sums");
+      ip.slot = F->p_slot;
+      ip.slot_size = F->slot_size;
+      ip.csum = csum;
+    }
+  }
+  const int64_t chunks = n * (plan.nz_pad / V);
+  const int init_grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((chunks + 255) / 256, width)));
+  if (st == DOS_OK) st = launch_init<T>(ip, init_grid, s);
+
+  if (mode == kModeLdos && st == DOS_OK) {
+    if (plan.tiles > 1) cu(cudaMemsetAsync(C_out, 0, sizeof(float) * static_cast<size_t>(M) * n, s), "memset C");
+    k_fill_f32<<<std::min<unsigned>(4096, std::max<unsigned>(1, ceil_div(n, 256))), 256, 0, s>>>(C_out, n, 1.0f);
+    count_launch();
+    cu(cudaGetLastError(), "k_fill_f32");
+  }
+
+  StepParams prm{};
+  prm.row_ptr = G->p_row_ptr;
+  prm.col = G->p_col;
+  prm.deg = G->p_deg;
+  prm.orig = G->p_orig;
+  prm.compact = G->p_compact;
+  prm.n = n;
+  prm.n_heavy = G->n_heavy;
+  prm.heavy_ctas = plan.heavy_ctas;
+  prm.nz = Nz;
+  prm.inv_nz = 1.0f / static_cast<float>(Nz);
+  prm.seed = seed;
+  prm.ldos_atomic = plan.tiles > 1 ? 1 : 0;
+  const bool prof = profiling_on();
+  for (int k = 0; k < steps && st == DOS_OK; ++k) {
+    prm.u_cur = (k & 1) ? ub : ua;
+    prm.u_pn = (k & 1) ? ua : ub;
+    prm.first = k == 0 ? 1 : 0;
+    prm.partial = partial + static_cast<size_t>(1 + static_cast<int64_t>(k) * n_dots) * width;
+    prm.ldos = mode == kModeLdos ? C_out + static_cast<size_t>(k + 1) * n : nullptr;
+    if (prof) profile_begin(s);
+    st = launch_step<T>(plan, mode, prm, s);
+    if (prof) profile_end(s);
+  }
+  if (st == DOS_OK) {
+    k_reduce_partials<<<static_cast<unsigned>(n_raw), 256, 0, s>>>(partial, width, raw);
+    count_launch();
+    cu(cudaGetLastError(), "k_reduce_partials");
+  }
+  if (st == DOS_OK && d_out) {
+    const double r = F ? static_cast<double>(n - F->removed) : static_cast<double>(n);
+    k_moments_from_raw<<<1, 256, 0, s>>>(raw, M, mode == kModeDos ? 1 : 0, r * Nz, d_out);
+    count_launch();
+    cu(cudaGetLastError(), "k_moments_from_raw");
+  }
+  cleanup();
+  return st;
+}
+
+static int run_kpm(const Graph* G, const Filter* F, int M, int Nz, uint64_t seed, int prec, int mode,
+                   double* d_out, float* C_out, cudaStream_t s) {
+  if (!G) return fail(DOS_EINVAL, "null graph");
+  if (G->n < 1) return fail(DOS_EINVAL, "graph has no edges");
+  if (M < 1 || M > (1 << 20)) return fail(DOS_EINVAL, "M must be in [1, 2^20]");
+  if (Nz < 1 || Nz > 65536) return fail(DOS_EINVAL, "Nz must be in [1, 65536]");
+  if (prec != DOS_FP32 && prec != DOS_BF16 && prec != DOS_FP16) return fail(DOS_EINVAL, "unknown precision");
+  if (F && F->g != G) return fail(DOS_EINVAL, "filter belongs to another graph");
+  Plan plan;
+  NDOS_CHECK(make_plan(G, Nz, prec, &plan));
+  switch (prec) {
+    case DOS_BF16:
+      return run_steps<__nv_bfloat16>(G, F, plan, M, Nz, seed, mode, d_out, C_out, s);
+    case DOS_FP16:
+      return run_steps<__half>(G, F, plan, M, Nz, seed, mode, d_out, C_out, s);
+    default:
+      return run_steps<float>(G, F, plan, M, Nz, seed, mode, d_out, C_out, s);
+  }
+}
+
+}  // namespace netdos
+
+using namespace netdos;
+
+extern "C" {
+
+int dos_moments(dos_graph_t g, dos_filter_t f, int M, int Nz, uint64_t seed, int prec, double* d_out,
+                void* stream) {
+  clear_error();
+  if (!d_out) return fail(DOS_EINVAL, "dos_moments: d_out is NULL");
+  return run_kpm(reinterpret_cast<const Graph*>(g), reinterpret_cast<const Filter*>(f), M, Nz, seed, prec,
+                 kModeDos, d_out, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+int ldos_moments(dos_graph_t g, int M, int Nz, uint64_t seed, int prec, float* C_out, double* d_out,
+                 void* stream) {
+  clear_error();
+  if (!C_out) return fail(DOS_EINVAL, "ldos_moments: C_out is NULL");
+  return run_kpm(reinterpret_cast<const Graph*>(g), nullptr, M, Nz, seed, prec, kModeLdos, d_out, C_out,
+                 static_cast<cudaStream_t>(stream));
+}
+
+int dos_set_plan(int tile_width, int slots) {
+  if (tile_width != 0 && (tile_width < 4 || tile_width > 64 || (tile_width & (tile_width - 1))))
+    return fail(DOS_EINVAL, "dos_set_plan: tile width must be 0 or a power of two in [4, 64]");
+  if (slots != 0 && slots != 1 && slots != 2 && slots != 4)
+    return fail(DOS_EINVAL, "dos_set_plan: slots must be 0, 1, 2 or 4");
+  g_force_t = tile_width;
+  g_force_p = slots;
+  return DOS_OK;
+}
+
+int dos_get_plan(dos_graph_t g, int Nz, int prec, int* tile_width, int* slots, int* tiles, int* grid_x) {
+  Plan pl;
+  if (!g) return fail(DOS_EINVAL, "dos_get_plan: null graph");
+  NDOS_CHECK(make_plan(reinterpret_cast<const Graph*>(g), Nz, prec, &pl));
+  if (tile_width) *tile_width = pl.t;
+  if (slots) *slots = pl.p;
+  if (tiles) *tiles = pl.tiles;
+  if (grid_x) *grid_x = pl.gx;
+  return DOS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,232 @@
+// dos_motif_filter: classes of nodes with identical neighbourhoods, the
+// lambda = 0 twin motif of §3.4 (Fig. 3a).
+//
+// Detection follows the paper's hashing idea with an integer hash: each node
+// gets h_i = mix(d_i) + sum_{j in N(i)} mix(j) (mod 2^64), an order-free
+// function of its neighbour set, so twins always share a hash.  Nodes are
+// sorted by hash (stable in the node id); inside each run of equal hashes the
+// neighbour lists are compared exactly, so a hash collision never merges
+// different neighbourhoods.  Class id = smallest member (compact id).
+#include <cub/device/device_radix_sort.cuh>
+#include <cub/device/device_scan.cuh>
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace netdos {
+namespace {
+
+__device__ __forceinline__ uint64_t mix_id(uint64_t x) { return splitmix64(0x5bd1e9955bd1e995ull, x); }
+
+// warp per row: order-free neighbourhood hash
+__global__ void k_row_hash(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                           const int32_t* __restrict__ deg, int64_t n, uint64_t* __restrict__ hash,
+                           int32_t* __restrict__ idx) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
+  const int64_t nw = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t i = w0; i < n; i += nw) {
+    uint64_t h = 0;
+    for (int64_t e = row_ptr[i] + lane; e < row_ptr[i + 1]; e += 32) h += mix_id(static_cast<uint64_t>(col[e]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xffffffffu, h, o);
+    if (lane == 0) {
+      hash[i] = h + mix_id(0x8000000000000000ull | static_cast<uint64_t>(deg[i]));
+      idx[i] = static_cast<int32_t>(i);
+    }
+  }
+}
+
+// after sorting: class_id = own id for nodes alone in their hash run, -1 for
+// members of longer runs; record the start of each longer run
+__global__ void k_mark_runs(const uint64_t* __restrict__ h, const int32_t* __restrict__ node, int64_t n,
+                            int32_t* __restrict__ class_id, int64_t* __restrict__ run_start,
+                            unsigned long long* __restrict__ n_runs) {
+  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < n;
+       k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const bool same_prev = k > 0 && h[k - 1] == h[k];
+    const bool same_next = k + 1 < n && h[k + 1] == h[k];
+    class_id[node[k]] = (same_prev || same_next) ? -1 : node[k];
+    if (!same_prev && same_next) run_start[atomicAdd(n_runs, 1ull)] = k;
+  }
+}
+
+__device__ __forceinline__ bool same_list(const int64_t* row_ptr, const int32_t* col, int32_t a, int32_t b) {
+  const int64_t ba = row_ptr[a], bb = row_ptr[b];
+  const int64_t la = row_ptr[a + 1] - ba;
+  if (la != row_ptr[b + 1] - bb) return false;
+  for (int64_t e = 0; e < la; ++e)
+    if (col[ba + e] != col[bb + e]) return false;
+  return true;
+}
+
+// warp per run: repeated leader election in id order; every unassigned member
+// equal to the leader joins its class
+__global__ void k_resolve_runs(const uint64_t* __restrict__ h, const int32_t* __restrict__ node, int64_t n,
+                               const int64_t* __restrict__ run_start, int64_t n_runs,
+                               const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                               int32_t* class_id) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
+  const int64_t nw = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t r = w0; r < n_runs; r += nw) {
+    const int64_t a = run_start[r];
+    int64_t b = a + 1;
+    while (b < n && h[b] == h[a]) ++b;
+    for (int64_t lead = a; lead < b; ++lead) {
+      const int32_t ln = node[lead];
+      __syncwarp();
+      if (*reinterpret_cast<volatile int32_t*>(class_id + ln) != -1) continue;  // warp-uniform
+      if (lane == 0) class_id[ln] = ln;
+      for (int64_t k = lead + 1 + lane; k < b; k += 32) {
+        const int32_t m = node[k];
+        if (*reinterpret_cast<volatile int32_t*>(class_id + m) == -1 && same_list(row_ptr, col, ln, m))
+          class_id[m] = ln;
+      }
+      __syncwarp();
+    }
+  }
+}
+
+__global__ void k_class_counts(const int32_t* __restrict__ class_id, int64_t n, int32_t* __restrict__ cnt,
+                               unsigned long long* __restrict__ removed) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int32_t c = class_id[i];
+    atomicAdd(&cnt[c], 1);
+    if (c != i) atomicAdd(removed, 1ull);
+  }
+}
+
+__global__ void k_leader_flags(const int32_t* __restrict__ cnt, int64_t n, int32_t* __restrict__ flag) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    flag[i] = cnt[i] >= 2 ? 1 : 0;
+}
+
+// slot of each position's class (degree-sorted order) and class sizes
+__global__ void k_slots(const int32_t* __restrict__ class_id, const int32_t* __restrict__ cnt,
+                        const int32_t* __restrict__ slot_of_leader, const int32_t* __restrict__ p_compact, int64_t n,
+                        int32_t* __restrict__ p_slot, int32_t* __restrict__ slot_size) {
+  for (int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; p < n;
+       p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int32_t c = class_id[p_compact[p]];
+    const int32_t sz = cnt[c];
+    if (sz >= 2) {
+      const int32_t sl = slot_of_leader[c];
+      p_slot[p] = sl;
+      slot_size[sl] = sz;
+    } else {
+      p_slot[p] = -1;
+    }
+  }
+}
+
+inline unsigned grid_for(int64_t work, int per_block = 256) {
+  int64_t b = (work + per_block - 1) / per_block;
+  const int64_t cap = static_cast<int64_t>(num_sms()) * 32;
+  if (b > cap) b = cap;
+  return static_cast<unsigned>(b < 1 ? 1 : b);
+}
+
+
+}  // namespace
+
+static int motif_filter_impl(const Graph* G, cudaStream_t s, Filter* F) {
+  const int64_t n = G->n;
+  Temps t(s);
+  auto palloc = [](int32_t** p, int64_t count) -> int {
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), sizeof(int32_t) * (count > 0 ? count : 1));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return cuda_fail(e, "cudaMalloc", __FILE__, __LINE__);
+    }
+    return DOS_OK;
+  };
+  NDOS_CHECK(palloc(&F->class_id, n));
+  NDOS_CHECK(palloc(&F->p_slot, n));
+  if (n == 0) {
+    NDOS_CHECK(palloc(&F->slot_size, 1));
+    return DOS_OK;
+  }
+  uint64_t *h = nullptr, *h_alt = nullptr;
+  int32_t *idx = nullptr, *idx_alt = nullptr, *cnt = nullptr, *flag = nullptr, *slot_of = nullptr;
+  int64_t* run_start = nullptr;
+  unsigned long long* counters = nullptr;  // [0] runs, [1] removed
+  NDOS_CHECK(t.get(&h, n));
+  NDOS_CHECK(t.get(&h_alt, n));
+  NDOS_CHECK(t.get(&idx, n));
+  NDOS_CHECK(t.get(&idx_alt, n));
+  NDOS_CHECK(t.get(&cnt, n));
+  NDOS_CHECK(t.get(&flag, n + 1));
+  NDOS_CHECK(t.get(&slot_of, n + 1));
+  NDOS_CHECK(t.get(&run_start, n));
+  NDOS_CHECK(t.get(&counters, 2));
+  NDOS_CUDA(cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned long long), s));
+  NDOS_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * n, s));
+
+  k_row_hash<<<grid_for(n * 32), 256, 0, s>>>(G->row_ptr, G->col, G->deg, n, h, idx);
+  NDOS_LAUNCHED();
+  cub::DoubleBuffer<uint64_t> kb(h, h_alt);
+  cub::DoubleBuffer<int32_t> vb(idx, idx_alt);
+  size_t bytes = 0;
+  NDOS_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, bytes, kb, vb, n, 0, 64, s));
+  char* tmp = nullptr;
+  NDOS_CHECK(t.get(&tmp, bytes));
+  NDOS_CUDA(cub::DeviceRadixSort::SortPairs(tmp, bytes, kb, vb, n, 0, 64, s));
+  count_launch();
+  k_mark_runs<<<grid_for(n), 256, 0, s>>>(kb.Current(), vb.Current(), n, F->class_id, run_start, counters);
+  NDOS_LAUNCHED();
+  unsigned long long n_runs = 0;
+  NDOS_CUDA(cudaMemcpyAsync(&n_runs, counters, sizeof(n_runs), cudaMemcpyDeviceToHost, s));
+  NDOS_CUDA(cudaStreamSynchronize(s));
+  if (n_runs > 0) {
+    k_resolve_runs<<<grid_for(static_cast<int64_t>(n_runs) * 32), 256, 0, s>>>(
+        kb.Current(), vb.Current(), n, run_start, static_cast<int64_t>(n_runs), G->row_ptr, G->col, F->class_id);
+    NDOS_LAUNCHED();
+  }
+  k_class_counts<<<grid_for(n), 256, 0, s>>>(F->class_id, n, cnt, counters + 1);
+  NDOS_LAUNCHED();
+  k_leader_flags<<<grid_for(n), 256, 0, s>>>(cnt, n, flag);
+  NDOS_LAUNCHED();
+  NDOS_CUDA(cudaMemsetAsync(flag + n, 0, sizeof(int32_t), s));
+  bytes = 0;
+  NDOS_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, bytes, flag, slot_of, n + 1, s));
+  char* tmp2 = nullptr;
+  NDOS_CHECK(t.get(&tmp2, bytes));
+  NDOS_CUDA(cub::DeviceScan::ExclusiveSum(tmp2, bytes, flag, slot_of, n + 1, s));
+  count_launch();
+  int32_t n_classes = 0;
+  unsigned long long removed = 0;
+  NDOS_CUDA(cudaMemcpyAsync(&n_classes, slot_of + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  NDOS_CUDA(cudaMemcpyAsync(&removed, counters + 1, sizeof(removed), cudaMemcpyDeviceToHost, s));
+  NDOS_CUDA(cudaStreamSynchronize(s));
+  F->n_classes = n_classes;
+  F->removed = static_cast<int64_t>(removed);
+  NDOS_CHECK(palloc(&F->slot_size, n_classes));
+  k_slots<<<grid_for(n), 256, 0, s>>>(F->class_id, cnt, slot_of, G->p_compact, n, F->p_slot, F->slot_size);
+  NDOS_LAUNCHED();
+  NDOS_CUDA(cudaStreamSynchronize(s));
+  return DOS_OK;
+}
+
+}  // namespace netdos
+
+using namespace netdos;
+
+extern "C" int dos_motif_filter(dos_graph_t g, void* stream, dos_filter_t* out) {
+  clear_error();
+  if (!out) return fail(DOS_EINVAL, "dos_motif_filter: out is NULL");
+  *out = nullptr;
+  if (!g) return fail(DOS_EINVAL, "dos_motif_filter: null graph");
+  Filter* F = new Filter();
+  F->g = reinterpret_cast<const Graph*>(g);
+  int st = motif_filter_impl(F->g, static_cast<cudaStream_t>(stream), F);
+  if (st != DOS_OK) {
+    dos_filter_destroy(reinterpret_cast<dos_filter_t>(F));
+    return st;
+  }
+  *out = reinterpret_cast<dos_filter_t>(F);
+  return DOS_OK;
+}

@@ -1,0 +1,255 @@
+"""GPU parity: the CUDA library (through the C ABI) against the CPU oracle on
+identical seeded inputs.
+
+Tolerances:
+* CSR, degrees, 1/sqrt(d), old ids, twin classes: bit-exact.
+* FP32 DOS moments: |d_gpu - d_oracle| <= 1e-5 absolute on the normalised
+  moments (|d_m| <= d_0 = 1), identical probes.
+* FP32 per-node (LDOS) moments C[k, m]: <= 1e-4 absolute for M <= 100.  Each
+  step rounds every entry with relative error ~6e-8 and the Chebyshev
+  recurrence carries an error made at step s into step m with a factor
+  |U_{m-s}| <= m - s + 1, so per-entry errors accumulate like a random walk,
+  ~ eps * m^1.5 / sqrt(3) ~ 3.5e-5 at m = 100 before the 1/Nz average; the
+  bound keeps a margin for the maximum over N * M entries.
+* Density from the same moments: 1e-12 (FP64 on both sides).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synthgraphs as sg
+
+pytestmark = pytest.mark.gpu
+
+nd = pytest.importorskip("paper_1905_09758_gb300")
+
+TOL_D = 1e-5
+TOL_C = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1905_09758_gb300.build import build
+
+    build()
+    yield
+    nd.dos_set_plan(0, 0)
+
+
+def _gpu_graph(src, dst, n, host=False):
+    s = torch.from_numpy(np.ascontiguousarray(src, np.int64))
+    d = torch.from_numpy(np.ascontiguousarray(dst, np.int64))
+    if not host:
+        s, d = s.cuda(), d.cuda()
+    return nd.dos_build_csr(s, d, n)
+
+
+def _graphs():
+    yield "er2000", sg.erdos_renyi(2000, 0.005, 1)
+    s, d, n = sg.chung_lu(6000, 2.5, 12.0, 7)
+    yield "cl_twins", sg.add_twin_leaves(s, d, n, 300, 8)
+    # a hub of degree 3000 exercises the CTA-per-row path
+    s, d, n = sg.erdos_renyi(4000, 0.003, 2)
+    hub = np.zeros(3000, np.int64)
+    leaves = 1 + np.arange(3000, dtype=np.int64)
+    yield "hub", (np.concatenate([s, hub, [5, 5, 9]]), np.concatenate([d, leaves, [5, 9, 5]]), n)
+    yield "ba", sg.barabasi_albert(3000, 4, 3)
+
+
+GRAPHS = dict(_graphs())
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+def test_csr_bit_exact(name):
+    src, dst, n = GRAPHS[name]
+    ref = oracle.build_csr(src, dst, n)
+    g = _gpu_graph(src, dst, n)
+    info = g.info()
+    assert (info["n"], info["nnz"], info["n_isolated"], info["n_original"]) == (ref.n, ref.nnz, ref.n_isolated, n)
+    ex = {k: v.cpu().numpy() for k, v in nd.dos_graph_export(g).items()}
+    assert np.array_equal(ex["row_ptr"], ref.row_ptr)
+    assert np.array_equal(ex["col"], ref.col)
+    assert np.array_equal(ex["deg"], ref.deg)
+    assert np.array_equal(ex["inv_sqrt_deg"], ref.s64)
+    assert np.array_equal(ex["inv_sqrt_deg32"], ref.s32)
+    assert np.array_equal(ex["old_id"], ref.old_id)
+
+
+def test_csr_from_host_buffers_and_edge_cases():
+    src = np.array([0, 1, 1, 3, 3, 5, 2, 0, 6])
+    dst = np.array([1, 0, 1, 5, 5, 3, 2, 6, 0])
+    ref = oracle.build_csr(src, dst, 9)
+    g = _gpu_graph(src, dst, 9, host=True)
+    ex = nd.dos_graph_export(g)
+    assert np.array_equal(ex["col"].cpu().numpy(), ref.col)
+    assert g.info()["n_isolated"] == ref.n_isolated == 4  # nodes 2 (self-loop only), 4, 7, 8
+    # no edges at all
+    g0 = _gpu_graph(np.zeros(0, np.int64), np.zeros(0, np.int64), 7)
+    assert g0.info() == {"n": 0, "nnz": 0, "n_isolated": 7, "n_original": 7}
+    with pytest.raises(nd.DosError):
+        nd.dos_moments(g0, 10, 4, 1)
+    # only self-loops
+    g1 = _gpu_graph(np.array([3, 3]), np.array([3, 3]), 4)
+    assert g1.info()["nnz"] == 0
+
+
+def test_invalid_ids_are_rejected():
+    with pytest.raises(nd.DosError) as e:
+        _gpu_graph(np.array([0, 7]), np.array([1, 2]), 5)
+    assert e.value.status == nd.DOS_EINVAL
+    with pytest.raises(nd.DosError):
+        _gpu_graph(np.array([-1]), np.array([1]), 5)
+
+
+def _dos_ref(ref, seed, nz, m, filt=None):
+    z = oracle.probes(seed, ref.old_id, nz)
+    r = ref.n
+    if filt is not None:
+        cid, removed = filt
+        z = oracle.project_probes(z, cid)
+        r = ref.n - removed
+    return oracle.kpm_doubled(ref, z, m) / (r * nz)
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+@pytest.mark.parametrize("m,nz", [(100, 20), (31, 37), (2, 1), (1, 5)])
+def test_dos_moments_fp32(name, m, nz):
+    src, dst, n = GRAPHS[name]
+    ref = oracle.build_csr(src, dst, n)
+    g = _gpu_graph(src, dst, n)
+    d = nd.dos_moments(g, m, nz, 11).cpu().numpy()
+    d_ref = _dos_ref(ref, 11, nz, m)
+    assert abs(d[0] - 1.0) < 1e-12
+    assert np.abs(d - d_ref).max() <= TOL_D
+
+
+PLANS = [(t, p) for t in (4, 8, 16, 32, 64) for p in (1, 2, 4) if (t // 4) * p <= 32]
+
+
+@pytest.mark.parametrize("t,p", PLANS)
+def test_every_kernel_variant_fp32(t, p):
+    src, dst, n = GRAPHS["hub"]
+    ref = oracle.build_csr(src, dst, n)
+    g = _gpu_graph(src, dst, n)
+    nd.dos_set_plan(t, p)
+    try:
+        plan = nd.dos_get_plan(g, 70)
+        assert plan["tile_width"] == t and plan["slots"] == p
+        d = nd.dos_moments(g, 24, 70, 5).cpu().numpy()
+        c, dl = nd.ldos_moments(g, 12, 70, 5)
+    finally:
+        nd.dos_set_plan(0, 0)
+    assert np.abs(d - _dos_ref(ref, 5, 70, 24)).max() <= TOL_D
+    z = oracle.probes(5, ref.old_id, 70)
+    mu, cref = oracle.kpm_direct(ref, z, 12, ldos=True)
+    assert np.abs(c.cpu().numpy().T - cref).max() <= TOL_C
+    assert np.abs(dl.cpu().numpy() - mu / (ref.n * 70)).max() <= TOL_D
+
+
+@pytest.mark.parametrize("name", ["er2000", "cl_twins", "hub"])
+def test_ldos_fp32(name):
+    src, dst, n = GRAPHS[name]
+    ref = oracle.build_csr(src, dst, n)
+    g = _gpu_graph(src, dst, n)
+    m, nz = 100, 20
+    c, dl = nd.ldos_moments(g, m, nz, 3)
+    z = oracle.probes(3, ref.old_id, nz)
+    mu, cref = oracle.kpm_direct(ref, z, m, ldos=True)
+    c = c.cpu().numpy()
+    assert c.shape == (m, ref.n)
+    assert np.all(c[0] == 1.0)
+    assert np.abs(c.T - cref).max() <= TOL_C
+    assert np.abs(dl.cpu().numpy() - mu / (ref.n * nz)).max() <= TOL_D
+    # the doubled DOS path and the direct LDOS path estimate the same moments
+    d = nd.dos_moments(g, m, nz, 3).cpu().numpy()
+    assert np.abs(d - dl.cpu().numpy()).max() <= 2 * TOL_D
+
+
+def test_twin_filter_bit_exact_and_filtered_moments():
+    src, dst, n = GRAPHS["cl_twins"]
+    ref = oracle.build_csr(src, dst, n)
+    g = _gpu_graph(src, dst, n)
+    f = nd.dos_motif_filter(g)
+    cid_ref, removed = oracle.twin_classes(ref)
+    cid = nd.dos_filter_export(f).cpu().numpy()
+    assert np.array_equal(cid, cid_ref)
+    info = f.info()
+    assert info["removed"] == removed and info["r"] == ref.n - removed
+    assert info["n_classes"] == int(np.sum(np.bincount(cid_ref, minlength=ref.n) >= 2))
+    d = nd.dos_moments(g, 60, 16, 9, filter=f).cpu().numpy()
+    d_ref = _dos_ref(ref, 9, 16, 60, filt=(cid_ref, removed))
+    assert np.abs(d - d_ref).max() <= TOL_D
+
+
+def test_twin_filter_star_and_bipartite():
+    for (s, d, n), expect in [(sg.star(50), 49), (sg.complete_bipartite(6, 9), 13)]:
+        ref = oracle.build_csr(s, d, n)
+        g = _gpu_graph(s, d, n)
+        f = nd.dos_motif_filter(g)
+        assert f.info()["removed"] == expect
+        assert np.array_equal(nd.dos_filter_export(f).cpu().numpy(), oracle.twin_classes(ref)[0])
+
+
+@pytest.mark.parametrize("kernel", ["jackson", "none"])
+@pytest.mark.parametrize("m,b", [(100, 200), (7, 5), (1, 3), (500, 50)])
+def test_density_matches_oracle(kernel, m, b):
+    rng = np.random.default_rng(m * 1000 + b)
+    d = rng.uniform(-1, 1, m)
+    d[0] = 1.0
+    h = nd.dos_density(torch.from_numpy(d).cuda(), b, kernel=kernel).cpu().numpy()
+    assert np.abs(h - oracle.histogram(d, b, kernel=kernel)).max() <= 1e-12
+
+
+def test_density_spikes_and_scale():
+    d = np.zeros(10)
+    d[0] = 1.0
+    spikes = [(0.0, 0.25), (-1.0, 0.1), (0.33, 0.05)]
+    h = nd.dos_density(torch.from_numpy(d).cuda(), 4, scale=0.6, spikes=spikes).cpu().numpy()
+    ref = 0.6 * oracle.histogram(d, 4) + oracle.point_mass_histogram([s[0] for s in spikes], [s[1] for s in spikes], 4)
+    assert np.abs(h - ref).max() <= 1e-12
+
+
+def test_filtered_density_assembly():
+    src, dst, n = GRAPHS["cl_twins"]
+    ref = oracle.build_csr(src, dst, n)
+    g = _gpu_graph(src, dst, n)
+    f = nd.dos_motif_filter(g)
+    d = nd.dos_moments(g, 80, 16, 4, filter=f)
+    h = nd.density_with_spikes(d, g, 50, filter=f).cpu().numpy()
+    cid, removed = oracle.twin_classes(ref)
+    n_total = ref.n + ref.n_isolated
+    d_ref = _dos_ref(ref, 4, 16, 80, filt=(cid, removed))
+    h_ref = (ref.n - removed) / n_total * oracle.histogram(d_ref, 50)
+    h_ref += oracle.point_mass_histogram([0.0], [(removed + ref.n_isolated) / n_total], 50)
+    assert abs(h.sum() - 1.0) < 1e-3
+    assert np.abs(h - h_ref).max() <= 1e-5
+
+
+def test_argument_errors():
+    src, dst, n = GRAPHS["er2000"]
+    g = _gpu_graph(src, dst, n)
+    for bad in [dict(M=0, Nz=4), dict(M=4, Nz=0), dict(M=4, Nz=70000)]:
+        with pytest.raises(nd.DosError) as e:
+            nd.dos_moments(g, bad["M"], bad["Nz"], 1, d_out=torch.empty(max(1, bad["M"]), dtype=torch.float64,
+                                                                           device="cuda"))
+        assert e.value.status == nd.DOS_EINVAL
+    with pytest.raises(nd.DosError):
+        nd.dos_density(torch.zeros(4, dtype=torch.float64, device="cuda"), 0)
+    # a filter from another graph is refused
+    g2 = _gpu_graph(*sg.star(5))
+    f2 = nd.dos_motif_filter(g2)
+    with pytest.raises(nd.DosError):
+        nd.dos_moments(g, 4, 4, 1, filter=f2)
+
+
+def test_kernels_are_counted():
+    src, dst, n = GRAPHS["er2000"]
+    g = _gpu_graph(src, dst, n)
+    before = nd.dos_launch_count()
+    nd.dos_moments(g, 40, 8, 1)
+    torch.cuda.synchronize()
+    # init + 20 steps + reduction + moments
+    assert nd.dos_launch_count() - before >= 23
