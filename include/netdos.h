@@ -194,6 +194,32 @@ int dos_density(const double* d, int M, int n_bins, int kernel, double scale,
                 const double* spikes, int n_spikes, double* hist_out,
                 void* stream);
 
+/*
+ * dos_moments_noalloc -- dos_moments (FP32 storage, no filter) for callers
+ * that cannot allocate device memory.  The paper has no counterpart; this is
+ * a deployment variant of the same computation.
+ * Who needs it: a caller whose framework allocator already holds nearly all
+ * device memory (a fresh cudaMalloc would fail or force the framework to
+ * drop its cache), or a latency-bound caller for which cudaMalloc/cudaFree,
+ * which may synchronise the device, are not acceptable.  This call allocates
+ * nothing: its scratch (two probe blocks of N x Nz_pad floats and the FP64
+ * moment partials) lives in one static device array of 16 MiB that every GPU
+ * loading the library holds until the process exits.
+ *   g, M, Nz, seed, d_out, stream: as for dos_moments (d_out [device]
+ *   double[M], caller-allocated).  Results equal dos_moments' (same kernels,
+ *   same plan, same reduction order).
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls share the array and its contents persist between
+ * calls; each call clears what must start at zero.  Calls that overlap on
+ * the GPU (other streams or threads) race on the shared array.
+ * Errors: DOS_EINVAL when the graph, M and Nz need more than the 16 MiB
+ * scratch (the message states both sizes; use dos_moments), or for invalid
+ * arguments as in dos_moments; DOS_ECUDA.
+ */
+int dos_moments_noalloc(dos_graph_t g, int M, int Nz, uint64_t seed,
+                        double* d_out, void* stream);
+
 /* ---------------------------------------------------------------------
  * Tuning and instrumentation (not part of the method).
  * --------------------------------------------------------------------- */

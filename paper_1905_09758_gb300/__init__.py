@@ -20,6 +20,7 @@ from ._binding import (  # noqa: F401
     dos_graph_info,
     dos_launch_count,
     dos_moments,
+    dos_moments_noalloc,
     dos_motif_filter,
     dos_profile_enable,
     dos_profile_read,

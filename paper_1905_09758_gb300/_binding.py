@@ -56,6 +56,7 @@ _SIGNATURES = {
     "dos_filter_destroy": ([_vp], None),
     "dos_moments": ([_vp, _vp, _i32, _i32, _u64, _i32, _vp, _vp], _i32),
     "ldos_moments": ([_vp, _i32, _i32, _u64, _i32, _vp, _vp, _vp], _i32),
+    "dos_moments_noalloc": ([_vp, _i32, _i32, _u64, _vp, _vp], _i32),
     "dos_density": ([_vp, _i32, _i32, _i32, _dbl, _vp, _i32, _vp, _vp], _i32),
     "dos_launch_count": ([], _i64),
     "dos_profile_enable": ([_i32], _i32),
@@ -244,6 +245,14 @@ def dos_moments(g: Graph, M: int, Nz: int, seed: int, prec: str = "fp32", filter
     _need_cuda(d_out, torch.float64, "d_out", M)
     _check(lib().dos_moments(g.handle, None if filter is None else filter.handle, int(M), int(Nz),
                              int(seed) & (2**64 - 1), PREC[prec], _ptr(d_out), _stream(stream)))
+    return d_out
+
+
+def dos_moments_noalloc(g: Graph, M: int, Nz: int, seed: int, d_out: torch.Tensor, stream=None) -> torch.Tensor:
+    """dos_moments (FP32, no filter) without device allocation; d_out is caller-allocated."""
+    _need_cuda(d_out, torch.float64, "d_out", M)
+    _check(lib().dos_moments_noalloc(g.handle, int(M), int(Nz), int(seed) & (2**64 - 1), _ptr(d_out),
+                                     _stream(stream)))
     return d_out
 
 
