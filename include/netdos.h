@@ -224,17 +224,25 @@ int dos_moments_noalloc(dos_graph_t g, int M, int Nz, uint64_t seed,
  * Tuning and instrumentation (not part of the method).
  * --------------------------------------------------------------------- */
 
-/* Planner override: force the probe tile width t (a power of two in [4, 64]
- * that is a multiple of 16 bytes of the storage type; 0 = automatic) and the
- * neighbour slots per light row (1, 2 or 4; 0 = automatic) of later
- * dos_moments / ldos_moments calls.  Process-wide.  Errors: DOS_EINVAL. */
-int dos_set_plan(int tile_width, int slots);
+/* Planner override (tuning): force the probe tile width t (a power of two in
+ * [4, 64] that is a multiple of 16 bytes of the storage type; 0 = automatic)
+ * and the resident CTAs per SM of the light-row step kernel (0 = as many as
+ * fit) of later dos_moments / ldos_moments calls.  Process-wide.
+ * Errors: DOS_EINVAL. */
+int dos_set_plan(int tile_width, int ctas_per_sm);
 
-/* The plan dos_moments / ldos_moments would use for (g, Nz, prec): tile
- * width t, neighbour slots, number of tiles T = ceil(Nz / t) and the step
- * grid's x extent [host outputs; any may be NULL]. */
-int dos_get_plan(dos_graph_t g, int Nz, int prec, int* tile_width, int* slots,
-                 int* tiles, int* grid_x);
+/* The plan dos_moments would use for (g, Nz, prec): tile width t, light-row
+ * CTAs per SM, number of tiles T = ceil(Nz / t) and the number of CTAs of the
+ * light-row kernel [host outputs; any may be NULL]. */
+int dos_get_plan(dos_graph_t g, int Nz, int prec, int* tile_width,
+                 int* ctas_per_sm, int* tiles, int* grid_x);
+
+/* Status of the device-side error word of the current device: the step
+ * kernels' waits on their shared-memory pipeline are bounded (2 s); if one
+ * gives up, the kernel records it, leaves, and the affected call's moments are
+ * NaN.  Synchronises `stream`, returns the word in *status (0 = none; may be
+ * NULL) and clears it.  Returns DOS_ETIMEOUT if a wait gave up, else DOS_OK. */
+int dos_device_status(void* stream, int* status);
 
 /* Number of kernels this library has launched since load (all threads). */
 int64_t dos_launch_count(void);

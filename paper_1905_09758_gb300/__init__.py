@@ -13,6 +13,7 @@ from ._binding import (  # noqa: F401
     density_with_spikes,
     dos_build_csr,
     dos_density,
+    dos_device_status,
     dos_filter_export,
     dos_filter_info,
     dos_get_plan,

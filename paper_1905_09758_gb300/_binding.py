@@ -58,6 +58,7 @@ _SIGNATURES = {
     "ldos_moments": ([_vp, _i32, _i32, _u64, _i32, _vp, _vp, _vp], _i32),
     "dos_moments_noalloc": ([_vp, _i32, _i32, _u64, _vp, _vp], _i32),
     "dos_density": ([_vp, _i32, _i32, _i32, _dbl, _vp, _i32, _vp, _vp], _i32),
+    "dos_device_status": ([_vp, C.POINTER(C.c_int)], _i32),
     "dos_launch_count": ([], _i64),
     "dos_profile_enable": ([_i32], _i32),
     "dos_profile_read": ([C.POINTER(C.c_double), _P64, _i32], _i32),
@@ -289,6 +290,13 @@ def dos_density(d: torch.Tensor, n_bins: int, kernel: str = "jackson", scale: fl
     return hist_out
 
 
+def dos_device_status(stream=None) -> int:
+    """Device error word (0 = no bounded wait gave up); raises DosError(DOS_ETIMEOUT) otherwise."""
+    st = C.c_int()
+    _check(lib().dos_device_status(_stream(stream), C.byref(st)))
+    return st.value
+
+
 def dos_launch_count() -> int:
     return int(lib().dos_launch_count())
 
@@ -304,14 +312,15 @@ def dos_profile_read(reset: bool = True):
     return ms.value, n.value
 
 
-def dos_set_plan(tile_width: int = 0, slots: int = 0):
-    _check(lib().dos_set_plan(int(tile_width), int(slots)))
+def dos_set_plan(tile_width: int = 0, ctas_per_sm: int = 0):
+    """Force the probe tile width (4..64) and light-kernel CTAs per SM; 0 = automatic."""
+    _check(lib().dos_set_plan(int(tile_width), int(ctas_per_sm)))
 
 
 def dos_get_plan(g: Graph, Nz: int, prec: str = "fp32") -> dict:
     t, p, tiles, gx = (C.c_int() for _ in range(4))
     _check(lib().dos_get_plan(g.handle, int(Nz), PREC[prec], C.byref(t), C.byref(p), C.byref(tiles), C.byref(gx)))
-    return {"tile_width": t.value, "slots": p.value, "tiles": tiles.value, "grid_x": gx.value}
+    return {"tile_width": t.value, "ctas_per_sm": p.value, "tiles": tiles.value, "grid_x": gx.value}
 
 
 # ---------------------------------------------------------------------------

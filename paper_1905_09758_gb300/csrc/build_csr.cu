@@ -99,7 +99,7 @@ __global__ void k_perm_nodes(const int32_t* __restrict__ p_compact, int64_t n, c
                              const int32_t* __restrict__ old_id, int32_t* __restrict__ compact_to_p,
                              int32_t* __restrict__ p_deg, int64_t* __restrict__ p_deg64,
                              int32_t* __restrict__ p_orig, unsigned long long* __restrict__ n_heavy,
-                             int heavy_deg) {
+                             unsigned long long* __restrict__ n_mid, int heavy_deg, int mid_deg) {
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
        p += (int64_t)gridDim.x * blockDim.x) {
     const int32_t k = p_compact[p];
@@ -109,6 +109,7 @@ __global__ void k_perm_nodes(const int32_t* __restrict__ p_compact, int64_t n, c
     p_deg64[p] = d;
     p_orig[p] = old_id[k];
     if (d >= heavy_deg) atomicAdd(n_heavy, 1ull);
+    if (d >= mid_deg) atomicAdd(n_mid, 1ull);
   }
 }
 
@@ -122,6 +123,32 @@ __global__ void k_perm_keys(const uint64_t* __restrict__ keys, int64_t nnz, cons
     const uint64_t pv = static_cast<uint32_t>(compact_to_p[new_id[key & 0xffffffffull]]);
     out[k] = (pu << 32) | pv;
   }
+}
+
+// light row i (position n_mid + i) starts an item at i = 0, every kItemRows
+// rows, and wherever its row offset enters a new multiple of kItemNnzStep; an
+// item then holds fewer than kItemNnzStep + kMediumDeg nonzeros
+__global__ void k_item_flags(const int64_t* __restrict__ p_row_ptr, int64_t n_mid, int64_t n_light,
+                             int32_t* __restrict__ flag) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_light;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = n_mid + i;
+    flag[i] = (i == 0 || i % kItemRows == 0 || p_row_ptr[r] / kItemNnzStep != p_row_ptr[r - 1] / kItemNnzStep) ? 1 : 0;
+  }
+}
+
+__global__ void k_item_scatter(const int32_t* __restrict__ flag, const int32_t* __restrict__ id, int64_t n_light,
+                               int32_t* __restrict__ item_row) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_light;
+       i += (int64_t)gridDim.x * blockDim.x)
+    if (flag[i]) item_row[id[i]] = static_cast<int32_t>(i);
+}
+
+__global__ void k_item_offsets(const int32_t* __restrict__ item_row, int64_t n_items, const int64_t* __restrict__ p_row_ptr,
+                               int64_t n_mid, int64_t* __restrict__ item_e) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c <= n_items;
+       c += (int64_t)gridDim.x * blockDim.x)
+    item_e[c] = p_row_ptr[n_mid + item_row[c]];
 }
 
 __global__ void k_low_word(const uint64_t* __restrict__ keys, int64_t nnz, int32_t* __restrict__ out) {
@@ -261,11 +288,17 @@ static int build_csr_impl(const int64_t* src_in, const int64_t* dst_in, int64_t 
   NDOS_CHECK(persistent_alloc(&G->s64, n));
   NDOS_CHECK(persistent_alloc(&G->s32, n));
   NDOS_CHECK(persistent_alloc(&G->old_id, n));
-  NDOS_CHECK(persistent_alloc(&G->p_row_ptr, n + 1));
-  NDOS_CHECK(persistent_alloc(&G->p_col, nnz));
+  // the hot-path arrays are padded: the step kernel's bulk copies round
+  // their ranges out to 16-byte boundaries
+  NDOS_CHECK(persistent_alloc(&G->p_row_ptr, n + 3));
+  NDOS_CHECK(persistent_alloc(&G->p_col, nnz + 4));
   NDOS_CHECK(persistent_alloc(&G->p_deg, n));
-  NDOS_CHECK(persistent_alloc(&G->p_orig, n));
-  NDOS_CHECK(persistent_alloc(&G->p_compact, n));
+  NDOS_CHECK(persistent_alloc(&G->p_orig, n + 4));
+  NDOS_CHECK(persistent_alloc(&G->p_compact, n + 4));
+  NDOS_CUDA(cudaMemsetAsync(G->p_row_ptr, 0, sizeof(int64_t) * (n + 3), s));
+  NDOS_CUDA(cudaMemsetAsync(G->p_col, 0, sizeof(int32_t) * (nnz + 4), s));
+  NDOS_CUDA(cudaMemsetAsync(G->p_orig, 0, sizeof(int32_t) * (n + 4), s));
+  NDOS_CUDA(cudaMemsetAsync(G->p_compact, 0, sizeof(int32_t) * (n + 4), s));
   NDOS_CHECK(persistent_alloc(&G->compact_to_p, n));
 
   int64_t* deg64 = nullptr;
@@ -282,9 +315,9 @@ static int build_csr_impl(const int64_t* src_in, const int64_t* dst_in, int64_t 
   }
 
   // ---- degree-sorted relabelling ----
-  unsigned long long* n_heavy_d = nullptr;
-  NDOS_CHECK(t.get(&n_heavy_d, 1));
-  NDOS_CUDA(cudaMemsetAsync(n_heavy_d, 0, sizeof(unsigned long long), s));
+  unsigned long long* n_heavy_d = nullptr;  // [0] deg >= kHeavyDeg, [1] deg >= kMediumDeg
+  NDOS_CHECK(t.get(&n_heavy_d, 2));
+  NDOS_CUDA(cudaMemsetAsync(n_heavy_d, 0, 2 * sizeof(unsigned long long), s));
   if (n > 0) {
     uint32_t *dk = nullptr, *dk_alt = nullptr;
     int32_t *idx = nullptr, *idx_alt = nullptr;
@@ -306,7 +339,8 @@ static int build_csr_impl(const int64_t* src_in, const int64_t* dst_in, int64_t 
     int64_t* pdeg64 = nullptr;
     NDOS_CHECK(t.get(&pdeg64, n));
     k_perm_nodes<<<grid_for(n), kThreads, 0, s>>>(G->p_compact, n, G->deg, G->old_id, G->compact_to_p, G->p_deg,
-                                                 pdeg64, G->p_orig, n_heavy_d, kHeavyDeg);
+                                                 pdeg64, G->p_orig, n_heavy_d, n_heavy_d + 1, kHeavyDeg,
+                                                 kMediumDeg);
     NDOS_LAUNCHED();
     NDOS_CHECK(exclusive_scan_i64(pdeg64, G->p_row_ptr, n, t));
   } else {
@@ -323,13 +357,47 @@ static int build_csr_impl(const int64_t* src_in, const int64_t* dst_in, int64_t 
     k_low_word<<<grid_for(nnz), kThreads, 0, s>>>(k2, nnz, G->p_col);
     NDOS_LAUNCHED();
   }
-  unsigned long long nh = 0;
-  NDOS_CUDA(cudaMemcpyAsync(&nh, n_heavy_d, sizeof(nh), cudaMemcpyDeviceToHost, s));
+  unsigned long long nh[2] = {0, 0};
+  NDOS_CUDA(cudaMemcpyAsync(nh, n_heavy_d, sizeof(nh), cudaMemcpyDeviceToHost, s));
   int32_t md = 0;
   if (n > 0) NDOS_CUDA(cudaMemcpyAsync(&md, G->p_deg, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   NDOS_CUDA(cudaStreamSynchronize(s));
-  G->n_heavy = static_cast<int64_t>(nh);
+  G->n_heavy = static_cast<int64_t>(nh[0]);
+  G->n_mid = static_cast<int64_t>(nh[1]);
+
+  // ---- warp items over the light rows ----
+  const int64_t n_light = n - G->n_mid;
+  int32_t *flag = nullptr, *id = nullptr;
+  NDOS_CHECK(t.get(&flag, n_light + 1));
+  NDOS_CHECK(t.get(&id, n_light + 1));
+  int32_t n_items = 0;
+  if (n_light > 0) {
+    k_item_flags<<<grid_for(n_light), kThreads, 0, s>>>(G->p_row_ptr, G->n_mid, n_light, flag);
+    NDOS_LAUNCHED();
+    NDOS_CUDA(cudaMemsetAsync(flag + n_light, 0, sizeof(int32_t), s));
+    size_t bytes = 0;
+    NDOS_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, bytes, flag, id, n_light + 1, s));
+    void* tmp = nullptr;
+    NDOS_CHECK(t.get(reinterpret_cast<char**>(&tmp), bytes));
+    NDOS_CUDA(cub::DeviceScan::ExclusiveSum(tmp, bytes, flag, id, n_light + 1, s));
+    count_launch();
+    NDOS_CUDA(cudaMemcpyAsync(&n_items, id + n_light, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    NDOS_CUDA(cudaStreamSynchronize(s));
+  }
+  NDOS_CHECK(persistent_alloc(&G->item_row, static_cast<size_t>(n_items) + 1));
+  if (n_light > 0) {
+    k_item_scatter<<<grid_for(n_light), kThreads, 0, s>>>(flag, id, n_light, G->item_row);
+    NDOS_LAUNCHED();
+  }
+  const int32_t end_row = static_cast<int32_t>(n_light);
+  NDOS_CUDA(cudaMemcpyAsync(G->item_row + n_items, &end_row, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  NDOS_CHECK(persistent_alloc(&G->item_e, static_cast<size_t>(n_items) + 1));
+  k_item_offsets<<<grid_for(n_items + 1), kThreads, 0, s>>>(G->item_row, n_items, G->p_row_ptr, G->n_mid, G->item_e);
+  NDOS_LAUNCHED();
+  NDOS_CUDA(cudaStreamSynchronize(s));
+  G->n_items = n_items;
   G->max_deg = md;
+
   return DOS_OK;
 }
 

@@ -114,6 +114,13 @@ struct Graph {
   int32_t* compact_to_p = nullptr; // [n]
   int32_t max_deg = 0;
   int64_t n_heavy = 0;          // positions [0, n_heavy) have deg >= kHeavyDeg
+  int64_t n_mid = 0;            // positions [n_heavy, n_mid) have kMediumDeg <= deg < kHeavyDeg
+  // light rows [n_mid, n) cut into warp items: item c = positions n_mid +
+  // [item_row[c], item_row[c+1]), at most kItemRows rows and fewer than
+  // kItemNnzStep + kMediumDeg nonzeros
+  int32_t* item_row = nullptr;  // [n_items+1]
+  int64_t* item_e = nullptr;    // [n_items+1] row offset of each item's first row
+  int64_t n_items = 0;
 };
 
 struct Filter {
@@ -127,6 +134,9 @@ struct Filter {
 };
 
 constexpr int kHeavyDeg = 2048;  // rows at or above this degree get a whole CTA
+constexpr int kMediumDeg = 64;   // rows at or above this degree (and below kHeavyDeg) get a warp
+constexpr int kItemRows = 64;     // light rows per warp item (at most)
+constexpr int kItemNnzStep = 256; // an item ends where a row offset enters a new multiple
 
 // ---------------------------------------------------------------------------
 // SplitMix64 (Steele, Lea, Flood, OOPSLA 2014): n-th output of the stream

@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "kpm_kernels.cuh"
 
@@ -52,8 +53,13 @@ __global__ void __launch_bounds__(256) k_reduce_partials(const double* __restric
 // DOS (doubled): raw[0] = <V0,V0>, step k: raw[1+2k] = <V_{k+1},V_{k+1}>,
 // raw[2+2k] = <V_{k+1},V_k>.  LDOS (direct): raw[m] = mu_m.
 __global__ void k_moments_from_raw(const double* __restrict__ raw, int M, int doubled, double norm,
-                                   double* __restrict__ d) {
+                                   const int* __restrict__ err, double* __restrict__ d) {
+  const bool failed = err && *err != 0;  // a bounded wait gave up: no valid moments
   for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) {
+    if (failed) {
+      d[m] = __longlong_as_double(0x7ff8000000000000ll);
+      continue;
+    }
     double mu;
     if (!doubled) {
       mu = raw[m];
@@ -80,23 +86,58 @@ __global__ void k_fill_f32(float* __restrict__ p, int64_t n, float v) {
 
 
 static int g_force_t = 0;  // 0 = planner's choice
-static int g_force_p = 0;
+static int g_force_ctas = 0;  // light-row CTAs per SM, 0 = as many as fit
 
 static int elem_size(int prec) { return prec == DOS_FP32 ? 4 : 2; }
 
-template <typename T>
-static int occupancy_for(const Plan& plan) {
-  return step_occupancy<T>(plan);
+// error word written by the step kernels' bounded waits (one per device)
+__device__ int g_step_err;
+static std::mutex g_err_mu;
+static int* g_err_addr[64] = {};
+
+int step_error_word(int** out) {
+  int dev = 0;
+  NDOS_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(DOS_EINVAL, "device ordinal out of range");
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  if (!g_err_addr[dev]) {
+    void* p = nullptr;
+    NDOS_CUDA(cudaGetSymbolAddress(&p, g_step_err));
+    g_err_addr[dev] = static_cast<int*>(p);
+  }
+  *out = g_err_addr[dev];
+  return DOS_OK;
 }
 
-static int occupancy(int prec, const Plan& plan) {
+// side streams and events of the step launches, one set per device
+static std::mutex g_side_mu;
+static SideStreams g_side[64];
+
+static int side_streams(SideStreams* out) {
+  int dev = 0;
+  NDOS_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(DOS_EINVAL, "device ordinal out of range");
+  std::lock_guard<std::mutex> lk(g_side_mu);
+  SideStreams& sd = g_side[dev];
+  if (!sd.a) {
+    NDOS_CUDA(cudaStreamCreateWithFlags(&sd.a, cudaStreamNonBlocking));
+    NDOS_CUDA(cudaStreamCreateWithFlags(&sd.b, cudaStreamNonBlocking));
+    NDOS_CUDA(cudaEventCreateWithFlags(&sd.fork, cudaEventDisableTiming));
+    NDOS_CUDA(cudaEventCreateWithFlags(&sd.join_a, cudaEventDisableTiming));
+    NDOS_CUDA(cudaEventCreateWithFlags(&sd.join_b, cudaEventDisableTiming));
+  }
+  *out = sd;
+  return DOS_OK;
+}
+
+static int light_config(int prec, int q, int mode, int* smem, int* ctas) {
   switch (prec) {
     case DOS_BF16:
-      return occupancy_for<__nv_bfloat16>(plan);
+      return step_config<__nv_bfloat16>(q, mode, smem, ctas);
     case DOS_FP16:
-      return occupancy_for<__half>(plan);
+      return step_config<__half>(q, mode, smem, ctas);
     default:
-      return occupancy_for<float>(plan);
+      return step_config<float>(q, mode, smem, ctas);
   }
 }
 
@@ -105,7 +146,7 @@ static int occupancy(int prec, const Plan& plan) {
 // in a share of L2 when possible; among the tilings that fit, the one with
 // the least modelled traffic per step (T re-reads of the CSR + three probe
 // blocks including padding) wins.
-int make_plan(const Graph* G, int Nz, int prec, Plan* out) {
+int make_plan(const Graph* G, int Nz, int prec, int mode, Plan* out) {
   const int es = elem_size(prec);
   const int V = 16 / es;
   const int qmax = prec == DOS_FP32 ? 16 : 8;
@@ -136,26 +177,21 @@ int make_plan(const Graph* G, int Nz, int prec, Plan* out) {
     }
   }
   if (!have) return fail(DOS_EINVAL, "no tile width matches the forced plan");
-  // neighbour slots per light row from the light rows' mean degree
-  const double light_rows = std::max(1.0, n - static_cast<double>(G->n_heavy));
-  const double avg = nnz / std::max(1.0, n) * (n / light_rows);
-  int p = 1;
-  while (p < 4 && pl.q * p * 2 <= 32 && avg >= 8.0 * p) p *= 2;
-  if (g_force_p) {
-    if (g_force_p != 1 && g_force_p != 2 && g_force_p != 4) return fail(DOS_EINVAL, "slots must be 1, 2 or 4");
-    if (pl.q * g_force_p > 32) return fail(DOS_EINVAL, "slots * lanes per row exceeds a warp");
-    p = g_force_p;
-  }
-  pl.p = p;
   const int sms = num_sms();
-  const int occ = occupancy(prec, pl);
+  int smem = 0, ctas = 0;
+  NDOS_CHECK(light_config(prec, pl.q, mode, &smem, &ctas));
+  pl.smem = smem;
+  // two resident CTAs per SM measured best: more shared memory per SM leaves
+  // less L1 to hold the gathers in flight
+  ctas = std::min(ctas, g_force_ctas > 0 ? g_force_ctas : 2);
+  const int64_t n_light = G->n - G->n_mid;
+  const int64_t rounds = (n_light + 32 / pl.q - 1) / (32 / pl.q) * pl.tiles;
+  pl.light_ctas = static_cast<int>(std::min<int64_t>(static_cast<int64_t>(std::max(1, ctas)) * sms,
+                                                     (rounds + kStepWarps - 1) / kStepWarps));
   pl.heavy_ctas = static_cast<int>(std::min<int64_t>(G->n_heavy, 4LL * sms));
-  const int64_t light_n = G->n - G->n_heavy;
-  const int64_t rows_per_cta = static_cast<int64_t>(kStepWarps) * (32 / (pl.q * pl.p));
-  int64_t light = (light_n + rows_per_cta - 1) / rows_per_cta;
-  light = std::min<int64_t>(light, static_cast<int64_t>(occ) * sms);
-  if (light < 1) light = 1;
-  pl.gx = pl.heavy_ctas + static_cast<int>(light);
+  const int64_t n_mid_rows = G->n_mid - G->n_heavy;
+  pl.mid_ctas = static_cast<int>(std::min<int64_t>((n_mid_rows + kStepWarps - 1) / kStepWarps, 4LL * sms));
+  pl.part_width = static_cast<int64_t>(pl.heavy_ctas + pl.mid_ctas) * pl.tiles + pl.light_ctas;
   *out = pl;
   return DOS_OK;
 }
@@ -167,7 +203,7 @@ static int run_steps(const Graph* G, const Filter* F, const Plan& plan, int M, i
   const int64_t n = G->n;
   const int steps = mode == kModeDos ? M / 2 : M - 1;
   const int n_dots = mode == kModeDos ? 2 : 1;
-  const int64_t width = static_cast<int64_t>(plan.tiles) * plan.gx;
+  const int64_t width = plan.part_width;
   const int64_t n_raw = 1 + static_cast<int64_t>(steps) * n_dots;
   const size_t elems = static_cast<size_t>(n) * plan.nz_pad;
 
@@ -230,17 +266,26 @@ static int run_steps(const Graph* G, const Filter* F, const Plan& plan, int M, i
   StepParams prm{};
   prm.row_ptr = G->p_row_ptr;
   prm.col = G->p_col;
-  prm.deg = G->p_deg;
   prm.orig = G->p_orig;
   prm.compact = G->p_compact;
   prm.n = n;
   prm.n_heavy = G->n_heavy;
-  prm.heavy_ctas = plan.heavy_ctas;
+  prm.n_mid = G->n_mid;
+  prm.item_row = G->item_row;
+  prm.item_e = G->item_e;
+  prm.n_items = G->n_items;
+  prm.tiles = plan.tiles;
+  prm.part_width = plan.part_width;
+  prm.mid_part_off = static_cast<int64_t>(plan.heavy_ctas) * plan.tiles;
+  prm.light_part_off = static_cast<int64_t>(plan.heavy_ctas + plan.mid_ctas) * plan.tiles;
+  if (st == DOS_OK) st = step_error_word(&prm.err);
   prm.nz = Nz;
   prm.inv_nz = 1.0f / static_cast<float>(Nz);
   prm.seed = seed;
   prm.ldos_atomic = plan.tiles > 1 ? 1 : 0;
   const bool prof = profiling_on();
+  SideStreams side;
+  if (st == DOS_OK) st = side_streams(&side);
   for (int k = 0; k < steps && st == DOS_OK; ++k) {
     prm.u_cur = (k & 1) ? ub : ua;
     prm.u_pn = (k & 1) ? ua : ub;
@@ -248,7 +293,7 @@ static int run_steps(const Graph* G, const Filter* F, const Plan& plan, int M, i
     prm.partial = partial + static_cast<size_t>(1 + static_cast<int64_t>(k) * n_dots) * width;
     prm.ldos = mode == kModeLdos ? C_out + static_cast<size_t>(k + 1) * n : nullptr;
     if (prof) profile_begin(s);
-    st = launch_step<T>(plan, mode, prm, s);
+    st = launch_step<T>(plan, mode, prm, s, side);
     if (prof) profile_end(s);
   }
   if (st == DOS_OK) {
@@ -258,7 +303,7 @@ static int run_steps(const Graph* G, const Filter* F, const Plan& plan, int M, i
   }
   if (st == DOS_OK && d_out) {
     const double r = F ? static_cast<double>(n - F->removed) : static_cast<double>(n);
-    k_moments_from_raw<<<1, 256, 0, s>>>(raw, M, mode == kModeDos ? 1 : 0, r * Nz, d_out);
+    k_moments_from_raw<<<1, 256, 0, s>>>(raw, M, mode == kModeDos ? 1 : 0, r * Nz, prm.err, d_out);
     count_launch();
     cu(cudaGetLastError(), "k_moments_from_raw");
   }
@@ -275,7 +320,7 @@ static int run_kpm(const Graph* G, const Filter* F, int M, int Nz, uint64_t seed
   if (prec != DOS_FP32 && prec != DOS_BF16 && prec != DOS_FP16) return fail(DOS_EINVAL, "unknown precision");
   if (F && F->g != G) return fail(DOS_EINVAL, "filter belongs to another graph");
   Plan plan;
-  NDOS_CHECK(make_plan(G, Nz, prec, &plan));
+  NDOS_CHECK(make_plan(G, Nz, prec, mode, &plan));
   switch (prec) {
     case DOS_BF16:
       return run_steps<__nv_bfloat16>(G, F, plan, M, Nz, seed, mode, d_out, C_out, s);
@@ -308,25 +353,36 @@ int ldos_moments(dos_graph_t g, int M, int Nz, uint64_t seed, int prec, float* C
                  static_cast<cudaStream_t>(stream));
 }
 
-int dos_set_plan(int tile_width, int slots) {
+int dos_set_plan(int tile_width, int ctas_per_sm) {
   if (tile_width != 0 && (tile_width < 4 || tile_width > 64 || (tile_width & (tile_width - 1))))
     return fail(DOS_EINVAL, "dos_set_plan: tile width must be 0 or a power of two in [4, 64]");
-  if (slots != 0 && slots != 1 && slots != 2 && slots != 4)
-    return fail(DOS_EINVAL, "dos_set_plan: slots must be 0, 1, 2 or 4");
+  if (ctas_per_sm < 0 || ctas_per_sm > 32) return fail(DOS_EINVAL, "dos_set_plan: ctas_per_sm must be in [0, 32]");
   g_force_t = tile_width;
-  g_force_p = slots;
+  g_force_ctas = ctas_per_sm;
   return DOS_OK;
 }
 
-int dos_get_plan(dos_graph_t g, int Nz, int prec, int* tile_width, int* slots, int* tiles, int* grid_x) {
+int dos_get_plan(dos_graph_t g, int Nz, int prec, int* tile_width, int* ctas_per_sm, int* tiles, int* grid_x) {
   Plan pl;
   if (!g) return fail(DOS_EINVAL, "dos_get_plan: null graph");
-  NDOS_CHECK(make_plan(reinterpret_cast<const Graph*>(g), Nz, prec, &pl));
+  NDOS_CHECK(make_plan(reinterpret_cast<const Graph*>(g), Nz, prec, kModeDos, &pl));
   if (tile_width) *tile_width = pl.t;
-  if (slots) *slots = pl.p;
+  if (ctas_per_sm) *ctas_per_sm = (pl.light_ctas + num_sms() - 1) / num_sms();
   if (tiles) *tiles = pl.tiles;
-  if (grid_x) *grid_x = pl.gx;
+  if (grid_x) *grid_x = pl.light_ctas;
   return DOS_OK;
+}
+
+int dos_device_status(void* stream, int* status) {
+  int* err = nullptr;
+  NDOS_CHECK(step_error_word(&err));
+  int h = 0;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  NDOS_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  NDOS_CUDA(cudaStreamSynchronize(s));
+  if (h != 0) NDOS_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+  if (status) *status = h;
+  return h == 0 ? DOS_OK : fail(DOS_ETIMEOUT, "a bounded device wait of the step kernel gave up");
 }
 
 }  // extern "C"

@@ -13,14 +13,15 @@
 // Block layout ("tile-major"): a block of Nz_pad = T * t probe columns over
 // n rows is stored as T tiles of n x t, row-major inside a tile:
 //     element (row p, probe j) at ((j / t) * n + p) * t + (j % t).
-// One launch processes every tile (blockIdx.y = tile) of one step, so the
-// rows gathered by concurrently running CTAs are one tile of U_k.
+// Work is ordered tile-major, so the rows gathered by concurrently running
+// CTAs come from one tile of U_k.
 //
-// Rows are in degree-sorted order (heavy rows first).  CTAs with
-// blockIdx.x < heavy_ctas own whole heavy rows (all 256 threads on one row);
-// the remaining CTAs give each light row a group of G = Q * P lanes: P
-// neighbour slots, each slot Q lanes that read one 16-byte chunk of the
-// neighbour's tile row (t = Q * VEC probes).
+// Rows are in degree-sorted order (heavy rows first).  Heavy rows get a CTA
+// each (k_cheb_heavy); light rows are processed by a persistent,
+// warp-specialised kernel that stages each chunk's contiguous data in shared
+// memory with TMA bulk copies (k_cheb_light).  A light row gets a group of
+// G = Q * P lanes: P neighbour slots, each slot Q lanes that read one 16-byte
+// chunk of the neighbour's tile row (t = Q * VEC probes).
 #pragma once
 
 #include <cuda_bf16.h>
@@ -117,60 +118,104 @@ __device__ __forceinline__ uint4 ld_stream(const uint4* p) { return __ldcs(p); }
 __device__ __forceinline__ void st_stream(uint4* p, const uint4& v) { __stcs(p, v); }
 __device__ __forceinline__ int32_t ld_col(const int32_t* p) { return __ldcs(p); }
 
+// ---- TMA bulk copies and mbarriers (inline PTX) ------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Every wait is bounded: after kWaitLimitNs the caller gets false and must
+// record the failure and leave.
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (global_ns() - t0 > kWaitLimitNs) return false;
+  return true;
+}
+// global -> shared bulk copy completing on `bar` (16-byte aligned, size % 16 == 0)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// device error word codes (dos_device_status)
+constexpr int kErrWaitTimeout = 1;
+
 struct StepParams {
-  const int64_t* __restrict__ row_ptr;   // [n+1] degree-sorted CSR
-  const int32_t* __restrict__ col;       // [nnz] neighbour positions
-  const int32_t* __restrict__ deg;       // [n]
-  const int32_t* __restrict__ orig;      // [n] original ids (LDOS probe signs)
-  const int32_t* __restrict__ compact;   // [n] compact ids (LDOS output column)
+  const int64_t* __restrict__ row_ptr;   // [n+1] degree-sorted CSR (allocation padded to n+3)
+  const int32_t* __restrict__ col;       // [nnz] neighbour positions (padded to nnz+4)
+  const int32_t* __restrict__ orig;      // [n] original ids (padded to n+4)
+  const int32_t* __restrict__ compact;   // [n] compact ids (padded to n+4)
   const void* u_cur;                     // U_k
   void* u_pn;                            // U_{k-1} in, U_{k+1} out (in place)
   int64_t n;
-  int64_t n_heavy;
-  int heavy_ctas;
+  int64_t n_heavy;  // rows [0, n_heavy): k_cheb_heavy
+  int64_t n_mid;    // rows [n_heavy, n_mid): k_cheb_medium; [n_mid, n): k_cheb_light
+  const int32_t* __restrict__ item_row;  // [n_items+1] light warp items (rows relative to n_mid)
+  const int64_t* __restrict__ item_e;    // [n_items+1] row offset of each item's first row
+  int64_t n_items;
+  int tiles;
   int first;        // 1: U_1 = S^2 A U_0 (no U_{k-1} term)
   int nz;           // real probe count (columns >= nz are zero padding)
   float inv_nz;
   uint64_t seed;
-  double* partial;  // this step's partials: [n_dots][T][gridDim.x]
+  double* partial;  // this step's partials: [n_dots][part_width]
+  int64_t part_width;
+  int64_t mid_part_off;    // medium CTAs write partial[mid_part_off + tile * grid + blockIdx.x]
+  int64_t light_part_off;  // light CTAs write partial[light_part_off + blockIdx.x]
   float* ldos;      // LDOS: C_out + m * n_compact, indexed by compact id
   int ldos_atomic;  // 1 when several tiles add into the same C entry
+  int* err;         // device error word
 };
 
 // Epilogue of one row: recurrence update, store, fused dots / LDOS.
-// Executed by all 32 lanes of a warp; `active` lanes own a row whose
-// neighbour sum is in acc (ql = which 16-byte chunk of the tile row).
+// Executed by all 32 lanes of a warp (the Q-lane reductions are warp
+// shuffles); `active` lanes own a row whose neighbour sum is in acc.
 template <typename T, int Q, int MODE>
 __device__ __forceinline__ void step_epilogue(const StepParams& prm, bool active, int64_t p, int ql, int tile,
-                                              const float* acc, bool owner, double& dd0, double& dd1) {
+                                              const float* acc, const float* prev, const float* own, float fd,
+                                              uint32_t orig, int32_t compact, bool owner, double& dd0,
+                                              double& dd1) {
   constexpr int V = VecT<T>::N;
-  constexpr int TW = Q * V;  // tile width t
+  constexpr int TW = Q * V;
   float prod0 = 0.f, prod1 = 0.f;
-  float fd = 1.f;
   if (active) {
-    const int d = prm.deg[p];
-    fd = static_cast<float>(d);
     const size_t off = (static_cast<size_t>(tile) * prm.n + p) * TW + ql * V;
     uint4* pn = reinterpret_cast<uint4*>(reinterpret_cast<T*>(prm.u_pn) + off);
     float u[V];
-    if (prm.first) {
-      const float sc = 1.0f / fd;
+    const float sc = (prm.first ? 1.0f : 2.0f) / fd;
 #pragma unroll
-      for (int v = 0; v < V; ++v) u[v] = acc[v] * sc;
-    } else {
-      const float sc = 2.0f / fd;
-      float prev[V];
-      unpack16<T>(ld_stream(pn), prev);
-#pragma unroll
-      for (int v = 0; v < V; ++v) u[v] = fmaf(acc[v], sc, -prev[v]);
-    }
+    for (int v = 0; v < V; ++v) u[v] = fmaf(acc[v], sc, -prev[v]);
     const uint4 packed = pack16<T>(u);
     st_stream(pn, packed);
     unpack16<T>(packed, u);  // the dots use the stored (rounded) values
     if (MODE == kModeDos) {
-      float own[V];
-      const uint4* cur = reinterpret_cast<const uint4*>(reinterpret_cast<const T*>(prm.u_cur) + off);
-      unpack16<T>(ld_gather(cur), own);  // own row of U_k: also gathered by neighbours
 #pragma unroll
       for (int v = 0; v < V; ++v) {
         prod0 = fmaf(u[v], u[v], prod0);
@@ -178,7 +223,7 @@ __device__ __forceinline__ void step_epilogue(const StepParams& prm, bool active
       }
     } else {
       const int j0 = tile * TW + ql * V;
-      const uint64_t word = probe_word(prm.seed, static_cast<uint32_t>(prm.orig[p]), static_cast<uint32_t>(j0 >> 6));
+      const uint64_t word = probe_word(prm.seed, orig, static_cast<uint32_t>(j0 >> 6));
 #pragma unroll
       for (int v = 0; v < V; ++v) {
         const int j = j0 + v;
@@ -188,9 +233,9 @@ __device__ __forceinline__ void step_epilogue(const StepParams& prm, bool active
   }
   // reduce over the Q lanes that share a row
 #pragma unroll
-  for (int o = 1; o < Q; o <<= 1) {
-    prod0 += __shfl_xor_sync(0xffffffffu, prod0, o);
-    if (MODE == kModeDos) prod1 += __shfl_xor_sync(0xffffffffu, prod1, o);
+  for (int s = 1; s < Q; s <<= 1) {
+    prod0 += __shfl_xor_sync(0xffffffffu, prod0, s);
+    if (MODE == kModeDos) prod1 += __shfl_xor_sync(0xffffffffu, prod1, s);
   }
   if (active && owner) {
     if (MODE == kModeDos) {
@@ -199,7 +244,7 @@ __device__ __forceinline__ void step_epilogue(const StepParams& prm, bool active
     } else {
       const float vsum = prod0 * sqrtf(fd);  // sum_j z_j (V_{k+1})_j of this tile
       dd0 += static_cast<double>(vsum);
-      float* dst = prm.ldos + prm.compact[p];
+      float* dst = prm.ldos + compact;
       if (prm.ldos_atomic)
         atomicAdd(dst, vsum * prm.inv_nz);
       else
@@ -208,46 +253,38 @@ __device__ __forceinline__ void step_epilogue(const StepParams& prm, bool active
   }
 }
 
+constexpr int kGatherBatch = 8;  // independent row gathers in flight per lane
 
-// acc[0..V) += sum of the 16-byte chunk `ql` of U_k rows col[e], e = beg + slot,
-// beg + slot + STRIDE, ... < end
+// acc += chunk `ql` of U_k rows idx[s + STRIDE*u], u = 0, 1, ..., over the
+// staged indices idx[0..cnt).  Loads are issued in batches of kGatherBatch
+// independent requests; the early exit is warp-uniform.
 template <typename T, int Q, int STRIDE>
-__device__ __forceinline__ void gather_sum(const StepParams& prm, int64_t beg, int64_t end, int slot, int ql,
-                                           int tile, float* acc) {
+__device__ __forceinline__ void gather_list(const uint4* __restrict__ ubase, const int32_t* idx, int cnt, int s,
+                                            int ql, float* acc) {
   constexpr int V = VecT<T>::N;
-  const uint4* base = reinterpret_cast<const uint4*>(prm.u_cur) + static_cast<size_t>(tile) * prm.n * Q + ql;
-  int64_t e = beg + slot;
-  for (; e + 3 * STRIDE < end; e += 4 * STRIDE) {
-    const int32_t j0 = ld_col(prm.col + e);
-    const int32_t j1 = ld_col(prm.col + e + STRIDE);
-    const int32_t j2 = ld_col(prm.col + e + 2 * STRIDE);
-    const int32_t j3 = ld_col(prm.col + e + 3 * STRIDE);
-    const uint4 r0 = ld_gather(base + static_cast<size_t>(j0) * Q);
-    const uint4 r1 = ld_gather(base + static_cast<size_t>(j1) * Q);
-    const uint4 r2 = ld_gather(base + static_cast<size_t>(j2) * Q);
-    const uint4 r3 = ld_gather(base + static_cast<size_t>(j3) * Q);
-    float a[V], b[V];
-    unpack16<T>(r0, a);
-    unpack16<T>(r1, b);
+#pragma unroll 1
+  for (int u0 = 0;; u0 += kGatherBatch) {
+    if (!__any_sync(0xffffffffu, s + STRIDE * u0 < cnt)) break;
+    uint4 r[kGatherBatch];
 #pragma unroll
-    for (int v = 0; v < V; ++v) acc[v] += a[v] + b[v];
-    unpack16<T>(r2, a);
-    unpack16<T>(r3, b);
+    for (int v = 0; v < kGatherBatch; ++v) {
+      const int j = s + STRIDE * (u0 + v);
+      r[v] = j < cnt ? ld_gather(ubase + static_cast<size_t>(idx[j]) * Q + ql) : make_uint4(0u, 0u, 0u, 0u);
+    }
 #pragma unroll
-    for (int v = 0; v < V; ++v) acc[v] += a[v] + b[v];
-  }
-  for (; e < end; e += STRIDE) {
-    const int32_t j0 = ld_col(prm.col + e);
-    float a[V];
-    unpack16<T>(ld_gather(base + static_cast<size_t>(j0) * Q), a);
+    for (int v = 0; v < kGatherBatch; ++v) {
+      float a[V];
+      unpack16<T>(r[v], a);
 #pragma unroll
-    for (int v = 0; v < V; ++v) acc[v] += a[v];
+      for (int w = 0; w < V; ++w) acc[w] += a[w];
+    }
   }
 }
 
-// CTA-wide deterministic sum of two doubles; thread 0 gets the result
+// CTA-wide deterministic sum of two doubles over NW warps; thread 0 gets it
+template <int NW>
 __device__ __forceinline__ void block_sum2(double& a, double& b) {
-  __shared__ double sa[kStepWarps], sb[kStepWarps];
+  __shared__ double sa[NW], sb[NW];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     a += __shfl_xor_sync(0xffffffffu, a, o);
@@ -262,7 +299,7 @@ __device__ __forceinline__ void block_sum2(double& a, double& b) {
   __syncthreads();
   if (threadIdx.x == 0) {
     double x = 0.0, y = 0.0;
-    for (int w = 0; w < kStepWarps; ++w) {
+    for (int w = 0; w < NW; ++w) {
       x += sa[w];
       y += sb[w];
     }
@@ -271,75 +308,348 @@ __device__ __forceinline__ void block_sum2(double& a, double& b) {
   }
 }
 
-// One Chebyshev step over every tile: U_{k+1} = (2/d) A U_k - U_{k-1}, fused
-// with the moment dots (DOS: <V_{k+1},V_{k+1}> and <V_{k+1},V_k>; LDOS:
-// z o V_{k+1} per node and its sum).
-template <typename T, int Q, int P, int MODE>
-__global__ void __launch_bounds__(kStepThreads) k_cheb_step(const StepParams prm) {
+// ---------------------------------------------------------------------------
+// Heavy rows (degree >= kHeavyDeg, a prefix of the degree-sorted order): a
+// CTA per row, kStepThreads / Q neighbour slots, column indices staged in
+// shared memory 2048 at a time.  Grid (heavy_ctas, T).
+// ---------------------------------------------------------------------------
+constexpr int kHeavyColsPerThread = 8;
+
+template <typename T, int Q, int MODE>
+__global__ void __launch_bounds__(kStepThreads) k_cheb_heavy(const StepParams prm) {
   constexpr int V = VecT<T>::N;
+  constexpr int TW = Q * V;
+  constexpr int PH = kStepThreads / Q;
+  constexpr int BLK = kStepThreads * kHeavyColsPerThread;
+  __shared__ int32_t s_col[BLK];
+  __shared__ float red[kStepWarps][TW];
   const int tile = blockIdx.y;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int slot = tid / Q, ql = tid % Q;
+  const uint4* ubase = reinterpret_cast<const uint4*>(prm.u_cur) + static_cast<size_t>(tile) * prm.n * Q;
   double dd0 = 0.0, dd1 = 0.0;
-  if (static_cast<int>(blockIdx.x) < prm.heavy_ctas) {
-    // ---- heavy rows: a CTA per row ----
-    constexpr int PH = kStepThreads / Q;
-    __shared__ float red[kStepWarps][Q * V];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int slot = tid / Q, ql = tid % Q;
-    for (int64_t p = blockIdx.x; p < prm.n_heavy; p += prm.heavy_ctas) {
-      float acc[V];
+  for (int64_t p = blockIdx.x; p < prm.n_heavy; p += gridDim.x) {
+    const int64_t beg = prm.row_ptr[p], end = prm.row_ptr[p + 1];
+    // epilogue operands, loaded early by warp 0
+    const int qv = lane % Q;
+    const size_t off = (static_cast<size_t>(tile) * prm.n + p) * TW + qv * V;
+    float prev[V], own[V];
 #pragma unroll
-      for (int v = 0; v < V; ++v) acc[v] = 0.f;
-      gather_sum<T, Q, PH>(prm, prm.row_ptr[p], prm.row_ptr[p + 1], slot, ql, tile, acc);
+    for (int v = 0; v < V; ++v) prev[v] = own[v] = 0.f;
+    uint32_t orig = 0;
+    int32_t compact = 0;
+    if (warp == 0) {
+      if (!prm.first)
+        unpack16<T>(ld_stream(reinterpret_cast<const uint4*>(reinterpret_cast<const T*>(prm.u_pn) + off)), prev);
+      if (MODE == kModeDos)
+        unpack16<T>(ld_gather(reinterpret_cast<const uint4*>(reinterpret_cast<const T*>(prm.u_cur) + off)), own);
+      else {
+        orig = static_cast<uint32_t>(prm.orig[p]);
+        compact = prm.compact[p];
+      }
+    }
+    float acc[V];
 #pragma unroll
-      for (int o = Q; o < 32; o <<= 1)
-#pragma unroll
-        for (int v = 0; v < V; ++v) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], o);
-      if (lane < Q)
-#pragma unroll
-        for (int v = 0; v < V; ++v) red[warp][lane * V + v] = acc[v];
+    for (int v = 0; v < V; ++v) acc[v] = 0.f;
+    for (int64_t e0 = beg; e0 < end; e0 += BLK) {
       __syncthreads();
-      if (warp == 0) {
-        const int qv = lane % Q;
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
-          float s = 0.f;
-#pragma unroll
-          for (int w = 0; w < kStepWarps; ++w) s += red[w][qv * V + v];
-          acc[v] = s;
-        }
-        step_epilogue<T, Q, MODE>(prm, true, p, qv, tile, acc, lane == 0, dd0, dd1);
+      for (int i = 0; i < kHeavyColsPerThread; ++i) {
+        const int64_t e = e0 + tid + kStepThreads * i;
+        s_col[tid + kStepThreads * i] = e < end ? ld_col(prm.col + e) : 0;
       }
       __syncthreads();
+      const int cnt = static_cast<int>(end - e0 < BLK ? end - e0 : BLK);
+      gather_list<T, Q, PH>(ubase, s_col, cnt, slot, ql, acc);
     }
-  } else {
-    // ---- light rows: G = Q * P lanes per row ----
-    constexpr int G = Q * P;
-    constexpr int RPW = 32 / G;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int grp = lane / G, lig = lane % G, slot = lig / Q, ql = lig % Q;
-    const int64_t light_n = prm.n - prm.n_heavy;
-    const int64_t w_id = static_cast<int64_t>(blockIdx.x - prm.heavy_ctas) * kStepWarps + warp;
-    const int64_t n_w = static_cast<int64_t>(gridDim.x - prm.heavy_ctas) * kStepWarps;
-    for (int64_t base = w_id * RPW; base < light_n; base += n_w * RPW) {
-      const bool active = base + grp < light_n;
-      const int64_t p = prm.n_heavy + base + grp;
-      float acc[V];
 #pragma unroll
-      for (int v = 0; v < V; ++v) acc[v] = 0.f;
-      if (active) gather_sum<T, Q, P>(prm, prm.row_ptr[p], prm.row_ptr[p + 1], slot, ql, tile, acc);
+    for (int o = Q; o < 32; o <<= 1)
 #pragma unroll
-      for (int o = Q; o < G; o <<= 1)
+      for (int v = 0; v < V; ++v) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], o);
+    if (lane < Q)
 #pragma unroll
-        for (int v = 0; v < V; ++v) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], o);
-      step_epilogue<T, Q, MODE>(prm, active, p, ql, tile, acc, slot == 0 && ql == 0, dd0, dd1);
+      for (int v = 0; v < V; ++v) red[warp][lane * V + v] = acc[v];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        float sum = 0.f;
+#pragma unroll
+        for (int w = 0; w < kStepWarps; ++w) sum += red[w][qv * V + v];
+        acc[v] = sum;
+      }
+      step_epilogue<T, Q, MODE>(prm, true, p, qv, tile, acc, prev, own, static_cast<float>(end - beg), orig, compact,
+                                lane == 0, dd0, dd1);
     }
+    __syncthreads();
   }
-  block_sum2(dd0, dd1);
+  block_sum2<kStepWarps>(dd0, dd1);
   if (threadIdx.x == 0) {
-    const size_t w = static_cast<size_t>(gridDim.y) * gridDim.x;
     const size_t i = static_cast<size_t>(tile) * gridDim.x + blockIdx.x;
     prm.partial[i] = dd0;
-    if (MODE == kModeDos) prm.partial[w + i] = dd1;
+    if (MODE == kModeDos) prm.partial[prm.part_width + i] = dd1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Medium rows (kMediumDeg <= degree < kHeavyDeg): a warp per row, 32/Q
+// neighbour slots; each block of 256 column indices is staged in the warp's
+// shared memory with coalesced loads before its gathers.  Grid (ctas, T).
+// ---------------------------------------------------------------------------
+constexpr int kMediumCols = 256;  // staged indices per warp per block
+
+template <typename T, int Q, int MODE>
+__global__ void __launch_bounds__(kStepThreads) k_cheb_medium(const StepParams prm) {
+  constexpr int V = VecT<T>::N;
+  constexpr int TW = Q * V;
+  constexpr int PS = 32 / Q;  // neighbour slots per row
+  __shared__ int32_t s_col[kStepWarps][kMediumCols];
+  const int tile = blockIdx.y;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int slot = lane / Q, ql = lane % Q;
+  const uint4* ubase = reinterpret_cast<const uint4*>(prm.u_cur) + static_cast<size_t>(tile) * prm.n * Q;
+  double dd0 = 0.0, dd1 = 0.0;
+  const int64_t w0 = static_cast<int64_t>(blockIdx.x) * kStepWarps + warp;
+  const int64_t nw = static_cast<int64_t>(gridDim.x) * kStepWarps;
+  for (int64_t p = prm.n_heavy + w0; p < prm.n_mid; p += nw) {
+    const int64_t beg = prm.row_ptr[p], end = prm.row_ptr[p + 1];
+    const size_t off = (static_cast<size_t>(tile) * prm.n + p) * TW + ql * V;
+    float prev[V], own[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) prev[v] = own[v] = 0.f;
+    uint32_t orig = 0;
+    int32_t compact = 0;
+    if (!prm.first) unpack16<T>(ld_stream(reinterpret_cast<const uint4*>(reinterpret_cast<const T*>(prm.u_pn) + off)), prev);
+    if (MODE == kModeDos)
+      unpack16<T>(ld_gather(reinterpret_cast<const uint4*>(reinterpret_cast<const T*>(prm.u_cur) + off)), own);
+    else {
+      orig = static_cast<uint32_t>(prm.orig[p]);
+      compact = prm.compact[p];
+    }
+    float acc[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[v] = 0.f;
+    for (int64_t e0 = beg; e0 < end; e0 += kMediumCols) {
+#pragma unroll
+      for (int i = 0; i < kMediumCols / 32; ++i) {
+        const int64_t e = e0 + lane + 32 * i;
+        s_col[warp][lane + 32 * i] = e < end ? ld_col(prm.col + e) : 0;
+      }
+      __syncwarp();
+      const int cnt = static_cast<int>(end - e0 < kMediumCols ? end - e0 : kMediumCols);
+      gather_list<T, Q, PS>(ubase, s_col[warp], cnt, slot, ql, acc);
+      __syncwarp();
+    }
+#pragma unroll
+    for (int o = Q; o < 32; o <<= 1)
+#pragma unroll
+      for (int v = 0; v < V; ++v) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], o);
+    step_epilogue<T, Q, MODE>(prm, true, p, ql, tile, acc, prev, own, static_cast<float>(end - beg), orig, compact,
+                              lane == 0, dd0, dd1);
+  }
+  block_sum2<kStepWarps>(dd0, dd1);
+  if (threadIdx.x == 0) {
+    const size_t i = static_cast<size_t>(prm.mid_part_off) + static_cast<size_t>(tile) * gridDim.x + blockIdx.x;
+    prm.partial[i] = dd0;
+    if (MODE == kModeDos) prm.partial[prm.part_width + i] = dd1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Light rows (degree < kMediumDeg), the bulk of a sparse graph: every warp
+// runs its own two-slot TMA pipeline over "rounds" of R = 32/Q consecutive
+// rows (a group of Q lanes per row, one 16-byte chunk of the tile row each).
+// Work items (tile, round) are dealt to warps round-robin in tile-major
+// order.  While the warp gathers for item i, lane 0 has already issued the
+// bulk copies of item i+1 into the other slot: the row offsets, the column
+// indices, the U_{k-1} rows and the own U_k rows (DOS) or the original /
+// compact ids (LDOS), completing on the slot's mbarrier.  The row offsets of
+// item i+2 are loaded one iteration ahead, so no global load of the CSR or of
+// the streamed blocks is on the warp's critical path: only the gathers of
+// U_k rows are.
+// ---------------------------------------------------------------------------
+template <int Q, int ROWB, int MODE>
+struct RoundLayout {
+  static constexpr int R = 32 / Q;                                // rows per round
+  static constexpr int RP = (((R + 4) * 8) + 15) / 16 * 16;      // row offsets (rounded out to 16 B)
+  static constexpr int COL = ((R * (kMediumDeg - 1) + 8) * 4 + 15) / 16 * 16;
+  static constexpr int BLK = R * ROWB;
+  static constexpr int IDS = ((R + 8) * 4 + 15) / 16 * 16;
+  static constexpr int off_rp = 0;
+  static constexpr int off_col = off_rp + RP;
+  static constexpr int off_prev = off_col + COL;
+  static constexpr int off_aux = off_prev + BLK;
+  static constexpr int SLOT = off_aux + (MODE == kModeDos ? BLK : 2 * IDS);
+  static constexpr int WARP = 2 * SLOT;  // two slots per warp
+};
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+template <typename T, int Q, int MODE>
+__global__ void __launch_bounds__(kStepThreads, 3) k_cheb_light(const StepParams prm) {
+  constexpr int V = VecT<T>::N;
+  constexpr int TW = Q * V;
+  constexpr int ROWB = TW * static_cast<int>(sizeof(T));
+  using L = RoundLayout<Q, ROWB, MODE>;
+  constexpr int R = L::R;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ uint64_t bars[kStepWarps][2];
+  unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int grp = lane / Q, ql = lane % Q;
+  unsigned char* wbuf = smem + warp * L::WARP;
+  uint64_t* bar = bars[warp];
+  if (lane == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_fence_init();
+  }
+  __syncwarp();
+  const int64_t light0 = prm.n_mid;
+  const int64_t n_light = prm.n - light0;
+  const int64_t n_rounds = (n_light + R - 1) / R;
+  const int64_t wid = static_cast<int64_t>(blockIdx.x) * kStepWarps + warp;
+  const int64_t nwarps = static_cast<int64_t>(gridDim.x) * kStepWarps;
+  double dd0 = 0.0, dd1 = 0.0;
+
+  // (tile, round) cursor advanced without divisions
+  struct Cursor {
+    int64_t round;
+    int tile;
+  };
+  auto advance = [&](Cursor& c) {
+    c.round += nwarps;
+    while (c.round >= n_rounds) {
+      c.round -= n_rounds;
+      ++c.tile;
+    }
+  };
+  auto rows_of = [&](const Cursor& c, int64_t& r0, int64_t& r1) {
+    r0 = light0 + c.round * R;
+    r1 = r0 + R < prm.n ? r0 + R : prm.n;
+  };
+  // lane 0: issue the bulk copies of an item into slot s (e0, e1 = its CSR range)
+  auto issue = [&](const Cursor& c, int s, int64_t e0, int64_t e1) {
+    int64_t r0, r1;
+    rows_of(c, r0, r1);
+    unsigned char* sl = wbuf + s * L::SLOT;
+    const int64_t r0a = r0 & ~int64_t(1), ea = e0 & ~int64_t(3), r0i = r0 & ~int64_t(3);
+    const uint32_t rp_bytes = static_cast<uint32_t>(((r1 + 2 - r0a) & ~int64_t(1)) * 8);
+    const uint32_t col_bytes = static_cast<uint32_t>((((e1 + 3) & ~int64_t(3)) - ea) * 4);
+    const uint32_t blk_bytes = static_cast<uint32_t>((r1 - r0) * ROWB);
+    const uint32_t id_bytes = static_cast<uint32_t>((((r1 + 3) & ~int64_t(3)) - r0i) * 4);
+    uint32_t tx = rp_bytes + col_bytes + (prm.first ? 0u : blk_bytes) + (MODE == kModeDos ? blk_bytes : 2 * id_bytes);
+    mbar_arrive_expect_tx(&bar[s], tx);
+    const size_t row_off = (static_cast<size_t>(c.tile) * prm.n + r0) * TW;
+    bulk_g2s(sl + L::off_rp, prm.row_ptr + r0a, rp_bytes, &bar[s]);
+    bulk_g2s(sl + L::off_col, prm.col + ea, col_bytes, &bar[s]);
+    if (!prm.first) bulk_g2s(sl + L::off_prev, reinterpret_cast<const T*>(prm.u_pn) + row_off, blk_bytes, &bar[s]);
+    if (MODE == kModeDos) {
+      bulk_g2s(sl + L::off_aux, reinterpret_cast<const T*>(prm.u_cur) + row_off, blk_bytes, &bar[s]);
+    } else {
+      bulk_g2s(sl + L::off_aux, prm.orig + r0i, id_bytes, &bar[s]);
+      bulk_g2s(sl + L::off_aux + L::IDS, prm.compact + r0i, id_bytes, &bar[s]);
+    }
+  };
+
+  // cur = this iteration's item, nx1 = the next, nx2 = the one after
+  Cursor cur{wid, 0};
+  if (n_rounds == 0) cur.tile = prm.tiles;
+  while (cur.tile < prm.tiles && cur.round >= n_rounds) {
+    cur.round -= n_rounds;
+    ++cur.tile;
+  }
+  Cursor nx1 = cur;
+  if (n_rounds > 0) advance(nx1);
+  Cursor nx2 = nx1;
+  if (n_rounds > 0) advance(nx2);
+  int64_t nb0 = 0, nb1 = 0;  // lane 0: CSR range of nx1
+  int64_t nn0 = 0, nn1 = 0;  // lane 0: CSR range of nx2
+  if (lane == 0 && cur.tile < prm.tiles) {
+    int64_t r0, r1;
+    rows_of(cur, r0, r1);
+    issue(cur, 0, prm.row_ptr[r0], prm.row_ptr[r1]);
+    if (nx1.tile < prm.tiles) {
+      rows_of(nx1, r0, r1);
+      nb0 = prm.row_ptr[r0];
+      nb1 = prm.row_ptr[r1];
+    }
+  }
+  for (int it = 0; cur.tile < prm.tiles; ++it) {
+    const int s = it & 1;
+    // issue nx1 (range loaded one iteration ago), load the range of nx2
+    if (lane == 0 && nx1.tile < prm.tiles) {
+      fence_proxy_async_smem();
+      issue(nx1, s ^ 1, nb0, nb1);
+      if (nx2.tile < prm.tiles) {
+        int64_t r0, r1;
+        rows_of(nx2, r0, r1);
+        nn0 = prm.row_ptr[r0];
+        nn1 = prm.row_ptr[r1];
+      }
+    }
+    // wait for this item's slot (bounded; lane 0 decides for the warp)
+    int ok = 1;
+    if (lane == 0) ok = mbar_wait(&bar[s], static_cast<uint32_t>((it >> 1) & 1)) ? 1 : 0;
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (!ok) {
+      if (lane == 0) {
+        atomicExch(prm.err, kErrWaitTimeout);
+        // leave only after the copies issued for the next item have landed
+        if (nx1.tile < prm.tiles) mbar_wait(&bar[s ^ 1], static_cast<uint32_t>(((it + 1) >> 1) & 1));
+      }
+      break;
+    }
+    const int tile = cur.tile;
+    int64_t r0, r1;
+    rows_of(cur, r0, r1);
+    const unsigned char* sl = wbuf + s * L::SLOT;
+    const int64_t r0a = r0 & ~int64_t(1), r0i = r0 & ~int64_t(3);
+    const int64_t* rp = reinterpret_cast<const int64_t*>(sl + L::off_rp) + (r0 - r0a);
+    const int64_t ea = rp[0] & ~int64_t(3);
+    const int32_t* cidx = reinterpret_cast<const int32_t*>(sl + L::off_col);
+    const uint4* ubase = reinterpret_cast<const uint4*>(prm.u_cur) + static_cast<size_t>(tile) * prm.n * Q;
+    const bool active = r0 + grp < r1;
+    int64_t beg = 0, end = 0;
+    float prev[V], own[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) prev[v] = own[v] = 0.f;
+    uint32_t orig = 0;
+    int32_t compact = 0;
+    if (active) {
+      beg = rp[grp];
+      end = rp[grp + 1];
+      if (!prm.first) unpack16<T>(*reinterpret_cast<const uint4*>(sl + L::off_prev + grp * ROWB + ql * 16), prev);
+      if (MODE == kModeDos) {
+        unpack16<T>(*reinterpret_cast<const uint4*>(sl + L::off_aux + grp * ROWB + ql * 16), own);
+      } else {
+        orig = static_cast<uint32_t>(reinterpret_cast<const int32_t*>(sl + L::off_aux)[r0 + grp - r0i]);
+        compact = reinterpret_cast<const int32_t*>(sl + L::off_aux + L::IDS)[r0 + grp - r0i];
+      }
+    }
+    float acc[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[v] = 0.f;
+    gather_list<T, Q, 1>(ubase, cidx + (beg - ea), static_cast<int>(end - beg), 0, ql, acc);
+    step_epilogue<T, Q, MODE>(prm, active, r0 + grp, ql, tile, acc, prev, own, static_cast<float>(end - beg), orig,
+                              compact, ql == 0, dd0, dd1);
+    __syncwarp();  // the slot is read; it is refilled next iteration
+    cur = nx1;
+    nx1 = nx2;
+    if (n_rounds > 0) advance(nx2);
+    if (lane == 0) {
+      nb0 = nn0;
+      nb1 = nn1;
+    }
+  }
+  // the loop consumed every item it issued; nothing is left in flight
+  block_sum2<kStepWarps>(dd0, dd1);
+  if (threadIdx.x == 0) {
+    const size_t i = static_cast<size_t>(prm.light_part_off) + blockIdx.x;
+    prm.partial[i] = dd0;
+    if (MODE == kModeDos) prm.partial[prm.part_width + i] = dd1;
   }
 }
 
@@ -397,67 +707,115 @@ __global__ void __launch_bounds__(256) k_init_block(const InitParams prm) {
     const size_t off = (static_cast<size_t>(tile) * prm.n + p) * prm.t + (j0 % prm.t);
     *reinterpret_cast<uint4*>(reinterpret_cast<T*>(prm.u0) + off) = pack16<T>(u);
   }
-  block_sum2(acc, dummy);
+  block_sum2<8>(acc, dummy);
   if (threadIdx.x == 0) prm.partial[blockIdx.x] = acc;
 }
 
 // ---- launch entry points (instantiated per storage type) -------------------
 struct Plan {
-  int t = 16;      // tile width (probes per tile)
-  int q = 4;       // lanes per 16-byte-chunked tile row
-  int p = 2;       // neighbour slots per light row
-  int tiles = 1;   // T
+  int t = 16;       // tile width (probes per tile)
+  int q = 4;        // 16-byte chunks per tile row
+  int tiles = 1;    // T
   int nz_pad = 16;
-  int gx = 1;      // grid.x of a step (heavy + light CTAs)
   int heavy_ctas = 0;
+  int mid_ctas = 0;
+  int light_ctas = 0;
+  int smem = 0;     // dynamic shared memory of the light kernel
+  int64_t part_width = 1;  // partial slots per dot
 };
 
-template <typename T, int Q, int P>
-int launch_step_qp(const Plan& plan, int mode, const StepParams& prm, cudaStream_t s) {
-  const dim3 grid(plan.gx, plan.tiles);
-  if (mode == kModeDos)
-    k_cheb_step<T, Q, P, kModeDos><<<grid, kStepThreads, 0, s>>>(prm);
-  else
-    k_cheb_step<T, Q, P, kModeLdos><<<grid, kStepThreads, 0, s>>>(prm);
-  NDOS_LAUNCHED();
+template <typename T, int Q, int MODE>
+int light_smem() {
+  return kStepWarps * RoundLayout<Q, Q * 16, MODE>::WARP + 128;
+}
+
+template <typename T, int Q, int MODE>
+int light_config_q(int* smem, int* ctas_per_sm) {
+  *smem = light_smem<T, Q, MODE>();
+  static int s_limit = 0;  // the limit only grows, so earlier plans stay launchable
+  if (*smem > s_limit) {
+    cudaError_t e = cudaFuncSetAttribute(k_cheb_light<T, Q, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, *smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute", __FILE__, __LINE__);
+    s_limit = *smem;
+  }
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_cheb_light<T, Q, MODE>, kStepThreads, *smem);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor", __FILE__, __LINE__);
   return DOS_OK;
 }
 
-template <typename T, int Q>
-int launch_step_q(const Plan& plan, int mode, const StepParams& prm, cudaStream_t s) {
-  switch (plan.p) {
-    case 1:
-      return launch_step_qp<T, Q, 1>(plan, mode, prm, s);
-    case 2:
-      if constexpr (Q * 2 <= 32) return launch_step_qp<T, Q, 2>(plan, mode, prm, s);
-      break;
-    case 4:
-      if constexpr (Q * 4 <= 32) return launch_step_qp<T, Q, 4>(plan, mode, prm, s);
-      break;
-    default:
-      break;
+// Optional side streams: the heavy- and medium-row kernels run on them,
+// forked from and joined back into the caller's stream, so they overlap the
+// light-row kernel.  All null: everything runs on the caller's stream.
+struct SideStreams {
+  cudaStream_t a = nullptr, b = nullptr;
+  cudaEvent_t fork = nullptr, join_a = nullptr, join_b = nullptr;
+};
+
+template <typename T, int Q, int MODE>
+int launch_step_q(const Plan& plan, const StepParams& prm, cudaStream_t s, const SideStreams& side) {
+  const bool heavy = prm.n_heavy > 0 && plan.heavy_ctas > 0;
+  const bool mid = prm.n_mid > prm.n_heavy && plan.mid_ctas > 0;
+  const bool fork = side.a && side.b && (heavy || mid);
+  if (fork) NDOS_CUDA(cudaEventRecord(side.fork, s));
+  if (heavy) {
+    cudaStream_t hs = fork ? side.a : s;
+    if (fork) NDOS_CUDA(cudaStreamWaitEvent(hs, side.fork, 0));
+    k_cheb_heavy<T, Q, MODE><<<dim3(plan.heavy_ctas, plan.tiles), kStepThreads, 0, hs>>>(prm);
+    NDOS_LAUNCHED();
+    if (fork) NDOS_CUDA(cudaEventRecord(side.join_a, hs));
   }
-  return fail(DOS_EINVAL, "unsupported neighbour-slot count");
+  if (mid) {
+    cudaStream_t ms = fork ? side.b : s;
+    if (fork) NDOS_CUDA(cudaStreamWaitEvent(ms, side.fork, 0));
+    k_cheb_medium<T, Q, MODE><<<dim3(plan.mid_ctas, plan.tiles), kStepThreads, 0, ms>>>(prm);
+    NDOS_LAUNCHED();
+    if (fork) NDOS_CUDA(cudaEventRecord(side.join_b, ms));
+  }
+  if (prm.n > prm.n_mid && plan.light_ctas > 0) {
+    k_cheb_light<T, Q, MODE><<<plan.light_ctas, kStepThreads, plan.smem, s>>>(prm);
+    NDOS_LAUNCHED();
+  }
+  if (fork && heavy) NDOS_CUDA(cudaStreamWaitEvent(s, side.join_a, 0));
+  if (fork && mid) NDOS_CUDA(cudaStreamWaitEvent(s, side.join_b, 0));
+  return DOS_OK;
 }
+
+// dispatch on q to a template instance
+#define NDOS_DISPATCH_Q(T, q, CALL)                   \
+  switch (q) {                                        \
+    case 1:                                           \
+      return CALL(T, 1);                              \
+    case 2:                                           \
+      return CALL(T, 2);                              \
+    case 4:                                           \
+      return CALL(T, 4);                              \
+    case 8:                                           \
+      return CALL(T, 8);                              \
+    case 16:                                          \
+      if constexpr (VecT<T>::N == 4) return CALL(T, 16); \
+      break;                                          \
+    default:                                          \
+      break;                                          \
+  }
 
 // Chebyshev step launch for storage type T (instantiated in kpm_<type>.cu)
 template <typename T>
-int launch_step(const Plan& plan, int mode, const StepParams& prm, cudaStream_t s) {
-  switch (plan.q) {
-    case 1:
-      return launch_step_q<T, 1>(plan, mode, prm, s);
-    case 2:
-      return launch_step_q<T, 2>(plan, mode, prm, s);
-    case 4:
-      return launch_step_q<T, 4>(plan, mode, prm, s);
-    case 8:
-      return launch_step_q<T, 8>(plan, mode, prm, s);
-    case 16:
-      if constexpr (VecT<T>::N == 4) return launch_step_q<T, 16>(plan, mode, prm, s);
-      break;
-    default:
-      break;
-  }
+int launch_step(const Plan& plan, int mode, const StepParams& prm, cudaStream_t s, const SideStreams& side) {
+#define NDOS_LAUNCH_CALL(TT, QQ)                                     \
+  (mode == kModeDos ? launch_step_q<TT, QQ, kModeDos>(plan, prm, s, side) \
+                    : launch_step_q<TT, QQ, kModeLdos>(plan, prm, s, side))
+  NDOS_DISPATCH_Q(T, plan.q, NDOS_LAUNCH_CALL)
+#undef NDOS_LAUNCH_CALL
+  return fail(DOS_EINVAL, "unsupported tile width");
+}
+
+// dynamic shared memory and resident CTAs per SM of the light kernel
+template <typename T>
+int step_config(int q, int mode, int* smem, int* ctas) {
+#define NDOS_CONFIG_CALL(TT, QQ) \
+  (mode == kModeDos ? light_config_q<TT, QQ, kModeDos>(smem, ctas) : light_config_q<TT, QQ, kModeLdos>(smem, ctas))
+  NDOS_DISPATCH_Q(T, q, NDOS_CONFIG_CALL)
+#undef NDOS_CONFIG_CALL
   return fail(DOS_EINVAL, "unsupported tile width");
 }
 
@@ -468,7 +826,4 @@ int launch_init(const InitParams& prm, int grid, cudaStream_t s) {
   return DOS_OK;
 }
 
-// occupancy (resident CTAs per SM) of the step kernel for a plan
-template <typename T>
-int step_occupancy(const Plan& plan);
 }  // namespace netdos

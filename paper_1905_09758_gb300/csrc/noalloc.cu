@@ -28,7 +28,8 @@
 
 namespace netdos {
 
-int make_plan(const Graph* G, int Nz, int prec, Plan* out);  // kpm.cu
+int make_plan(const Graph* G, int Nz, int prec, int mode, Plan* out);  // kpm.cu
+int step_error_word(int** out);                                       // kpm.cu
 
 constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;  // 16 MiB
 
@@ -76,7 +77,9 @@ __global__ void __launch_bounds__(256) k_noalloc_reduce(const double* __restrict
 
 // doubled moments from the dot slots: raw[0] = <V0,V0>, raw[1+2k] =
 // <V_{k+1},V_{k+1}>, raw[2+2k] = <V_{k+1},V_k>
-__global__ void k_noalloc_moments(const double* __restrict__ raw, int M, double norm, double* __restrict__ d) {
+__global__ void k_noalloc_moments(const double* __restrict__ raw, int M, double norm, const int* __restrict__ err,
+                                  double* __restrict__ d) {
+  const bool failed = *err != 0;  // a bounded wait of the step kernel gave up
   for (int m = threadIdx.x; m < M; m += blockDim.x) {
     double mu;
     if (m == 0)
@@ -87,7 +90,7 @@ __global__ void k_noalloc_moments(const double* __restrict__ raw, int M, double 
       mu = 2.0 * raw[1 + 2 * (m / 2 - 1)] - raw[0];
     else
       mu = 2.0 * raw[2 + 2 * ((m - 1) / 2)] - raw[2];
-    d[m] = mu / norm;
+    d[m] = failed ? __longlong_as_double(0x7ff8000000000000ll) : mu / norm;
   }
 }
 
@@ -95,10 +98,10 @@ __global__ void k_noalloc_moments(const double* __restrict__ raw, int M, double 
 
 static int moments_noalloc(const Graph* G, int M, int Nz, uint64_t seed, double* d_out, cudaStream_t s) {
   Plan plan;
-  NDOS_CHECK(make_plan(G, Nz, DOS_FP32, &plan));
+  NDOS_CHECK(make_plan(G, Nz, DOS_FP32, kModeDos, &plan));
   const int64_t n = G->n;
   const int steps = M / 2;
-  const int64_t width = static_cast<int64_t>(plan.tiles) * plan.gx;
+  const int64_t width = plan.part_width;
   const int64_t n_raw = 1 + 2 * static_cast<int64_t>(steps);
   const size_t block_bytes = round256(sizeof(float) * static_cast<size_t>(n) * plan.nz_pad);
   const size_t partial_bytes = round256(sizeof(double) * static_cast<size_t>(n_raw) * width);
@@ -141,12 +144,19 @@ static int moments_noalloc(const Graph* G, int M, int Nz, uint64_t seed, double*
   StepParams prm{};
   prm.row_ptr = G->p_row_ptr;
   prm.col = G->p_col;
-  prm.deg = G->p_deg;
   prm.orig = G->p_orig;
   prm.compact = G->p_compact;
   prm.n = n;
   prm.n_heavy = G->n_heavy;
-  prm.heavy_ctas = plan.heavy_ctas;
+  prm.n_mid = G->n_mid;
+  prm.item_row = G->item_row;
+  prm.item_e = G->item_e;
+  prm.n_items = G->n_items;
+  prm.tiles = plan.tiles;
+  prm.part_width = plan.part_width;
+  prm.mid_part_off = static_cast<int64_t>(plan.heavy_ctas) * plan.tiles;
+  prm.light_part_off = static_cast<int64_t>(plan.heavy_ctas + plan.mid_ctas) * plan.tiles;
+  NDOS_CHECK(step_error_word(&prm.err));
   prm.nz = Nz;
   prm.inv_nz = 1.0f / static_cast<float>(Nz);
   prm.seed = seed;
@@ -155,11 +165,11 @@ static int moments_noalloc(const Graph* G, int M, int Nz, uint64_t seed, double*
     prm.u_pn = (k & 1) ? ua : ub;
     prm.first = k == 0 ? 1 : 0;
     prm.partial = partial + static_cast<size_t>(1 + 2 * static_cast<int64_t>(k)) * width;
-    NDOS_CHECK(launch_step<float>(plan, kModeDos, prm, s));
+    NDOS_CHECK(launch_step<float>(plan, kModeDos, prm, s, SideStreams{}));
   }
   k_noalloc_reduce<<<static_cast<unsigned>(n_raw), 256, 0, s>>>(partial, width, raw);
   NDOS_LAUNCHED();
-  k_noalloc_moments<<<1, 256, 0, s>>>(raw, M, static_cast<double>(n) * Nz, d_out);
+  k_noalloc_moments<<<1, 256, 0, s>>>(raw, M, static_cast<double>(n) * Nz, prm.err, d_out);
   NDOS_LAUNCHED();
   return DOS_OK;
 }

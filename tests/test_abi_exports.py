@@ -42,4 +42,6 @@ def test_version_and_error_text_without_gpu(libpath):
     assert lib.dos_moments(None, None, 10, 4, 1, 0, None, None) == nd.DOS_EINVAL
     assert b"NULL" in lib.dos_last_error() or b"null" in lib.dos_last_error()
     assert lib.dos_set_plan(3, 0) == nd.DOS_EINVAL
+    assert lib.dos_set_plan(0, -1) == nd.DOS_EINVAL
+    assert lib.dos_set_plan(0, 2) == nd.DOS_OK
     assert lib.dos_set_plan(0, 0) == nd.DOS_OK
