@@ -184,7 +184,7 @@ int ldos_moments(dos_graph_t g, int M, int Nz, uint64_t seed, int prec,
  *   spikes   [host] double[2 * n_spikes] pairs (lambda, mass) added as point
  *            masses (a point on an interior bin edge splits evenly between
  *            the two bins; +-1 go to the end bins); NULL if n_spikes == 0.
- *            n_spikes <= 16.
+ *            n_spikes <= 16.  M <= 2^20.
  *   hist_out [device] double[B]: bin b gets
  *            scale * (g_0 d_0 I_0b + 2 sum_{m>=1} g_m d_m I_mb) + spikes,
  *            I_mb = integral over bin b of T_m(x) / (pi sqrt(1 - x^2)) dx.

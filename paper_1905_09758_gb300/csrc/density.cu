@@ -23,37 +23,47 @@ __device__ double jackson_g(int m, int M) {
   return ((M - m + 1.0) * cos(a * m) + sin(a * m) / tan(a)) / (M + 1.0);
 }
 
-// One CTA.  coef[m] folds the damping, the factor 2 of the m >= 1 terms and
-// the 1/(m pi) of the bin integral; bin b then gets
-//   coef[0] (theta_a - theta_b) + sum_{m>=1} coef[m] (sin(m theta_a) - sin(m theta_b)).
-__global__ void k_density(const double* __restrict__ d, int M, int B, int kernel, double scale, Spikes sp,
-                          double* __restrict__ h) {
-  extern __shared__ double coef[];
+// One CTA per bin b: thread i sums the terms m = i, i + blockDim, ... of
+//   coef[m] (sin(m theta_a) - sin(m theta_b))   (m >= 1; theta_a - theta_b for m = 0),
+// coef[m] folding the damping, the factor 2 of the m >= 1 terms and the
+// 1/(m pi) of the exact bin integral; the partial sums are combined in a
+// fixed tree order, so the result is deterministic.
+__global__ void __launch_bounds__(256) k_density(const double* __restrict__ d, int M, int B, int kernel, double scale,
+                                                 Spikes sp, double* __restrict__ h) {
+  __shared__ double red[256];
+  const int b = blockIdx.x;
+  const double w = 2.0 / B;
+  const double lo = -1.0 + w * b;
+  const double hi = b + 1 == B ? 1.0 : -1.0 + w * (b + 1);
+  const double ta = acos(lo), tb = acos(hi);
+  double s = 0.0;
   for (int m = threadIdx.x; m < M; m += blockDim.x) {
     const double g = kernel == DOS_KERNEL_JACKSON ? jackson_g(m, M) : 1.0;
-    coef[m] = m == 0 ? g * d[0] / M_PI : 2.0 * g * d[m] / (m * M_PI);
+    if (m == 0)
+      s += g * d[0] / M_PI * (ta - tb);
+    else
+      s += 2.0 * g * d[m] / (m * M_PI) * (sin(m * ta) - sin(m * tb));
   }
+  red[threadIdx.x] = s;
   __syncthreads();
-  const double w = 2.0 / B;
-  for (int b = threadIdx.x; b < B; b += blockDim.x) {
-    const double lo = -1.0 + w * b;
-    const double hi = b + 1 == B ? 1.0 : -1.0 + w * (b + 1);
-    const double ta = acos(lo), tb = acos(hi);
-    double s = coef[0] * (ta - tb);
-    for (int m = 1; m < M; ++m) s += coef[m] * (sin(m * ta) - sin(m * tb));
-    s *= scale;
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double v = scale * red[0];
     for (int k = 0; k < sp.n; ++k) {
       const double x = fmin(fmax(sp.lam[k], -1.0), 1.0);
       const int e = static_cast<int>(rint((x + 1.0) / w));
       if (e > 0 && e < B && fabs(x - (-1.0 + w * e)) <= 1e-9) {
-        if (b == e - 1 || b == e) s += 0.5 * sp.mass[k];
+        if (b == e - 1 || b == e) v += 0.5 * sp.mass[k];
       } else {
         int bb = static_cast<int>(floor((x + 1.0) / w));
         bb = bb < 0 ? 0 : (bb >= B ? B - 1 : bb);
-        if (b == bb) s += sp.mass[k];
+        if (b == bb) v += sp.mass[k];
       }
     }
-    h[b] = s;
+    h[b] = v;
   }
 }
 
@@ -66,7 +76,7 @@ extern "C" int dos_density(const double* d, int M, int n_bins, int kernel, doubl
                            int n_spikes, double* hist_out, void* stream) {
   clear_error();
   if (!d || !hist_out) return fail(DOS_EINVAL, "dos_density: null pointer");
-  if (M < 1 || M > 16384) return fail(DOS_EINVAL, "dos_density: M must be in [1, 16384]");
+  if (M < 1 || M > (1 << 20)) return fail(DOS_EINVAL, "dos_density: M must be in [1, 2^20]");
   if (n_bins < 1 || n_bins > (1 << 20)) return fail(DOS_EINVAL, "dos_density: n_bins must be in [1, 2^20]");
   if (kernel != DOS_KERNEL_NONE && kernel != DOS_KERNEL_JACKSON) return fail(DOS_EINVAL, "dos_density: kernel");
   if (n_spikes < 0 || n_spikes > kMaxSpikes || (n_spikes > 0 && !spikes))
@@ -77,11 +87,8 @@ extern "C" int dos_density(const double* d, int M, int n_bins, int kernel, doubl
     sp.lam[k] = spikes[2 * k];
     sp.mass[k] = spikes[2 * k + 1];
   }
-  const size_t smem = sizeof(double) * static_cast<size_t>(M);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (smem > 48 * 1024) NDOS_CUDA(cudaFuncSetAttribute(k_density, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                       static_cast<int>(smem)));
-  k_density<<<1, 256, smem, s>>>(d, M, n_bins, kernel, scale, sp, hist_out);
+  k_density<<<n_bins, 256, 0, s>>>(d, M, n_bins, kernel, scale, sp, hist_out);
   NDOS_LAUNCHED();
   return DOS_OK;
 }
