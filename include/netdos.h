@@ -221,6 +221,63 @@ int dos_moments_noalloc(dos_graph_t g, int M, int Nz, uint64_t seed,
                         double* d_out, void* stream);
 
 /* ---------------------------------------------------------------------
+ * Batches of graphs (one operator for many small graphs).
+ * --------------------------------------------------------------------- */
+
+/*
+ * dos_build_csr_batched -- a batch of graphs as one operator.
+ * Graph g owns the original node ids [node_offset[g], node_offset[g+1]);
+ * src/dst (as for dos_build_csr, global ids) must only join nodes of the same
+ * graph.  The batch's normalized adjacency is the block-diagonal union of the
+ * graphs' (§2.1), so its spectrum is the union of theirs and the step
+ * kernels advance every graph at once.
+ *   node_offset [host] int64[n_graphs+1], node_offset[0] = 0, non-decreasing.
+ * The handle works with every single-graph call (as the union) and with
+ * dos_moments_batched.  Synchronises `stream`.
+ * Errors: DOS_EINVAL (an edge between two graphs, bad offsets), as
+ * dos_build_csr otherwise.
+ */
+int dos_build_csr_batched(const int64_t* src, const int64_t* dst,
+                          int64_t n_edges, const int64_t* node_offset,
+                          int64_t n_graphs, uint32_t flags, void* stream,
+                          dos_graph_t* out);
+
+/* Batch sizes [host outputs; any may be NULL]: n_graphs (0 for a graph from
+ * dos_build_csr), and per graph its non-isolated node count graph_n[n_graphs]
+ * and isolated node count graph_isolated[n_graphs]. */
+int dos_batch_info(dos_graph_t g, int64_t* n_graphs, int64_t* graph_n,
+                   int64_t* graph_isolated);
+
+/*
+ * dos_moments_batched -- DOS moments of every graph of a batch.
+ * Paper: §3.1, Eq. (6), (9), (11), per graph (the union's Chebyshev
+ * recurrence restricted to a graph's block is that graph's recurrence).
+ *   d_out [device] double[n_graphs * M]: d_out[g * M + m] = d_m of graph g,
+ *         normalised by its non-isolated node count times Nz (NaN for a graph
+ *         without edges).  Same probes as dos_moments keyed by global ids.
+ *   M >= 2.  No filter.
+ * The sequence of kernels is captured into a CUDA graph on the first call
+ * with a given (M, Nz, seed, prec, d_out, plan), kept on the handle, and
+ * replayed with one graph launch on `stream` by later calls.  The per-graph
+ * FP64 accumulation uses atomics, so the last bits of the moments may vary
+ * from run to run.  Stream-ordered.
+ * Errors: DOS_EINVAL (not a batch, M < 2, ...), DOS_ENOMEM, DOS_ECUDA.
+ */
+int dos_moments_batched(dos_graph_t g, int M, int Nz, uint64_t seed, int prec,
+                        double* d_out, void* stream);
+
+/*
+ * dos_autotune -- time the step kernel's candidate plans (probe tile widths
+ * with at most 16 tiles, 1 to 3 light-row CTAs per SM) on this graph for
+ * (Nz, prec) and keep the fastest on the handle; later dos_moments /
+ * ldos_moments / dos_moments_batched calls with the same Nz and prec use it
+ * unless dos_set_plan forces another.  Outputs [host, may be NULL] the chosen
+ * tile width and CTAs per SM.  Synchronises `stream`.
+ */
+int dos_autotune(dos_graph_t g, int Nz, int prec, void* stream,
+                 int* tile_width, int* ctas_per_sm);
+
+/* ---------------------------------------------------------------------
  * Tuning and instrumentation (not part of the method).
  * --------------------------------------------------------------------- */
 

@@ -11,7 +11,10 @@ from ._binding import (  # noqa: F401
     Filter,
     Graph,
     density_with_spikes,
+    dos_autotune,
+    dos_batch_info,
     dos_build_csr,
+    dos_build_csr_batched,
     dos_density,
     dos_device_status,
     dos_filter_export,
@@ -21,6 +24,7 @@ from ._binding import (  # noqa: F401
     dos_graph_info,
     dos_launch_count,
     dos_moments,
+    dos_moments_batched,
     dos_moments_noalloc,
     dos_motif_filter,
     dos_profile_enable,

@@ -63,6 +63,10 @@ _SIGNATURES = {
     "dos_profile_enable": ([_i32], _i32),
     "dos_profile_read": ([C.POINTER(C.c_double), _P64, _i32], _i32),
     "dos_set_plan": ([_i32, _i32], _i32),
+    "dos_build_csr_batched": ([_vp, _vp, _i64, _vp, _i64, _u32, _vp, C.POINTER(_vp)], _i32),
+    "dos_batch_info": ([_vp, _P64, _vp, _vp], _i32),
+    "dos_moments_batched": ([_vp, _i32, _i32, _u64, _i32, _vp, _vp], _i32),
+    "dos_autotune": ([_vp, _i32, _i32, _vp, _PI, _PI], _i32),
     "dos_get_plan": ([_vp, _i32, _i32, _PI, _PI, _PI, _PI], _i32),
 }
 
@@ -196,6 +200,47 @@ def dos_build_csr(src: torch.Tensor, dst: torch.Tensor, n_nodes: int, stream=Non
     _check(lib().dos_build_csr(_ptr(src), _ptr(dst), src.numel(), int(n_nodes), flags, _stream(stream),
                                C.byref(out)))
     return Graph(out.value)
+
+
+def dos_build_csr_batched(src: torch.Tensor, dst: torch.Tensor, node_offset, stream=None) -> Graph:
+    """A batch of graphs: graph g owns original ids [node_offset[g], node_offset[g+1])."""
+    if src.dtype != torch.int64 or dst.dtype != torch.int64 or src.shape != dst.shape:
+        raise ValueError("src and dst must be int64 tensors of equal shape")
+    src, dst = src.contiguous(), dst.contiguous()
+    flags = 0 if src.is_cuda else DOS_INPUT_HOST
+    off = (C.c_int64 * len(node_offset))(*[int(x) for x in node_offset])
+    out = C.c_void_p()
+    _check(lib().dos_build_csr_batched(_ptr(src), _ptr(dst), src.numel(), off, len(node_offset) - 1, flags,
+                                       _stream(stream), C.byref(out)))
+    return Graph(out.value)
+
+
+def dos_batch_info(g: Graph) -> dict:
+    ng = C.c_int64()
+    _check(lib().dos_batch_info(g.handle, C.byref(ng), None, None))
+    gn = (C.c_int64 * max(1, ng.value))()
+    gi = (C.c_int64 * max(1, ng.value))()
+    _check(lib().dos_batch_info(g.handle, None, gn, gi))
+    return {"n_graphs": ng.value, "graph_n": list(gn)[: ng.value], "graph_isolated": list(gi)[: ng.value]}
+
+
+def dos_moments_batched(g: Graph, M: int, Nz: int, seed: int, prec: str = "fp32",
+                        d_out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Per-graph DOS moments of a batch: float64 CUDA tensor (n_graphs, M)."""
+    ng = dos_batch_info(g)["n_graphs"]
+    if d_out is None:
+        d_out = torch.empty((ng, M), dtype=torch.float64, device=torch.device("cuda", torch.cuda.current_device()))
+    _need_cuda(d_out, torch.float64, "d_out", ng * M)
+    _check(lib().dos_moments_batched(g.handle, int(M), int(Nz), int(seed) & (2**64 - 1), PREC[prec], _ptr(d_out),
+                                     _stream(stream)))
+    return d_out
+
+
+def dos_autotune(g: Graph, Nz: int, prec: str = "fp32", stream=None) -> dict:
+    """Time candidate plans on this graph and keep the fastest; returns it."""
+    t, c = C.c_int(), C.c_int()
+    _check(lib().dos_autotune(g.handle, int(Nz), PREC[prec], _stream(stream), C.byref(t), C.byref(c)))
+    return {"tile_width": t.value, "ctas_per_sm": c.value}
 
 
 def dos_graph_info(g: Graph) -> dict:

@@ -160,9 +160,10 @@ void dos_graph_destroy(dos_graph_t g) {
   if (!g) return;
   Graph* G = reinterpret_cast<Graph*>(g);
   void* ptrs[] = {G->row_ptr, G->col,    G->deg,    G->s64,       G->s32,     G->old_id,
-                  G->p_row_ptr, G->p_col, G->p_deg, G->p_orig, G->p_compact, G->compact_to_p, G->item_row, G->item_e};
+                  G->p_row_ptr, G->p_col, G->p_deg, G->p_orig, G->p_compact, G->compact_to_p, G->p_gid, G->graph_n};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  destroy_captured(G->captured);
   delete G;
 }
 

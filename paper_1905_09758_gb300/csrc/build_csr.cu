@@ -6,6 +6,8 @@
 #include <cub/device/device_scan.cuh>
 #include <cub/device/device_select.cuh>
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace netdos {
@@ -125,30 +127,33 @@ __global__ void k_perm_keys(const uint64_t* __restrict__ keys, int64_t nnz, cons
   }
 }
 
-// light row i (position n_mid + i) starts an item at i = 0, every kItemRows
-// rows, and wherever its row offset enters a new multiple of kItemNnzStep; an
-// item then holds fewer than kItemNnzStep + kMediumDeg nonzeros
-__global__ void k_item_flags(const int64_t* __restrict__ p_row_ptr, int64_t n_mid, int64_t n_light,
-                             int32_t* __restrict__ flag) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_light;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = n_mid + i;
-    flag[i] = (i == 0 || i % kItemRows == 0 || p_row_ptr[r] / kItemNnzStep != p_row_ptr[r - 1] / kItemNnzStep) ? 1 : 0;
+// graph of each position (largest g with node_off[g] <= original id) and
+// the non-isolated node count of each graph
+__global__ void k_graph_of(const int32_t* __restrict__ p_orig, int64_t n, const int64_t* __restrict__ node_off,
+                           int64_t n_graphs, int32_t* __restrict__ p_gid, unsigned long long* __restrict__ count) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = p_orig[p];
+    int64_t lo = 0, hi = n_graphs - 1;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi + 1) >> 1;
+      if (node_off[mid] <= o) lo = mid; else hi = mid - 1;
+    }
+    p_gid[p] = static_cast<int32_t>(lo);
+    atomicAdd(&count[lo], 1ull);
   }
 }
 
-__global__ void k_item_scatter(const int32_t* __restrict__ flag, const int32_t* __restrict__ id, int64_t n_light,
-                               int32_t* __restrict__ item_row) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_light;
-       i += (int64_t)gridDim.x * blockDim.x)
-    if (flag[i]) item_row[id[i]] = static_cast<int32_t>(i);
-}
-
-__global__ void k_item_offsets(const int32_t* __restrict__ item_row, int64_t n_items, const int64_t* __restrict__ p_row_ptr,
-                               int64_t n_mid, int64_t* __restrict__ item_e) {
-  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c <= n_items;
-       c += (int64_t)gridDim.x * blockDim.x)
-    item_e[c] = p_row_ptr[n_mid + item_row[c]];
+// every edge must join two nodes of the same graph (warp per row)
+__global__ void k_check_within(const int64_t* __restrict__ p_row_ptr, const int32_t* __restrict__ p_col,
+                               const int32_t* __restrict__ p_gid, int64_t n, int* __restrict__ bad) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t p = w0; p < n; p += nw) {
+    const int32_t g = p_gid[p];
+    for (int64_t e = p_row_ptr[p] + lane; e < p_row_ptr[p + 1]; e += 32)
+      if (p_gid[p_col[e]] != g) atomicOr(bad, 1);
+  }
 }
 
 __global__ void k_low_word(const uint64_t* __restrict__ keys, int64_t nnz, int32_t* __restrict__ out) {
@@ -365,45 +370,72 @@ static int build_csr_impl(const int64_t* src_in, const int64_t* dst_in, int64_t 
   G->n_heavy = static_cast<int64_t>(nh[0]);
   G->n_mid = static_cast<int64_t>(nh[1]);
 
-  // ---- warp items over the light rows ----
-  const int64_t n_light = n - G->n_mid;
-  int32_t *flag = nullptr, *id = nullptr;
-  NDOS_CHECK(t.get(&flag, n_light + 1));
-  NDOS_CHECK(t.get(&id, n_light + 1));
-  int32_t n_items = 0;
-  if (n_light > 0) {
-    k_item_flags<<<grid_for(n_light), kThreads, 0, s>>>(G->p_row_ptr, G->n_mid, n_light, flag);
-    NDOS_LAUNCHED();
-    NDOS_CUDA(cudaMemsetAsync(flag + n_light, 0, sizeof(int32_t), s));
-    size_t bytes = 0;
-    NDOS_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, bytes, flag, id, n_light + 1, s));
-    void* tmp = nullptr;
-    NDOS_CHECK(t.get(reinterpret_cast<char**>(&tmp), bytes));
-    NDOS_CUDA(cub::DeviceScan::ExclusiveSum(tmp, bytes, flag, id, n_light + 1, s));
-    count_launch();
-    NDOS_CUDA(cudaMemcpyAsync(&n_items, id + n_light, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    NDOS_CUDA(cudaStreamSynchronize(s));
-  }
-  NDOS_CHECK(persistent_alloc(&G->item_row, static_cast<size_t>(n_items) + 1));
-  if (n_light > 0) {
-    k_item_scatter<<<grid_for(n_light), kThreads, 0, s>>>(flag, id, n_light, G->item_row);
-    NDOS_LAUNCHED();
-  }
-  const int32_t end_row = static_cast<int32_t>(n_light);
-  NDOS_CUDA(cudaMemcpyAsync(G->item_row + n_items, &end_row, sizeof(int32_t), cudaMemcpyHostToDevice, s));
-  NDOS_CHECK(persistent_alloc(&G->item_e, static_cast<size_t>(n_items) + 1));
-  k_item_offsets<<<grid_for(n_items + 1), kThreads, 0, s>>>(G->item_row, n_items, G->p_row_ptr, G->n_mid, G->item_e);
-  NDOS_LAUNCHED();
-  NDOS_CUDA(cudaStreamSynchronize(s));
-  G->n_items = n_items;
-  G->max_deg = md;
-
   return DOS_OK;
 }
 
 }  // namespace netdos
 
 using namespace netdos;
+
+static int tag_graphs(Graph* G, const int64_t* node_offset, int64_t n_graphs, cudaStream_t s) {
+  Temps t(s);
+  int64_t* off = nullptr;
+  unsigned long long* cnt = nullptr;
+  int* bad = nullptr;
+  NDOS_CHECK(t.get(&off, n_graphs + 1));
+  NDOS_CHECK(t.get(&cnt, n_graphs));
+  NDOS_CHECK(t.get(&bad, 1));
+  NDOS_CHECK(persistent_alloc(&G->p_gid, G->n));
+  NDOS_CHECK(persistent_alloc(&G->graph_n, n_graphs));
+  NDOS_CUDA(cudaMemcpyAsync(off, node_offset, sizeof(int64_t) * (n_graphs + 1), cudaMemcpyHostToDevice, s));
+  NDOS_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * n_graphs, s));
+  NDOS_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+  if (G->n > 0) {
+    k_graph_of<<<grid_for(G->n), kThreads, 0, s>>>(G->p_orig, G->n, off, n_graphs, G->p_gid, cnt);
+    NDOS_LAUNCHED();
+    k_check_within<<<grid_for(G->n * 32), kThreads, 0, s>>>(G->p_row_ptr, G->p_col, G->p_gid, G->n, bad);
+    NDOS_LAUNCHED();
+  }
+  std::vector<unsigned long long> h(n_graphs);
+  int h_bad = 0;
+  NDOS_CUDA(cudaMemcpyAsync(h.data(), cnt, sizeof(unsigned long long) * n_graphs, cudaMemcpyDeviceToHost, s));
+  NDOS_CUDA(cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+  NDOS_CUDA(cudaStreamSynchronize(s));
+  if (h_bad) return fail(DOS_EINVAL, "dos_build_csr_batched: an edge joins nodes of two different graphs");
+  G->n_graphs = n_graphs;
+  G->h_graph_n.resize(n_graphs);
+  G->h_graph_iso.resize(n_graphs);
+  for (int64_t g = 0; g < n_graphs; ++g) {
+    G->h_graph_n[g] = static_cast<int64_t>(h[g]);
+    G->h_graph_iso[g] = (node_offset[g + 1] - node_offset[g]) - G->h_graph_n[g];
+  }
+  NDOS_CUDA(cudaMemcpyAsync(G->graph_n, G->h_graph_n.data(), sizeof(int64_t) * n_graphs, cudaMemcpyHostToDevice, s));
+  NDOS_CUDA(cudaStreamSynchronize(s));
+  return DOS_OK;
+}
+
+extern "C" int dos_build_csr_batched(const int64_t* src, const int64_t* dst, int64_t n_edges,
+                                     const int64_t* node_offset, int64_t n_graphs, uint32_t flags, void* stream,
+                                     dos_graph_t* out) {
+  clear_error();
+  if (!out) return fail(DOS_EINVAL, "dos_build_csr_batched: out is NULL");
+  *out = nullptr;
+  if (!node_offset || n_graphs < 1) return fail(DOS_EINVAL, "dos_build_csr_batched: need node_offset and n_graphs >= 1");
+  if (n_graphs > 0x7fffffffLL) return fail(DOS_EOVERFLOW, "dos_build_csr_batched: too many graphs");
+  if (node_offset[0] != 0) return fail(DOS_EINVAL, "dos_build_csr_batched: node_offset[0] must be 0");
+  for (int64_t g = 0; g < n_graphs; ++g)
+    if (node_offset[g + 1] < node_offset[g]) return fail(DOS_EINVAL, "dos_build_csr_batched: node_offset decreases");
+  dos_graph_t h = nullptr;
+  NDOS_CHECK(dos_build_csr(src, dst, n_edges, node_offset[n_graphs], flags, stream, &h));
+  Graph* G = reinterpret_cast<Graph*>(h);
+  const int st = tag_graphs(G, node_offset, n_graphs, static_cast<cudaStream_t>(stream));
+  if (st != DOS_OK) {
+    dos_graph_destroy(h);
+    return st;
+  }
+  *out = h;
+  return DOS_OK;
+}
 
 extern "C" int dos_build_csr(const int64_t* src, const int64_t* dst, int64_t n_edges, int64_t n_nodes,
                              uint32_t flags, void* stream, dos_graph_t* out) {

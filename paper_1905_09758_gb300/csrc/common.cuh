@@ -115,13 +115,20 @@ struct Graph {
   int32_t max_deg = 0;
   int64_t n_heavy = 0;          // positions [0, n_heavy) have deg >= kHeavyDeg
   int64_t n_mid = 0;            // positions [n_heavy, n_mid) have kMediumDeg <= deg < kHeavyDeg
-  // light rows [n_mid, n) cut into warp items: item c = positions n_mid +
-  // [item_row[c], item_row[c+1]), at most kItemRows rows and fewer than
-  // kItemNnzStep + kMediumDeg nonzeros
-  int32_t* item_row = nullptr;  // [n_items+1]
-  int64_t* item_e = nullptr;    // [n_items+1] row offset of each item's first row
-  int64_t n_items = 0;
+  // a batch of graphs (dos_build_csr_batched): the operator is their disjoint
+  // union; n_graphs = 0 for a single graph
+  int64_t n_graphs = 0;
+  int32_t* p_gid = nullptr;     // [n] graph of position k
+  int64_t* graph_n = nullptr;   // [n_graphs] non-isolated nodes per graph (device)
+  std::vector<int64_t> h_graph_n, h_graph_iso;  // per graph: non-isolated / isolated nodes
+  // plan chosen by dos_autotune (0 = none)
+  int tuned_t = 0, tuned_ctas = 0, tuned_nz = 0, tuned_prec = -1;
+  // captured batched-moment sequence (dos_moments_batched)
+  struct Captured* captured = nullptr;
 };
+
+struct Captured;
+void destroy_captured(Captured* c);  // batch.cu
 
 struct Filter {
   const Graph* g = nullptr;
@@ -135,8 +142,6 @@ struct Filter {
 
 constexpr int kHeavyDeg = 2048;  // rows at or above this degree get a whole CTA
 constexpr int kMediumDeg = 64;   // rows at or above this degree (and below kHeavyDeg) get a warp
-constexpr int kItemRows = 64;     // light rows per warp item (at most)
-constexpr int kItemNnzStep = 256; // an item ends where a row offset enters a new multiple
 
 // ---------------------------------------------------------------------------
 // SplitMix64 (Steele, Lea, Flood, OOPSLA 2014): n-th output of the stream

@@ -113,7 +113,7 @@ int step_error_word(int** out) {
 static std::mutex g_side_mu;
 static SideStreams g_side[64];
 
-static int side_streams(SideStreams* out) {
+int side_streams(SideStreams* out) {
   int dev = 0;
   NDOS_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) return fail(DOS_EINVAL, "device ordinal out of range");
@@ -129,6 +129,8 @@ static int side_streams(SideStreams* out) {
   *out = sd;
   return DOS_OK;
 }
+
+int side_streams_for_capture(SideStreams* out) { return side_streams(out); }
 
 static int light_config(int prec, int q, int mode, int* smem, int* ctas) {
   switch (prec) {
@@ -155,9 +157,13 @@ int make_plan(const Graph* G, int Nz, int prec, int mode, Plan* out) {
   bool have = false, have_fit = false;
   double best = 0.0;
   Plan pl;
+  // a plan forced process-wide wins over one tuned for this graph
+  const bool tuned = G->tuned_t > 0 && G->tuned_nz == Nz && G->tuned_prec == prec;
+  const int force_t = g_force_t ? g_force_t : (tuned ? G->tuned_t : 0);
+  const int force_ctas = g_force_ctas ? g_force_ctas : (tuned ? G->tuned_ctas : 0);
   for (int q = 1; q <= qmax; q *= 2) {
     const int t = q * V;
-    if (g_force_t && t != g_force_t) continue;
+    if (force_t && t != force_t) continue;
     const int tiles = (Nz + t - 1) / t;
     const int nz_pad = tiles * t;
     const double bytes = tiles * (4.0 * nnz + 8.0 * (n + 1) + 8.0 * n) + 3.0 * n * nz_pad * es;
@@ -183,7 +189,7 @@ int make_plan(const Graph* G, int Nz, int prec, int mode, Plan* out) {
   pl.smem = smem;
   // two resident CTAs per SM measured best: more shared memory per SM leaves
   // less L1 to hold the gathers in flight
-  ctas = std::min(ctas, g_force_ctas > 0 ? g_force_ctas : 2);
+  ctas = std::min(ctas, force_ctas > 0 ? force_ctas : 2);
   const int64_t n_light = G->n - G->n_mid;
   const int64_t rounds = (n_light + 32 / pl.q - 1) / (32 / pl.q) * pl.tiles;
   pl.light_ctas = static_cast<int>(std::min<int64_t>(static_cast<int64_t>(std::max(1, ctas)) * sms,
@@ -271,9 +277,6 @@ static int run_steps(const Graph* G, const Filter* F, const Plan& plan, int M, i
   prm.n = n;
   prm.n_heavy = G->n_heavy;
   prm.n_mid = G->n_mid;
-  prm.item_row = G->item_row;
-  prm.item_e = G->item_e;
-  prm.n_items = G->n_items;
   prm.tiles = plan.tiles;
   prm.part_width = plan.part_width;
   prm.mid_part_off = static_cast<int64_t>(plan.heavy_ctas) * plan.tiles;

@@ -177,9 +177,12 @@ struct StepParams {
   int64_t n;
   int64_t n_heavy;  // rows [0, n_heavy): k_cheb_heavy
   int64_t n_mid;    // rows [n_heavy, n_mid): k_cheb_medium; [n_mid, n): k_cheb_light
-  const int32_t* __restrict__ item_row;  // [n_items+1] light warp items (rows relative to n_mid)
-  const int64_t* __restrict__ item_e;    // [n_items+1] row offset of each item's first row
-  int64_t n_items;
+  // batch of graphs: gid[p] = graph of row p; the row's dot contributions go
+  // to gpartial[dot * n_graphs + gid] (FP64 atomics) instead of the per-CTA
+  // partials.  gid == nullptr for a single graph.
+  const int32_t* __restrict__ gid;
+  double* gpartial;
+  int64_t n_graphs;
   int tiles;
   int first;        // 1: U_1 = S^2 A U_0 (no U_{k-1} term)
   int nz;           // real probe count (columns >= nz are zero padding)
@@ -239,8 +242,14 @@ __device__ __forceinline__ void step_epilogue(const StepParams& prm, bool active
   }
   if (active && owner) {
     if (MODE == kModeDos) {
-      dd0 += static_cast<double>(fd * prod0);
-      dd1 += static_cast<double>(fd * prod1);
+      if (prm.gid) {
+        const int32_t g = prm.gid[p];
+        atomicAdd(prm.gpartial + g, static_cast<double>(fd * prod0));
+        atomicAdd(prm.gpartial + prm.n_graphs + g, static_cast<double>(fd * prod1));
+      } else {
+        dd0 += static_cast<double>(fd * prod0);
+        dd1 += static_cast<double>(fd * prod1);
+      }
     } else {
       const float vsum = prod0 * sqrtf(fd);  // sum_j z_j (V_{k+1})_j of this tile
       dd0 += static_cast<double>(vsum);
@@ -825,5 +834,18 @@ int launch_init(const InitParams& prm, int grid, cudaStream_t s) {
   NDOS_LAUNCHED();
   return DOS_OK;
 }
+
+// The kernels are instantiated once, in kpm_<type>.cu.  Other translation
+// units must not instantiate their own copies: each copy would be a separate
+// device function, and attributes set on one (the shared-memory limit) would
+// not apply to the other.
+#define NDOS_EXTERN_STEP(T)                                                                           \
+  extern template int launch_step<T>(const Plan&, int, const StepParams&, cudaStream_t, const SideStreams&); \
+  extern template int step_config<T>(int, int, int*, int*);                                          \
+  extern template int launch_init<T>(const InitParams&, int, cudaStream_t);
+NDOS_EXTERN_STEP(float)
+NDOS_EXTERN_STEP(__nv_bfloat16)
+NDOS_EXTERN_STEP(__half)
+#undef NDOS_EXTERN_STEP
 
 }  // namespace netdos

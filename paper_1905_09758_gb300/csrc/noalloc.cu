@@ -149,9 +149,6 @@ static int moments_noalloc(const Graph* G, int M, int Nz, uint64_t seed, double*
   prm.n = n;
   prm.n_heavy = G->n_heavy;
   prm.n_mid = G->n_mid;
-  prm.item_row = G->item_row;
-  prm.item_e = G->item_e;
-  prm.n_items = G->n_items;
   prm.tiles = plan.tiles;
   prm.part_width = plan.part_width;
   prm.mid_part_off = static_cast<int64_t>(plan.heavy_ctas) * plan.tiles;

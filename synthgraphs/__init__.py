@@ -18,11 +18,16 @@ The graph models follow the ones the paper works with:
   lambda = 0 motif of §3.4 (Fig. 3a).
 
 Recipes (the parameters of each model) are stated in each function's
-docstring.  All randomness comes from ``numpy.random.Generator(PCG64(seed))``.
+docstring.  Randomness comes from ``numpy.random.Generator(PCG64(seed))``,
+except for Barabasi-Albert, whose sequential attachment runs in a small C
+helper (``_native.c``, built with gcc on first use) drawing from SplitMix64.
 """
 from __future__ import annotations
 
+import ctypes
 import math
+import os
+import subprocess
 
 import numpy as np
 
@@ -37,11 +42,33 @@ __all__ = [
     "complete_bipartite",
     "path",
     "batch_graphs",
+    "union",
 ]
 
 
 def _rng(seed: int) -> np.random.Generator:
     return np.random.Generator(np.random.PCG64(int(seed)))
+
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_native = None
+
+
+def _native_lib():
+    """The C helpers (_native.c), built with gcc on first use."""
+    global _native
+    if _native is None:
+        so = os.path.join(_HERE, "_native.so")
+        src = os.path.join(_HERE, "_native.c")
+        if not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(src):
+            tmp = so + f".{os.getpid()}.tmp"
+            subprocess.check_call(["gcc", "-O2", "-shared", "-fPIC", "-o", tmp, src])
+            os.replace(tmp, so)
+        lib = ctypes.CDLL(so)
+        lib.ba_edges.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64] + [ctypes.c_void_p] * 3
+        lib.ba_edges.restype = ctypes.c_int64
+        _native = lib
+    return _native
 
 
 def _pair_from_linear(idx: np.ndarray, n: int):
@@ -123,41 +150,20 @@ def barabasi_albert(n: int, m: int, seed: int):
     Seed graph: the clique K_{m+1} on nodes 0..m.  Each later node t attaches to
     m distinct earlier nodes, each drawn with probability proportional to its
     current degree (uniform draws from the list of edge endpoints, redrawing
-    repeats).  Returns unique pairs.
+    repeats).  The draws use SplitMix64 seeded with ``seed`` (C helper).
+    Returns unique pairs.
     """
     n, m = int(n), int(m)
     if n <= m + 1:
         return complete(n)
-    rng = _rng(seed)
+    if not 1 <= m <= 64:
+        raise ValueError("m must be in [1, 64]")
     n_edges = m * (m + 1) // 2 + (n - m - 1) * m
     src = np.empty(n_edges, np.int64)
     dst = np.empty(n_edges, np.int64)
     ends = np.empty(2 * n_edges, np.int64)
-    e = 0
-    for a in range(m + 1):
-        for b in range(a + 1, m + 1):
-            src[e], dst[e] = a, b
-            ends[2 * e], ends[2 * e + 1] = a, b
-            e += 1
-    n_ends = 2 * e
-    # draw uniform numbers in batches to keep Python overhead bounded
-    buf = rng.random(4 * m + 8)
-    bpos = 0
-    for t in range(m + 1, n):
-        chosen = []
-        while len(chosen) < m:
-            if bpos >= buf.size:
-                buf = rng.random(4 * m + 8)
-                bpos = 0
-            c = int(ends[int(buf[bpos] * n_ends)])
-            bpos += 1
-            if c not in chosen:
-                chosen.append(c)
-        for c in chosen:
-            src[e], dst[e] = t, c
-            ends[n_ends], ends[n_ends + 1] = t, c
-            n_ends += 2
-            e += 1
+    got = _native_lib().ba_edges(n, m, int(seed) & (2**64 - 1), src.ctypes.data, dst.ctypes.data, ends.ctypes.data)
+    assert got == n_edges
     return src, dst, n
 
 
@@ -217,6 +223,22 @@ def complete_bipartite(a: int, b: int):
     """K_{a,b}: parts {0..a-1} and {a..a+b-1}."""
     u, v = np.meshgrid(np.arange(a), np.arange(a, a + b), indexing="ij")
     return u.ravel().astype(np.int64), v.ravel().astype(np.int64), a + b
+
+
+def union(graphs):
+    """Concatenate graphs [(src, dst, n), ...] into one edge list with global ids.
+
+    Returns (src, dst, node_offset) where graph g owns ids
+    [node_offset[g], node_offset[g+1]).
+    """
+    offs = [0]
+    srcs, dsts = [], []
+    for s, d, n in graphs:
+        srcs.append(np.asarray(s, np.int64) + offs[-1])
+        dsts.append(np.asarray(d, np.int64) + offs[-1])
+        offs.append(offs[-1] + int(n))
+    return (np.concatenate(srcs) if srcs else np.zeros(0, np.int64),
+            np.concatenate(dsts) if dsts else np.zeros(0, np.int64), np.asarray(offs, np.int64))
 
 
 def batch_graphs(count: int, seed: int, n_min: int = 200, n_max: int = 20000):
