@@ -32,4 +32,8 @@ Parity status of each function (what pins it, see ``tests/test_oracle_*.py``):
 * ``mlp_*``                        -- pinned by central finite differences.
 """
 from .kpm import *  # noqa: F401,F403
-from .kpm import __all__  # noqa: F401
+from .kpm import __all__ as _kpm_all
+from .mlp import *  # noqa: F401,F403
+from .mlp import __all__ as _mlp_all
+
+__all__ = list(_kpm_all) + list(_mlp_all)

@@ -1,0 +1,60 @@
+"""Oracle pins for the density-reconstruction MLP: central finite differences
+of the loss against the analytic gradient, softmax rows summing to 1, and an
+Adam step against its closed form on a scalar."""
+import numpy as np
+
+import oracle
+
+
+def _setup(seed=0):
+    rng = np.random.default_rng(seed)
+    sizes = [7, 9, 8, 5]
+    params = oracle.mlp_init(sizes, rng)
+    params = [(w, rng.normal(0, 0.1, b.shape)) for w, b in params]
+    x = rng.normal(size=(6, 7))
+    t = rng.random((6, 5))
+    t /= t.sum(axis=1, keepdims=True)
+    return params, x, t
+
+
+def test_softmax_rows_are_distributions():
+    params, x, _ = _setup()
+    p, _, _ = oracle.mlp_forward(params, x)
+    assert np.allclose(p.sum(axis=1), 1.0) and p.min() > 0
+
+
+def test_gradient_matches_central_differences():
+    params, x, t = _setup(1)
+    loss, grads = oracle.mlp_loss_grad(params, x, t)
+    h = 1e-6
+    for l, (w, b) in enumerate(params):
+        for arr, g in ((w, grads[l][0]), (b, grads[l][1])):
+            flat = arr.reshape(-1)
+            for idx in range(0, flat.size, max(1, flat.size // 7)):
+                old = flat[idx]
+                flat[idx] = old + h
+                lp, _ = oracle.mlp_loss_grad(params, x, t)
+                flat[idx] = old - h
+                lm, _ = oracle.mlp_loss_grad(params, x, t)
+                flat[idx] = old
+                num = (lp - lm) / (2 * h)
+                assert abs(num - g.reshape(-1)[idx]) <= 1e-6 * max(1.0, abs(num))
+
+
+def test_cross_entropy_is_minimal_at_the_target():
+    # with one linear layer and logits = log t, the loss equals the entropy of t
+    t = np.array([[0.2, 0.3, 0.5]])
+    params = [(np.zeros((3, 1)), np.log(t[0]))]
+    loss, grads = oracle.mlp_loss_grad(params, np.ones((1, 1)), t)
+    assert abs(loss - (-np.sum(t * np.log(t)))) < 1e-12
+    assert np.abs(grads[0][1]).max() < 1e-12
+
+
+def test_adam_first_step_is_lr_times_sign():
+    # after one step from zero moments, the bias-corrected update is lr * g / (|g| + eps)
+    params = [(np.array([[1.0]]), np.array([0.5]))]
+    grads = [(np.array([[2.0]]), np.array([-3.0]))]
+    zero = [(np.zeros((1, 1)), np.zeros(1))]
+    p, m, v = oracle.adam_step(params, grads, zero, zero, 1, 0.01)
+    assert abs(p[0][0][0, 0] - (1.0 - 0.01 * 2.0 / (2.0 + 1e-8))) < 1e-12
+    assert abs(p[0][1][0] - (0.5 + 0.01 * 3.0 / (3.0 + 1e-8))) < 1e-12
