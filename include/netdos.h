@@ -41,6 +41,7 @@ extern "C" {
 
 typedef struct dos_graph_s* dos_graph_t;
 typedef struct dos_filter_s* dos_filter_t;
+typedef struct dos_mlp_s* dos_mlp_t;
 
 enum dos_status {
   DOS_OK = 0,
@@ -276,6 +277,81 @@ int dos_moments_batched(dos_graph_t g, int M, int Nz, uint64_t seed, int prec,
  */
 int dos_autotune(dos_graph_t g, int Nz, int prec, void* stream,
                  int* tile_width, int* ctas_per_sm);
+
+/*
+ * dos_density_batched -- dos_density (kernel, no scale, no spikes) for every
+ * graph of a batch: hist_out[g * n_bins + b] from d[g * M .. g * M + M).
+ * Paper: §2.2 spectral histogram, Eq. (7)-(8); §4.1 Jackson damping.
+ *   d        [device] double[n_graphs * M] (e.g. from dos_moments_batched)
+ *   hist_out [device] double[n_graphs * n_bins]
+ * Errors: DOS_EINVAL (null pointer, M or n_bins outside [1, 2^20],
+ * n_graphs < 1).  Stream-ordered.
+ */
+int dos_density_batched(const double* d, int M, int64_t n_graphs, int n_bins,
+                        int kernel, double* hist_out, void* stream);
+
+/* ---------------------------------------------------------------------
+ * Learned reconstruction of the density from few noisy moments.
+ *
+ * Not part of the paper: a small fully connected network (ReLU hidden layers,
+ * softmax output over n_bins histogram bins) that maps a graph's feature
+ * vector (the Jackson histogram and the first K moments of a cheap KPM run)
+ * to its spectral histogram, trained with softmax cross-entropy against the
+ * histograms of an accurate KPM run and Adam (Kingma & Ba, 2015;
+ * beta1 = 0.9, beta2 = 0.999, eps = 1e-8, bias-corrected).  Plain Jackson
+ * KPM (dos_density) is its fallback.
+ *
+ * Parameters are one flat float32 buffer: for each layer l, W_l (out_l x
+ * in_l, row-major) then b_l[out_l].  All matrices are row-major float32 on
+ * the device.  Every call is stream-ordered; its reductions run in a fixed
+ * order, so results are bit-reproducible.
+ * --------------------------------------------------------------------- */
+
+/* Network with n_layers weight layers of sizes[0] -> sizes[1] -> ... ->
+ * sizes[n_layers] (each in [1, 8192], n_layers in [1, 16]); weights
+ * He-uniform from SplitMix64(seed), biases 0.  Synchronises the device.
+ * Errors: DOS_EINVAL, DOS_ENOMEM. */
+int dos_mlp_create(int n_layers, const int* sizes, uint64_t seed,
+                   dos_mlp_t* out);
+void dos_mlp_destroy(dos_mlp_t net);
+/* Number of float32 parameters [host output]. */
+int dos_mlp_param_count(dos_mlp_t net, int64_t* count);
+/* Copy the parameters to / from a device buffer of dos_mlp_param_count
+ * floats.  set_params also resets Adam's moments and step count. */
+int dos_mlp_get_params(dos_mlp_t net, float* out, void* stream);
+int dos_mlp_set_params(dos_mlp_t net, const float* in, void* stream);
+
+/* probs[rows][sizes[n_layers]] = softmax(network(x)), x[rows][sizes[0]].
+ * Errors: DOS_EINVAL (rows < 1, null pointer), DOS_ENOMEM. */
+int dos_mlp_forward(dos_mlp_t net, const float* x, int rows, float* probs,
+                    void* stream);
+
+/* Cross-entropy -(1/rows) sum t log p of targets t[rows][out] (rows of t
+ * sum to 1) and its gradient.  loss [device] float[1] or NULL; grad [device]
+ * float[param_count] or NULL (the gradient is kept on the handle). */
+int dos_mlp_loss_grad(dos_mlp_t net, const float* x, const float* t, int rows,
+                      float* loss, float* grad, void* stream);
+
+/* One Adam step on the minibatch rows idx[0..rows) of (x, t) (idx [device]
+ * int32, NULL = the first `rows` rows) with learning rate lr > 0; loss
+ * [device] float[1] or NULL receives the minibatch loss before the step. */
+int dos_mlp_train_step(dos_mlp_t net, const float* x, const float* t,
+                       const int32_t* idx, int rows, float lr, float* loss,
+                       void* stream);
+
+/* Feature rows for the network, one per graph g < n_graphs:
+ *   x_out[g] = [ n_bins * hist[g * n_bins + b] for b < n_bins,
+ *                d[g * ld_d + m] for 1 <= m < K ]      (n_bins + K - 1 floats)
+ * hist [device] double (a Jackson histogram, e.g. dos_density_batched),
+ * d [device] double moments (row stride ld_d >= K).  Errors: DOS_EINVAL. */
+int dos_mlp_features(const double* hist, int n_bins, const double* d,
+                     int ld_d, int K, int64_t n_graphs, float* x_out,
+                     void* stream);
+
+/* Training targets: t_out[g][b] = max(hist[g][b], 0) / sum_b max(hist[g][b], 0)
+ * (uniform if that sum is 0).  Errors: DOS_EINVAL. */
+int dos_hist_normalize(const double* hist, int n_bins, int64_t n_graphs,
+                       float* t_out, void* stream);
 
 /* ---------------------------------------------------------------------
  * Tuning and instrumentation (not part of the method).

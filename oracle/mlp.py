@@ -21,7 +21,7 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["mlp_init", "mlp_forward", "mlp_loss_grad", "adam_step"]
+__all__ = ["mlp_init", "mlp_forward", "mlp_loss_grad", "adam_step", "mlp_features", "normalize_hist"]
 
 
 def mlp_init(sizes, rng: np.random.Generator):
@@ -80,3 +80,23 @@ def adam_step(params, grads, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
         out_m.append((new[0][1], new[1][1]))
         out_v.append((new[0][2], new[1][2]))
     return out_p, out_m, out_v
+
+
+def mlp_features(hist, d, k):
+    """Feature row per graph: [B * bin masses of the histogram, d_1 .. d_{k-1}].
+
+    B * mass is the mean density over a bin scaled to [-1, 1] (O(1) values);
+    d_0 = 1 after normalisation carries no information and is left out.
+    """
+    hist = np.asarray(hist, np.float64)
+    d = np.asarray(d, np.float64)
+    return np.concatenate([hist.shape[1] * hist, d[:, 1:k]], axis=1)
+
+
+def normalize_hist(hist):
+    """Target distribution: negative bins clipped to 0, rows scaled to sum 1
+    (uniform where nothing is left)."""
+    h = np.maximum(np.asarray(hist, np.float64), 0.0)
+    s = h.sum(axis=1, keepdims=True)
+    uni = np.full_like(h, 1.0 / h.shape[1])
+    return np.where(s > 0.0, h / np.where(s > 0.0, s, 1.0), uni)

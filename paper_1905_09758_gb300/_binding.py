@@ -68,6 +68,17 @@ _SIGNATURES = {
     "dos_moments_batched": ([_vp, _i32, _i32, _u64, _i32, _vp, _vp], _i32),
     "dos_autotune": ([_vp, _i32, _i32, _vp, _PI, _PI], _i32),
     "dos_get_plan": ([_vp, _i32, _i32, _PI, _PI, _PI, _PI], _i32),
+    "dos_density_batched": ([_vp, _i32, _i64, _i32, _i32, _vp, _vp], _i32),
+    "dos_mlp_create": ([_i32, _PI, _u64, C.POINTER(_vp)], _i32),
+    "dos_mlp_destroy": ([_vp], None),
+    "dos_mlp_param_count": ([_vp, _P64], _i32),
+    "dos_mlp_get_params": ([_vp, _vp, _vp], _i32),
+    "dos_mlp_set_params": ([_vp, _vp, _vp], _i32),
+    "dos_mlp_forward": ([_vp, _vp, _i32, _vp, _vp], _i32),
+    "dos_mlp_loss_grad": ([_vp, _vp, _vp, _i32, _vp, _vp, _vp], _i32),
+    "dos_mlp_train_step": ([_vp, _vp, _vp, _vp, _i32, C.c_float, _vp, _vp], _i32),
+    "dos_mlp_features": ([_vp, _i32, _vp, _i32, _i32, _i64, _vp, _vp], _i32),
+    "dos_hist_normalize": ([_vp, _i32, _i64, _vp, _vp], _i32),
 }
 
 
@@ -172,6 +183,29 @@ class Filter:
     def close(self):
         if self._h is not None and self._h.value:
             lib().dos_filter_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Mlp:
+    """Owned dos_mlp_t handle (density-reconstruction network)."""
+
+    def __init__(self, handle: int, sizes):
+        self._h = C.c_void_p(handle)
+        self.sizes = [int(x) for x in sizes]
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            lib().dos_mlp_destroy(self._h)
         self._h = None
 
     def __del__(self):
@@ -387,3 +421,129 @@ def density_with_spikes(d: torch.Tensor, g: Graph, n_bins: int, filter: Filter |
     zeros = removed + (info["n_isolated"] if count_isolated else 0)
     spikes = [(0.0, zeros / n_total)] if zeros else []
     return dos_density(d, n_bins, kernel=kernel, scale=r / n_total, spikes=spikes, stream=stream)
+
+
+# ---------------------------------------------------------------------------
+# batched density and the density-reconstruction network
+# ---------------------------------------------------------------------------
+def dos_density_batched(d: torch.Tensor, n_bins: int, kernel: str = "jackson",
+                        hist_out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Per-graph histograms (n_graphs, n_bins) from moments d (n_graphs, M), float64 CUDA."""
+    _need_cuda(d, torch.float64, "d")
+    ng, M = d.shape
+    if hist_out is None:
+        hist_out = torch.empty((ng, n_bins), dtype=torch.float64, device=d.device)
+    _need_cuda(hist_out, torch.float64, "hist_out", ng * n_bins)
+    _check(lib().dos_density_batched(_ptr(d), int(M), int(ng), int(n_bins), KERNEL[kernel], _ptr(hist_out),
+                                     _stream(stream)))
+    return hist_out
+
+
+def dos_mlp_create(sizes, seed: int = 0) -> Mlp:
+    """Network sizes[0] -> ... -> sizes[-1] (ReLU hidden layers, softmax output)."""
+    arr = (C.c_int * len(sizes))(*[int(x) for x in sizes])
+    out = C.c_void_p()
+    _check(lib().dos_mlp_create(len(sizes) - 1, arr, int(seed) & (2**64 - 1), C.byref(out)))
+    return Mlp(out.value, sizes)
+
+
+def dos_mlp_destroy(net: Mlp):
+    net.close()
+
+
+def dos_mlp_param_count(net: Mlp) -> int:
+    n = C.c_int64()
+    _check(lib().dos_mlp_param_count(net.handle, C.byref(n)))
+    return n.value
+
+
+def _dev():
+    return torch.device("cuda", torch.cuda.current_device())
+
+
+def dos_mlp_get_params(net: Mlp, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    n = dos_mlp_param_count(net)
+    if out is None:
+        out = torch.empty(n, dtype=torch.float32, device=_dev())
+    _need_cuda(out, torch.float32, "out", n)
+    _check(lib().dos_mlp_get_params(net.handle, _ptr(out), _stream(stream)))
+    return out
+
+
+def dos_mlp_set_params(net: Mlp, params: torch.Tensor, stream=None):
+    _need_cuda(params, torch.float32, "params", dos_mlp_param_count(net))
+    _check(lib().dos_mlp_set_params(net.handle, _ptr(params), _stream(stream)))
+
+
+def dos_mlp_forward(net: Mlp, x: torch.Tensor, probs: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Softmax output (rows, sizes[-1]) for features x (rows, sizes[0])."""
+    _need_cuda(x, torch.float32, "x")
+    rows = x.shape[0]
+    if x.numel() != rows * net.sizes[0]:
+        raise ValueError("x must have shape (rows, sizes[0])")
+    if probs is None:
+        probs = torch.empty((rows, net.sizes[-1]), dtype=torch.float32, device=x.device)
+    _need_cuda(probs, torch.float32, "probs", rows * net.sizes[-1])
+    _check(lib().dos_mlp_forward(net.handle, _ptr(x), int(rows), _ptr(probs), _stream(stream)))
+    return probs
+
+
+def dos_mlp_loss_grad(net: Mlp, x: torch.Tensor, t: torch.Tensor, stream=None):
+    """(loss float32[1], flat gradient float32[param_count]) on the device."""
+    _need_cuda(x, torch.float32, "x")
+    _need_cuda(t, torch.float32, "t")
+    rows = x.shape[0]
+    if x.numel() != rows * net.sizes[0] or t.numel() != rows * net.sizes[-1]:
+        raise ValueError("x and t must have shapes (rows, sizes[0]) and (rows, sizes[-1])")
+    loss = torch.empty(1, dtype=torch.float32, device=x.device)
+    grad = torch.empty(dos_mlp_param_count(net), dtype=torch.float32, device=x.device)
+    _check(lib().dos_mlp_loss_grad(net.handle, _ptr(x), _ptr(t), int(rows), _ptr(loss), _ptr(grad),
+                                   _stream(stream)))
+    return loss, grad
+
+
+def dos_mlp_train_step(net: Mlp, x: torch.Tensor, t: torch.Tensor, lr: float, idx: torch.Tensor | None = None,
+                       loss: torch.Tensor | None = None, stream=None) -> torch.Tensor | None:
+    """One Adam step on rows idx (int32 CUDA tensor; None = all rows of x)."""
+    _need_cuda(x, torch.float32, "x")
+    _need_cuda(t, torch.float32, "t")
+    n_rows = x.shape[0]
+    if x.numel() != n_rows * net.sizes[0] or t.numel() != n_rows * net.sizes[-1]:
+        raise ValueError("x and t must have shapes (rows, sizes[0]) and (rows, sizes[-1])")
+    if idx is not None:
+        _need_cuda(idx, torch.int32, "idx")
+        rows = idx.numel()
+    else:
+        rows = n_rows
+    if loss is not None:
+        _need_cuda(loss, torch.float32, "loss", 1)
+    _check(lib().dos_mlp_train_step(net.handle, _ptr(x), _ptr(t), _ptr(idx), int(rows), float(lr), _ptr(loss),
+                                    _stream(stream)))
+    return loss
+
+
+def dos_mlp_features(hist: torch.Tensor, d: torch.Tensor, K: int, x_out: torch.Tensor | None = None,
+                     stream=None) -> torch.Tensor:
+    """Feature rows [n_bins * hist, d_1 .. d_{K-1}] (n_graphs, n_bins + K - 1), float32."""
+    _need_cuda(hist, torch.float64, "hist")
+    _need_cuda(d, torch.float64, "d")
+    ng, B = hist.shape
+    if d.shape[0] != ng or d.shape[1] < K:
+        raise ValueError("d must have shape (n_graphs, >= K)")
+    if x_out is None:
+        x_out = torch.empty((ng, B + K - 1), dtype=torch.float32, device=hist.device)
+    _need_cuda(x_out, torch.float32, "x_out", ng * (B + K - 1))
+    _check(lib().dos_mlp_features(_ptr(hist), int(B), _ptr(d), int(d.shape[1]), int(K), int(ng), _ptr(x_out),
+                                  _stream(stream)))
+    return x_out
+
+
+def dos_hist_normalize(hist: torch.Tensor, t_out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Clip negative bins and renormalise each row to sum 1 (float32 targets)."""
+    _need_cuda(hist, torch.float64, "hist")
+    ng, B = hist.shape
+    if t_out is None:
+        t_out = torch.empty((ng, B), dtype=torch.float32, device=hist.device)
+    _need_cuda(t_out, torch.float32, "t_out", ng * B)
+    _check(lib().dos_hist_normalize(_ptr(hist), int(B), int(ng), _ptr(t_out), _stream(stream)))
+    return t_out

@@ -23,7 +23,7 @@ __device__ double jackson_g(int m, int M) {
   return ((M - m + 1.0) * cos(a * m) + sin(a * m) / tan(a)) / (M + 1.0);
 }
 
-// One CTA per bin b: thread i sums the terms m = i, i + blockDim, ... of
+// One CTA per bin b (and per graph blockIdx.y of a batch): thread i sums the terms m = i, i + blockDim, ... of
 //   coef[m] (sin(m theta_a) - sin(m theta_b))   (m >= 1; theta_a - theta_b for m = 0),
 // coef[m] folding the damping, the factor 2 of the m >= 1 terms and the
 // 1/(m pi) of the exact bin integral; the partial sums are combined in a
@@ -32,6 +32,8 @@ __global__ void __launch_bounds__(256) k_density(const double* __restrict__ d, i
                                                  Spikes sp, double* __restrict__ h) {
   __shared__ double red[256];
   const int b = blockIdx.x;
+  d += static_cast<size_t>(blockIdx.y) * M;  // graph blockIdx.y of a batch
+  h += static_cast<size_t>(blockIdx.y) * B;
   const double w = 2.0 / B;
   const double lo = -1.0 + w * b;
   const double hi = b + 1 == B ? 1.0 : -1.0 + w * (b + 1);
@@ -90,5 +92,24 @@ extern "C" int dos_density(const double* d, int M, int n_bins, int kernel, doubl
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   k_density<<<n_bins, 256, 0, s>>>(d, M, n_bins, kernel, scale, sp, hist_out);
   NDOS_LAUNCHED();
+  return DOS_OK;
+}
+
+extern "C" int dos_density_batched(const double* d, int M, int64_t n_graphs, int n_bins, int kernel,
+                                   double* hist_out, void* stream) {
+  clear_error();
+  if (!d || !hist_out) return fail(DOS_EINVAL, "dos_density_batched: null pointer");
+  if (M < 1 || M > (1 << 20)) return fail(DOS_EINVAL, "dos_density_batched: M must be in [1, 2^20]");
+  if (n_bins < 1 || n_bins > (1 << 20)) return fail(DOS_EINVAL, "dos_density_batched: n_bins must be in [1, 2^20]");
+  if (n_graphs < 1) return fail(DOS_EINVAL, "dos_density_batched: n_graphs must be >= 1");
+  if (kernel != DOS_KERNEL_NONE && kernel != DOS_KERNEL_JACKSON) return fail(DOS_EINVAL, "dos_density_batched: kernel");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  constexpr int64_t kMaxY = 65535;
+  for (int64_t g0 = 0; g0 < n_graphs; g0 += kMaxY) {
+    const int64_t ng = n_graphs - g0 < kMaxY ? n_graphs - g0 : kMaxY;
+    k_density<<<dim3(n_bins, static_cast<unsigned>(ng)), 256, 0, s>>>(d + g0 * M, M, n_bins, kernel, 1.0, Spikes{},
+                                                                       hist_out + g0 * n_bins);
+    NDOS_LAUNCHED();
+  }
   return DOS_OK;
 }

@@ -58,3 +58,14 @@ def test_adam_first_step_is_lr_times_sign():
     p, m, v = oracle.adam_step(params, grads, zero, zero, 1, 0.01)
     assert abs(p[0][0][0, 0] - (1.0 - 0.01 * 2.0 / (2.0 + 1e-8))) < 1e-12
     assert abs(p[0][1][0] - (0.5 + 0.01 * 3.0 / (3.0 + 1e-8))) < 1e-12
+
+
+def test_features_hand_example():
+    # two bins with masses 0.25 / 0.75 -> densities 0.5 / 1.5; moments d_1 only
+    x = oracle.mlp_features([[0.25, 0.75]], [[1.0, 0.5, 0.1]], 2)
+    assert np.array_equal(x, [[0.5, 1.5, 0.5]])
+
+
+def test_normalize_hist_hand_example():
+    t = oracle.normalize_hist([[-0.1, 0.3, 0.1], [-1.0, 0.0, -2.0]])
+    assert np.allclose(t, [[0.0, 0.75, 0.25], [1 / 3, 1 / 3, 1 / 3]], rtol=0, atol=1e-15)
