@@ -64,6 +64,23 @@ def step_bytes(n: int, nnz: int, nz: int, ldos: bool) -> float:
     return b + (4.0 * n if ldos else 0.0)
 
 
+def max_over_ranks(dist, values, device):
+    """Each timing's maximum over all ranks (the slowest replica sets the
+    job's time); identity without a process group."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def whole_job_gbs(world: int, bytes_per_rank: float, seconds: float) -> float:
+    """Whole-job GB/s: every rank moved bytes_per_rank in `seconds` (max over ranks)."""
+    return world * bytes_per_rank / seconds / 1e9
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -222,17 +239,15 @@ def run_ours(args):
         torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / max(1, args.steps // 2)
 
-    if dist is not None:
-        t = torch.tensor([ms, e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, e2e_s = float(t[0]), float(t[1])
+    batched = None if args.no_batched else measure_batched(seed, dev, dist)
+    ms, e2e_s = max_over_ranks(dist, [ms, e2e_s], dev)
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return
 
     ms_step = ms / args.steps
-    value = world * bytes_step / (ms_step * 1e-3) / 1e9
+    value = whole_job_gbs(world, bytes_step, ms_step * 1e-3)
     peak, peak_kind = load_peaks()
     per_launch_bytes = (bytes_dos + bytes_ldos) / ((M // 2) + (M - 1))
     avg_launch_ms = step_ms_total / max(1, step_launches)
@@ -253,7 +268,7 @@ def run_ours(args):
         "config": dict(WORKLOAD, n_compact=n, nnz=nnz, plan=plan, parallelism=f"replicas{world}"),
         "roofline": {
             "bound": "hbm",
-            "kernel": "k_cheb_step (fused Chebyshev step, DOS and LDOS launches)",
+            "kernel": "fused Chebyshev step: k_cheb_light + k_cheb_medium + k_cheb_heavy (DOS and LDOS launches)",
             "achieved": round(achieved, 1),
             "peak": peak,
             "peak_kind": f"{peak_kind} hbm_gbs",
@@ -266,7 +281,7 @@ def run_ours(args):
             "share_of_step": round(step_ms_total / ms, 4) if ms > 0 else None,
         },
         "e2e": {
-            "value": round(world * bytes_step / e2e_s / 1e9, 2),
+            "value": round(whole_job_gbs(world, bytes_step, e2e_s), 2),
             "unit": "GB/s",
             "h2d_bytes_per_step": int(src_h.numel() * 8 * 2),
             "d2h_bytes_per_step": int(c_host.numel() * 4 + small_host.numel() * 8),
@@ -275,6 +290,8 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
+    if batched is not None:
+        out["batched"] = batched
     if not args.no_time_to_l1:
         out["time_to_l1"] = time_to_l1(src_d, dst_d, n_nodes, seed)
     if not args.no_cpu_baseline:
@@ -282,6 +299,63 @@ def run_ours(args):
     print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# many small graphs: the 4096-graph batch as one block-diagonal operator
+# ---------------------------------------------------------------------------
+BATCH = {"graphs": 4096, "n_min": 200, "n_max": 20000, "M": 200, "Nz": 16,
+         "models": "ER / BA m in [2,15] / Chung-Lu gamma in [2.1,3.0], mean degree U[4,30]"}
+
+
+def measure_batched(seed, dev, dist, calls: int = 10, warmup: int = 3) -> dict:
+    """Per-graph DOS moments of 4096 uneven graphs (one captured CUDA graph
+    per call, autotuned plan): whole-call time and algorithmic GB/s of its
+    M/2 fused steps over the union."""
+    import torch
+
+    import paper_1905_09758_gb300 as nd
+    import synthgraphs as sg
+
+    graphs = [(s, d, n) for s, d, n, _ in sg.batch_graphs(BATCH["graphs"], seed + 4096, BATCH["n_min"],
+                                                           BATCH["n_max"])]
+    src, dst, offs = sg.union(graphs)
+    del graphs
+    g = nd.dos_build_csr_batched(torch.from_numpy(src), torch.from_numpy(dst), offs)
+    n_edges = int(src.size)
+    del src, dst
+    info = g.info()
+    tune = nd.dos_autotune(g, BATCH["Nz"])
+    m, nz = BATCH["M"], BATCH["Nz"]
+    d = torch.empty((BATCH["graphs"], m), dtype=torch.float64, device=dev)
+    for _ in range(warmup):
+        nd.dos_moments_batched(g, m, nz, seed, d_out=d)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(calls):
+        nd.dos_moments_batched(g, m, nz, seed, d_out=d)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(dist, [ev0.elapsed_time(ev1) / calls], dev)[0]
+    world = dist.get_world_size() if dist is not None else 1
+    bytes_call = (m // 2) * step_bytes(info["n"], info["nnz"], nz, False)
+    return {
+        "workload": f"batch_{BATCH['graphs']}_graphs",
+        **BATCH,
+        "n_edges": n_edges,
+        "n_compact": info["n"],
+        "nnz": info["nnz"],
+        "plan": tune,
+        "ms_per_call": round(ms, 3),
+        "graphs_per_s": round(world * BATCH["graphs"] / (ms * 1e-3), 1),
+        "value": round(whole_job_gbs(world, bytes_call, ms * 1e-3), 2),
+        "unit": "GB/s",
+        "timed": "dos_moments_batched replays (CSR resident): init + M/2 fused steps + per-graph moments",
+    }
 
 
 # ---------------------------------------------------------------------------
@@ -306,7 +380,7 @@ def time_to_l1(src_d, dst_d, n_nodes, seed, target=1e-2):
     h_ref = run("fp32", 256, M, seed + 99991).cpu().numpy()
     sweep = []
     for prec in ("fp32", "fp16", "bf16"):
-        for m in (200, M):
+        for m in (50, 100, 200, M):
             for nz in (8, 16, 32, 64):
                 run(prec, nz, m, seed)  # warm
                 torch.cuda.synchronize()
@@ -418,6 +492,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-time-to-l1", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--ref-steps-per-sample", type=int, default=3)
     args = ap.parse_args()

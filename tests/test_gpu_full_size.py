@@ -1,0 +1,129 @@
+"""Parity at full workload sizes, in the launch configuration the benchmark
+times (automatic plan), against the FP64 oracle.
+
+* Chung-Lu 1M + 50k twin-leaf pairs (1.1M nodes, 2.0e7 nonzeros): CSR and
+  twin classes bit-exact; filtered DOS moments (M = 10) and LDOS moments
+  (M = 4, every node) on the benchmark's 64 probes, where the oracle still
+  finishes in seconds; at the benchmark's M = 500, properties that hold at any
+  size (d_0 = 1, |d_m| <= d_0, doubled and direct recurrences agree).
+* The 4096-graph batch (N uniform in [200, 20000], ER / BA / Chung-Lu mix,
+  ~4e7 nodes): per-graph moments at M = 200, Nz = 16 with the autotuned plan,
+  sampled graphs checked one by one against the oracle run on that graph alone.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synthgraphs as sg
+
+pytestmark = pytest.mark.gpu
+
+nd = pytest.importorskip("paper_1905_09758_gb300")
+
+TOL_D = 1e-5
+TOL_C = 1e-4
+SEED = 2025
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1905_09758_gb300.build import build
+
+    build()
+    nd.dos_set_plan(0, 0)
+    yield
+    nd.dos_set_plan(0, 0)
+
+
+@pytest.fixture(scope="module")
+def chung_lu_1m():
+    s, d, n = sg.chung_lu(1_000_000, 2.5, 20.0, SEED)
+    s, d, n = sg.add_twin_leaves(s, d, n, 50_000, SEED + 1)
+    ref = oracle.build_csr(s, d, n)
+    g = nd.dos_build_csr(torch.from_numpy(s).cuda(), torch.from_numpy(d).cuda(), n)
+    return s, d, n, ref, g
+
+
+def test_full_csr_and_twin_classes_bit_exact(chung_lu_1m):
+    _, _, n, ref, g = chung_lu_1m
+    info = g.info()
+    assert (info["n"], info["nnz"], info["n_isolated"]) == (ref.n, ref.nnz, ref.n_isolated)
+    assert ref.n == 1_099_818 and ref.nnz == 20_159_636
+    ex = {k: v.cpu().numpy() for k, v in nd.dos_graph_export(g).items()}
+    for key, want in (("row_ptr", ref.row_ptr), ("col", ref.col), ("deg", ref.deg), ("inv_sqrt_deg", ref.s64),
+                      ("inv_sqrt_deg32", ref.s32), ("old_id", ref.old_id)):
+        assert np.array_equal(ex[key], want), key
+    f = nd.dos_motif_filter(g)
+    cid_ref, removed = oracle.twin_classes(ref)
+    assert np.array_equal(nd.dos_filter_export(f).cpu().numpy(), cid_ref)
+    assert f.info()["removed"] == removed
+
+
+def test_full_filtered_dos_moments(chung_lu_1m):
+    _, _, _, ref, g = chung_lu_1m
+    nz, m = 64, 10
+    f = nd.dos_motif_filter(g)
+    d = nd.dos_moments(g, m, nz, SEED, filter=f).cpu().numpy()
+    cid, removed = oracle.twin_classes(ref)
+    z = oracle.project_probes(oracle.probes(SEED, ref.old_id, nz), cid)
+    d_ref = oracle.kpm_doubled(ref, z, m) / ((ref.n - removed) * nz)
+    assert np.abs(d - d_ref).max() <= TOL_D
+
+
+def test_full_ldos_every_node(chung_lu_1m):
+    _, _, _, ref, g = chung_lu_1m
+    nz, m = 64, 4
+    c, dl = nd.ldos_moments(g, m, nz, SEED + 7)
+    z = oracle.probes(SEED + 7, ref.old_id, nz)
+    mu, cref = oracle.kpm_direct(ref, z, m, ldos=True)
+    c = c.cpu().numpy()
+    assert np.all(c[0] == 1.0)
+    assert np.abs(c.T - cref).max() <= TOL_C
+    assert np.abs(dl.cpu().numpy() - mu / (ref.n * nz)).max() <= TOL_D
+
+
+def test_full_m500_properties(chung_lu_1m):
+    """At the benchmark's M = 500: d_0 = 1 (Rademacher probes), |d_m| <= d_0
+    (||T_m(H)|| <= 1 on the spectrum, so |z^T T_m(H) z| <= ||z||^2), and the
+    doubled recurrence (dos_moments) agrees with the direct one (the LDOS
+    run's column sums) on the same probes.  FP32 rounding of a stable
+    three-term recurrence grows about linearly in m; 1e-4 covers m = 500."""
+    _, _, _, ref, g = chung_lu_1m
+    m, nz = 500, 64
+    d = nd.dos_moments(g, m, nz, SEED).cpu().numpy()
+    _, dl = nd.ldos_moments(g, m, nz, SEED)
+    dl = dl.cpu().numpy()
+    assert abs(d[0] - 1.0) < 1e-12 and abs(dl[0] - 1.0) < 1e-12
+    assert np.all(np.abs(d) <= 1.0 + 1e-6) and np.all(np.abs(dl) <= 1.0 + 1e-6)
+    diff = np.abs(d - dl)
+    print(f"M=500 doubled vs direct: max |diff| {diff.max():.2e}")
+    assert diff.max() <= 1e-4
+
+
+def test_full_batch_of_4096_graphs_sampled():
+    graphs = [(s, d, n) for s, d, n, _ in sg.batch_graphs(4096, 4096)]
+    src, dst, offs = sg.union(graphs)
+    g = nd.dos_build_csr_batched(torch.from_numpy(src), torch.from_numpy(dst), offs)
+    del src, dst
+    info = nd.dos_batch_info(g)
+    assert info["n_graphs"] == 4096
+    nd.dos_autotune(g, 16)
+    m, nz, seed = 200, 16, 77
+    d = nd.dos_moments_batched(g, m, nz, seed).cpu().numpy()
+    # second call replays the captured graph: same values
+    d2 = nd.dos_moments_batched(g, m, nz, seed).cpu().numpy()
+    assert np.abs(d - d2).max() <= 1e-12
+    sizes = np.diff(offs)
+    rng = np.random.default_rng(1)
+    pick = sorted({int(np.argmin(sizes)), int(np.argmax(sizes)), *rng.choice(4096, 6, replace=False).tolist()})
+    for k in pick:
+        s, dd, n = graphs[k]
+        ref = oracle.build_csr(s, dd, n)
+        assert info["graph_n"][k] == ref.n and info["graph_isolated"][k] == ref.n_isolated
+        z = oracle.probes(seed, ref.old_id.astype(np.int64) + int(offs[k]), nz)
+        d_ref = oracle.kpm_doubled(ref, z, m) / (ref.n * nz)
+        assert np.abs(d[k] - d_ref).max() <= TOL_D, k
+    assert np.all(np.abs(d[:, 0] - 1.0) < 1e-9)
