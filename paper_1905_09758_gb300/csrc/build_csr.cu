@@ -6,6 +6,7 @@
 #include <cub/device/device_scan.cuh>
 #include <cub/device/device_select.cuh>
 
+#include <string>
 #include <vector>
 
 #include "common.cuh"
@@ -93,6 +94,31 @@ __global__ void k_deg_sort_key(const int32_t* __restrict__ deg, int64_t n, uint3
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
     key[k] = 0x7fffffffu - static_cast<uint32_t>(deg[k]);
+    idx[k] = static_cast<int32_t>(k);
+  }
+}
+
+// Batch order: heavy rows (degree >= kHeavyDeg) first by degree, then medium
+// and light rows, each class grouped by graph and degree-descending inside a
+// graph.  Rows processed together then gather from one graph's block of U_k
+// (a few MB, L2-resident) instead of from the whole batch.
+__global__ void k_batch_sort_key(const int32_t* __restrict__ deg, const int32_t* __restrict__ old_id, int64_t n,
+                                 const int64_t* __restrict__ node_off, int64_t n_graphs, uint64_t* __restrict__ key,
+                                 int32_t* __restrict__ idx) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = old_id[k];
+    int64_t lo = 0, hi = n_graphs - 1;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi + 1) >> 1;
+      if (node_off[mid] <= o) lo = mid; else hi = mid - 1;
+    }
+    const uint64_t d = static_cast<uint64_t>(deg[k]);
+    if (d >= static_cast<uint64_t>(kHeavyDeg))
+      key[k] = 0x7fffffffull - d;
+    else
+      key[k] = ((d >= static_cast<uint64_t>(kMediumDeg) ? 1ull : 2ull) << 62) | (static_cast<uint64_t>(lo) << 11) |
+               (2047ull - d);
     idx[k] = static_cast<int32_t>(k);
   }
 }
@@ -201,8 +227,10 @@ int sort_keys_u64(uint64_t*& keys, uint64_t*& alt, int64_t n, int end_bit, Temps
 
 }  // namespace
 
+// node_offset [host] (n_graphs + 1 entries) or NULL: with a batch, rows are
+// ordered graph by graph inside the medium and light classes
 static int build_csr_impl(const int64_t* src_in, const int64_t* dst_in, int64_t n_edges, int64_t n_nodes,
-                          uint32_t flags, cudaStream_t s, Graph* G) {
+                          uint32_t flags, const int64_t* node_offset, int64_t n_graphs, cudaStream_t s, Graph* G) {
   Temps t(s);
   const int64_t* src = src_in;
   const int64_t* dst = dst_in;
@@ -324,21 +352,36 @@ static int build_csr_impl(const int64_t* src_in, const int64_t* dst_in, int64_t 
   NDOS_CHECK(t.get(&n_heavy_d, 2));
   NDOS_CUDA(cudaMemsetAsync(n_heavy_d, 0, 2 * sizeof(unsigned long long), s));
   if (n > 0) {
-    uint32_t *dk = nullptr, *dk_alt = nullptr;
     int32_t *idx = nullptr, *idx_alt = nullptr;
-    NDOS_CHECK(t.get(&dk, n));
-    NDOS_CHECK(t.get(&dk_alt, n));
     NDOS_CHECK(t.get(&idx, n));
     NDOS_CHECK(t.get(&idx_alt, n));
-    k_deg_sort_key<<<grid_for(n), kThreads, 0, s>>>(G->deg, n, dk, idx);
-    NDOS_LAUNCHED();
-    cub::DoubleBuffer<uint32_t> kb(dk, dk_alt);
     cub::DoubleBuffer<int32_t> vb(idx, idx_alt);
     size_t bytes = 0;
-    NDOS_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, bytes, kb, vb, n, 0, 31, s));
     void* tmp = nullptr;
-    NDOS_CHECK(t.get(reinterpret_cast<char**>(&tmp), bytes));
-    NDOS_CUDA(cub::DeviceRadixSort::SortPairs(tmp, bytes, kb, vb, n, 0, 31, s));
+    if (node_offset && n_graphs > 1) {
+      uint64_t *bk = nullptr, *bk_alt = nullptr;
+      int64_t* off = nullptr;
+      NDOS_CHECK(t.get(&bk, n));
+      NDOS_CHECK(t.get(&bk_alt, n));
+      NDOS_CHECK(t.get(&off, n_graphs + 1));
+      NDOS_CUDA(cudaMemcpyAsync(off, node_offset, sizeof(int64_t) * (n_graphs + 1), cudaMemcpyHostToDevice, s));
+      k_batch_sort_key<<<grid_for(n), kThreads, 0, s>>>(G->deg, G->old_id, n, off, n_graphs, bk, idx);
+      NDOS_LAUNCHED();
+      cub::DoubleBuffer<uint64_t> kb(bk, bk_alt);
+      NDOS_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, bytes, kb, vb, n, 0, 64, s));
+      NDOS_CHECK(t.get(reinterpret_cast<char**>(&tmp), bytes));
+      NDOS_CUDA(cub::DeviceRadixSort::SortPairs(tmp, bytes, kb, vb, n, 0, 64, s));
+    } else {
+      uint32_t *dk = nullptr, *dk_alt = nullptr;
+      NDOS_CHECK(t.get(&dk, n));
+      NDOS_CHECK(t.get(&dk_alt, n));
+      k_deg_sort_key<<<grid_for(n), kThreads, 0, s>>>(G->deg, n, dk, idx);
+      NDOS_LAUNCHED();
+      cub::DoubleBuffer<uint32_t> kb(dk, dk_alt);
+      NDOS_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, bytes, kb, vb, n, 0, 31, s));
+      NDOS_CHECK(t.get(reinterpret_cast<char**>(&tmp), bytes));
+      NDOS_CUDA(cub::DeviceRadixSort::SortPairs(tmp, bytes, kb, vb, n, 0, 31, s));
+    }
     count_launch();
     NDOS_CUDA(cudaMemcpyAsync(G->p_compact, vb.Current(), sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
     int64_t* pdeg64 = nullptr;
@@ -364,8 +407,6 @@ static int build_csr_impl(const int64_t* src_in, const int64_t* dst_in, int64_t 
   }
   unsigned long long nh[2] = {0, 0};
   NDOS_CUDA(cudaMemcpyAsync(nh, n_heavy_d, sizeof(nh), cudaMemcpyDeviceToHost, s));
-  int32_t md = 0;
-  if (n > 0) NDOS_CUDA(cudaMemcpyAsync(&md, G->p_deg, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   NDOS_CUDA(cudaStreamSynchronize(s));
   G->n_heavy = static_cast<int64_t>(nh[0]);
   G->n_mid = static_cast<int64_t>(nh[1]);
@@ -376,6 +417,27 @@ static int build_csr_impl(const int64_t* src_in, const int64_t* dst_in, int64_t 
 }  // namespace netdos
 
 using namespace netdos;
+
+static int build_graph(const int64_t* src, const int64_t* dst, int64_t n_edges, int64_t n_nodes, uint32_t flags,
+                       const int64_t* node_offset, int64_t n_graphs, void* stream, dos_graph_t* out,
+                       const char* who) {
+  const std::string w(who);
+  if (n_edges < 0 || n_nodes < 0) return fail(DOS_EINVAL, w + ": negative size");
+  if (n_nodes > 0x7fffffffLL) return fail(DOS_EOVERFLOW, w + ": n_nodes exceeds 2^31 - 1");
+  if (n_edges > (1LL << 40)) return fail(DOS_EOVERFLOW, w + ": n_edges exceeds 2^40");
+  if (n_edges > 0 && (!src || !dst)) return fail(DOS_EINVAL, w + ": null edge arrays");
+  if (flags & ~static_cast<uint32_t>(DOS_INPUT_HOST)) return fail(DOS_EINVAL, w + ": unknown flags");
+  Graph* G = new Graph();
+  cudaGetDevice(&G->device);
+  int st = build_csr_impl(src, dst, n_edges, n_nodes, flags, node_offset, n_graphs, static_cast<cudaStream_t>(stream),
+                          G);
+  if (st != DOS_OK) {
+    dos_graph_destroy(reinterpret_cast<dos_graph_t>(G));
+    return st;
+  }
+  *out = reinterpret_cast<dos_graph_t>(G);
+  return DOS_OK;
+}
 
 static int tag_graphs(Graph* G, const int64_t* node_offset, int64_t n_graphs, cudaStream_t s) {
   Temps t(s);
@@ -426,7 +488,8 @@ extern "C" int dos_build_csr_batched(const int64_t* src, const int64_t* dst, int
   for (int64_t g = 0; g < n_graphs; ++g)
     if (node_offset[g + 1] < node_offset[g]) return fail(DOS_EINVAL, "dos_build_csr_batched: node_offset decreases");
   dos_graph_t h = nullptr;
-  NDOS_CHECK(dos_build_csr(src, dst, n_edges, node_offset[n_graphs], flags, stream, &h));
+  NDOS_CHECK(build_graph(src, dst, n_edges, node_offset[n_graphs], flags, node_offset, n_graphs, stream, &h,
+                         "dos_build_csr_batched"));
   Graph* G = reinterpret_cast<Graph*>(h);
   const int st = tag_graphs(G, node_offset, n_graphs, static_cast<cudaStream_t>(stream));
   if (st != DOS_OK) {
@@ -442,18 +505,5 @@ extern "C" int dos_build_csr(const int64_t* src, const int64_t* dst, int64_t n_e
   clear_error();
   if (!out) return fail(DOS_EINVAL, "dos_build_csr: out is NULL");
   *out = nullptr;
-  if (n_edges < 0 || n_nodes < 0) return fail(DOS_EINVAL, "dos_build_csr: negative size");
-  if (n_nodes > 0x7fffffffLL) return fail(DOS_EOVERFLOW, "dos_build_csr: n_nodes exceeds 2^31 - 1");
-  if (n_edges > (1LL << 40)) return fail(DOS_EOVERFLOW, "dos_build_csr: n_edges exceeds 2^40");
-  if (n_edges > 0 && (!src || !dst)) return fail(DOS_EINVAL, "dos_build_csr: null edge arrays");
-  if (flags & ~static_cast<uint32_t>(DOS_INPUT_HOST)) return fail(DOS_EINVAL, "dos_build_csr: unknown flags");
-  Graph* G = new Graph();
-  cudaGetDevice(&G->device);
-  int st = build_csr_impl(src, dst, n_edges, n_nodes, flags, static_cast<cudaStream_t>(stream), G);
-  if (st != DOS_OK) {
-    dos_graph_destroy(reinterpret_cast<dos_graph_t>(G));
-    return st;
-  }
-  *out = reinterpret_cast<dos_graph_t>(G);
-  return DOS_OK;
+  return build_graph(src, dst, n_edges, n_nodes, flags, nullptr, 0, stream, out, "dos_build_csr");
 }

@@ -187,9 +187,9 @@ int make_plan(const Graph* G, int Nz, int prec, int mode, Plan* out) {
   int smem = 0, ctas = 0;
   NDOS_CHECK(light_config(prec, pl.q, mode, &smem, &ctas));
   pl.smem = smem;
-  // two resident CTAs per SM measured best: more shared memory per SM leaves
-  // less L1 to hold the gathers in flight
-  ctas = std::min(ctas, force_ctas > 0 ? force_ctas : 2);
+  // at most three resident CTAs per SM (measured best on GB300 for t = 16
+  // and 32: more shared memory per SM leaves less L1 for gathers in flight)
+  ctas = std::min(ctas, force_ctas > 0 ? force_ctas : 3);
   const int64_t n_light = G->n - G->n_mid;
   const int64_t rounds = (n_light + 32 / pl.q - 1) / (32 / pl.q) * pl.tiles;
   pl.light_ctas = static_cast<int>(std::min<int64_t>(static_cast<int64_t>(std::max(1, ctas)) * sms,

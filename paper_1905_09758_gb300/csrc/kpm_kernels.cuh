@@ -16,12 +16,14 @@
 // Work is ordered tile-major, so the rows gathered by concurrently running
 // CTAs come from one tile of U_k.
 //
-// Rows are in degree-sorted order (heavy rows first).  Heavy rows get a CTA
-// each (k_cheb_heavy); light rows are processed by a persistent,
-// warp-specialised kernel that stages each chunk's contiguous data in shared
-// memory with TMA bulk copies (k_cheb_light).  A light row gets a group of
-// G = Q * P lanes: P neighbour slots, each slot Q lanes that read one 16-byte
-// chunk of the neighbour's tile row (t = Q * VEC probes).
+// Rows are relabelled by degree class: heavy rows (degree >= kHeavyDeg)
+// first, then medium (>= kMediumDeg), then light rows, degree-descending
+// inside a class (a batch of graphs groups the medium and light rows graph by
+// graph).  Heavy rows get a CTA each (k_cheb_heavy), medium rows a warp each
+// (k_cheb_medium); light rows go to a persistent kernel in which every warp
+// takes rounds of R = 32 / Q consecutive rows, Q lanes per row, each lane one
+// 16-byte chunk of the row's tile (t = Q * VEC probes), and stages the next
+// round's contiguous data in shared memory with bulk copies (k_cheb_light).
 #pragma once
 
 #include <cuda_bf16.h>
@@ -240,16 +242,36 @@ __device__ __forceinline__ void step_epilogue(const StepParams& prm, bool active
     prod0 += __shfl_xor_sync(0xffffffffu, prod0, s);
     if (MODE == kModeDos) prod1 += __shfl_xor_sync(0xffffffffu, prod1, s);
   }
+  if (MODE == kModeDos && prm.gid) {
+    // batch: per-graph sums.  Rows are grouped by graph, so a warp's rows
+    // nearly always share one graph: reduce in the warp and issue one atomic
+    // per dot instead of one per row (the rows of a graph all hit the same
+    // two addresses).
+    const int32_t g = active ? prm.gid[p] : -1;
+    const int32_t g0 = __shfl_sync(0xffffffffu, g, 0);
+    const bool uniform = __all_sync(0xffffffffu, !active || g == g0);
+    double a0 = active && owner ? static_cast<double>(fd * prod0) : 0.0;
+    double a1 = active && owner ? static_cast<double>(fd * prod1) : 0.0;
+    if (uniform) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+        a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+      }
+      if ((threadIdx.x & 31) == 0 && g0 >= 0) {
+        atomicAdd(prm.gpartial + g0, a0);
+        atomicAdd(prm.gpartial + prm.n_graphs + g0, a1);
+      }
+    } else if (active && owner) {
+      atomicAdd(prm.gpartial + g, a0);
+      atomicAdd(prm.gpartial + prm.n_graphs + g, a1);
+    }
+    return;
+  }
   if (active && owner) {
     if (MODE == kModeDos) {
-      if (prm.gid) {
-        const int32_t g = prm.gid[p];
-        atomicAdd(prm.gpartial + g, static_cast<double>(fd * prod0));
-        atomicAdd(prm.gpartial + prm.n_graphs + g, static_cast<double>(fd * prod1));
-      } else {
-        dd0 += static_cast<double>(fd * prod0);
-        dd1 += static_cast<double>(fd * prod1);
-      }
+      dd0 += static_cast<double>(fd * prod0);
+      dd1 += static_cast<double>(fd * prod1);
     } else {
       const float vsum = prod0 * sqrtf(fd);  // sum_j z_j (V_{k+1})_j of this tile
       dd0 += static_cast<double>(vsum);
