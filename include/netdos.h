@@ -348,6 +348,17 @@ int dos_mlp_features(const double* hist, int n_bins, const double* d,
                      int ld_d, int K, int64_t n_graphs, float* x_out,
                      void* stream);
 
+/* Density from the network's output: hist_out[r][b] = scale * probs[r][b]
+ * plus point masses (lambda, mass) pairs in `spikes` [host, n_spikes <= 16],
+ * placed as by dos_density (a point within 1e-9 of an interior bin edge
+ * splits evenly).  With a twin filter, scale = r / N and one spike at 0 of
+ * mass (removed + isolated) / N, as for the filtered series (§3.4).
+ *   probs [device] float[rows][n_bins]; hist_out [device] double[rows][n_bins].
+ * Errors: DOS_EINVAL. */
+int dos_hist_assemble(const float* probs, int n_bins, int64_t rows,
+                      double scale, const double* spikes, int n_spikes,
+                      double* hist_out, void* stream);
+
 /* Training targets: t_out[g][b] = max(hist[g][b], 0) / sum_b max(hist[g][b], 0)
  * (uniform if that sum is 0).  Errors: DOS_EINVAL. */
 int dos_hist_normalize(const double* hist, int n_bins, int64_t n_graphs,

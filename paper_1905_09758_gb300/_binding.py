@@ -79,6 +79,7 @@ _SIGNATURES = {
     "dos_mlp_train_step": ([_vp, _vp, _vp, _vp, _i32, C.c_float, _vp, _vp], _i32),
     "dos_mlp_features": ([_vp, _i32, _vp, _i32, _i32, _i64, _vp, _vp], _i32),
     "dos_hist_normalize": ([_vp, _i32, _i64, _vp, _vp], _i32),
+    "dos_hist_assemble": ([_vp, _i32, _i64, _dbl, _vp, _i32, _vp, _vp], _i32),
 }
 
 
@@ -547,3 +548,18 @@ def dos_hist_normalize(hist: torch.Tensor, t_out: torch.Tensor | None = None, st
     _need_cuda(t_out, torch.float32, "t_out", ng * B)
     _check(lib().dos_hist_normalize(_ptr(hist), int(B), int(ng), _ptr(t_out), _stream(stream)))
     return t_out
+
+
+def dos_hist_assemble(probs: torch.Tensor, scale: float = 1.0, spikes=(), hist_out: torch.Tensor | None = None,
+                      stream=None) -> torch.Tensor:
+    """float64 histograms scale * probs + point masses (spikes: (lambda, mass) pairs)."""
+    _need_cuda(probs, torch.float32, "probs")
+    rows, B = probs.shape
+    if hist_out is None:
+        hist_out = torch.empty((rows, B), dtype=torch.float64, device=probs.device)
+    _need_cuda(hist_out, torch.float64, "hist_out", rows * B)
+    sp = [float(x) for pair in spikes for x in pair]
+    arr = (C.c_double * max(1, len(sp)))(*sp)
+    _check(lib().dos_hist_assemble(_ptr(probs), int(B), int(rows), float(scale), arr if sp else None, len(sp) // 2,
+                                   _ptr(hist_out), _stream(stream)))
+    return hist_out

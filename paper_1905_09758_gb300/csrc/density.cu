@@ -1,7 +1,9 @@
 // dos_density: damped spectral histogram from Chebyshev moments (§2.2
 // spectral histogram, Eq. (7)-(8) dual basis and expansion, §4.1 Jackson
 // damping), plus point masses for the filtered spikes.
+#include <algorithm>
 #include <cmath>
+#include <string>
 
 #include "common.cuh"
 
@@ -15,6 +17,34 @@ struct Spikes {
   double lam[kMaxSpikes];
   double mass[kMaxSpikes];
 };
+
+// Mass that the point masses put into bin b of B equal bins over [-1, 1]: a
+// point within 1e-9 of an interior edge splits evenly between the two bins,
+// points at or beyond +-1 go to the end bins.
+__device__ double spike_mass(const Spikes& sp, int b, int B) {
+  const double w = 2.0 / B;
+  double v = 0.0;
+  for (int k = 0; k < sp.n; ++k) {
+    const double x = fmin(fmax(sp.lam[k], -1.0), 1.0);
+    const int e = static_cast<int>(rint((x + 1.0) / w));
+    if (e > 0 && e < B && fabs(x - (-1.0 + w * e)) <= 1e-9) {
+      if (b == e - 1 || b == e) v += 0.5 * sp.mass[k];
+    } else {
+      int bb = static_cast<int>(floor((x + 1.0) / w));
+      bb = bb < 0 ? 0 : (bb >= B ? B - 1 : bb);
+      if (b == bb) v += sp.mass[k];
+    }
+  }
+  return v;
+}
+
+// hist[r][b] = scale * probs[r][b] + spike masses (learned densities)
+__global__ void k_hist_assemble(const float* __restrict__ probs, int B, int64_t rows, double scale, Spikes sp,
+                                double* __restrict__ h) {
+  const int64_t total = rows * B;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
+    h[i] = scale * static_cast<double>(probs[i]) + spike_mass(sp, static_cast<int>(i % B), B);
+}
 
 // Jackson factor g_m for an M-term series (Jackson kernel of the KPM
 // literature): [(M-m+1) cos(pi m/(M+1)) + sin(pi m/(M+1)) cot(pi/(M+1))]/(M+1)
@@ -52,27 +82,25 @@ __global__ void __launch_bounds__(256) k_density(const double* __restrict__ d, i
     if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    double v = scale * red[0];
-    for (int k = 0; k < sp.n; ++k) {
-      const double x = fmin(fmax(sp.lam[k], -1.0), 1.0);
-      const int e = static_cast<int>(rint((x + 1.0) / w));
-      if (e > 0 && e < B && fabs(x - (-1.0 + w * e)) <= 1e-9) {
-        if (b == e - 1 || b == e) v += 0.5 * sp.mass[k];
-      } else {
-        int bb = static_cast<int>(floor((x + 1.0) / w));
-        bb = bb < 0 ? 0 : (bb >= B ? B - 1 : bb);
-        if (b == bb) v += sp.mass[k];
-      }
-    }
-    h[b] = v;
-  }
+  if (threadIdx.x == 0) h[b] = scale * red[0] + spike_mass(sp, b, B);
 }
 
 }  // namespace
 }  // namespace netdos
 
 using namespace netdos;
+
+static int read_spikes(const double* spikes, int n_spikes, Spikes* sp, const char* who) {
+  if (n_spikes < 0 || n_spikes > kMaxSpikes || (n_spikes > 0 && !spikes))
+    return fail(DOS_EINVAL, std::string(who) + ": at most 16 spikes");
+  *sp = Spikes{};
+  sp->n = n_spikes;
+  for (int k = 0; k < n_spikes; ++k) {
+    sp->lam[k] = spikes[2 * k];
+    sp->mass[k] = spikes[2 * k + 1];
+  }
+  return DOS_OK;
+}
 
 extern "C" int dos_density(const double* d, int M, int n_bins, int kernel, double scale, const double* spikes,
                            int n_spikes, double* hist_out, void* stream) {
@@ -81,14 +109,8 @@ extern "C" int dos_density(const double* d, int M, int n_bins, int kernel, doubl
   if (M < 1 || M > (1 << 20)) return fail(DOS_EINVAL, "dos_density: M must be in [1, 2^20]");
   if (n_bins < 1 || n_bins > (1 << 20)) return fail(DOS_EINVAL, "dos_density: n_bins must be in [1, 2^20]");
   if (kernel != DOS_KERNEL_NONE && kernel != DOS_KERNEL_JACKSON) return fail(DOS_EINVAL, "dos_density: kernel");
-  if (n_spikes < 0 || n_spikes > kMaxSpikes || (n_spikes > 0 && !spikes))
-    return fail(DOS_EINVAL, "dos_density: at most 16 spikes");
   Spikes sp{};
-  sp.n = n_spikes;
-  for (int k = 0; k < n_spikes; ++k) {
-    sp.lam[k] = spikes[2 * k];
-    sp.mass[k] = spikes[2 * k + 1];
-  }
+  NDOS_CHECK(read_spikes(spikes, n_spikes, &sp, "dos_density"));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   k_density<<<n_bins, 256, 0, s>>>(d, M, n_bins, kernel, scale, sp, hist_out);
   NDOS_LAUNCHED();
@@ -111,5 +133,19 @@ extern "C" int dos_density_batched(const double* d, int M, int64_t n_graphs, int
                                                                        hist_out + g0 * n_bins);
     NDOS_LAUNCHED();
   }
+  return DOS_OK;
+}
+
+extern "C" int dos_hist_assemble(const float* probs, int n_bins, int64_t rows, double scale, const double* spikes,
+                                 int n_spikes, double* hist_out, void* stream) {
+  clear_error();
+  if (!probs || !hist_out) return fail(DOS_EINVAL, "dos_hist_assemble: null pointer");
+  if (n_bins < 1 || n_bins > (1 << 20) || rows < 1) return fail(DOS_EINVAL, "dos_hist_assemble: bad sizes");
+  Spikes sp{};
+  NDOS_CHECK(read_spikes(spikes, n_spikes, &sp, "dos_hist_assemble"));
+  const int64_t total = rows * n_bins;
+  const unsigned blocks = static_cast<unsigned>(std::min<int64_t>((total + 255) / 256, 152 * 16));
+  k_hist_assemble<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(probs, n_bins, rows, scale, sp, hist_out);
+  NDOS_LAUNCHED();
   return DOS_OK;
 }

@@ -1,0 +1,103 @@
+"""Learned reconstruction of a graph's spectral density from few noisy moments.
+
+Not part of the paper's method: a small network (``dos_mlp_*``) maps the
+Jackson histogram and the first ``m_in`` moments of a cheap KPM run on the
+twin-filtered operator P^T H P (§3.4) to that operator's density over
+``bins`` equal bins of [-1, 1]; the filtered spike at 0 and the r/N scale are
+added afterwards exactly as for the plain filtered series.  It is trained on
+pairs (cheap run, accurate run: ``m_ref`` moments, ``nz_ref`` probes,
+independent seed) computed by the library on graphs of the family it will be
+used on.  Plain Jackson-damped KPM (``density_with_spikes``) is its fallback.
+
+This module only sequences calls of the C ABI (argument marshalling and the
+training loop's schedule); every computation runs in the library's kernels.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import torch
+
+from . import _binding as nd
+
+
+@dataclass
+class Reconstructor:
+    """A trained network and the settings its features were made with."""
+
+    net: nd.Mlp
+    m_in: int
+    nz_in: int
+    bins: int
+
+    @property
+    def sizes(self):
+        return self.net.sizes
+
+
+def filtered_operator(src, dst, n_nodes: int, stream=None):
+    """CSR handle and twin filter of an edge list (int64 tensors, CUDA or host)."""
+    src = torch.as_tensor(src, dtype=torch.int64)
+    dst = torch.as_tensor(dst, dtype=torch.int64)
+    g = nd.dos_build_csr(src, dst, n_nodes, stream=stream)
+    return g, nd.dos_motif_filter(g, stream=stream)
+
+
+def features(g: nd.Graph, f: nd.Filter | None, m_in: int, nz_in: int, seed: int, bins: int,
+             stream=None) -> torch.Tensor:
+    """Feature row (1, bins + m_in - 1) of a graph from a cheap filtered run."""
+    d = nd.dos_moments(g, m_in, nz_in, seed, filter=f, stream=stream)
+    h = nd.dos_density(d, bins, stream=stream)
+    return nd.dos_mlp_features(h.view(1, bins), d.view(1, m_in), m_in, stream=stream)
+
+
+def target(g: nd.Graph, f: nd.Filter | None, m_ref: int, nz_ref: int, seed: int, bins: int,
+           stream=None) -> torch.Tensor:
+    """Target row (1, bins): the accurate run's filtered density, clipped at 0
+    and normalised to unit mass."""
+    d = nd.dos_moments(g, m_ref, nz_ref, seed, filter=f, stream=stream)
+    h = nd.dos_density(d, bins, stream=stream)
+    return nd.dos_hist_normalize(h.view(1, bins), stream=stream)
+
+
+def training_set(graphs, m_in: int = 50, nz_in: int = 8, m_ref: int = 500, nz_ref: int = 256, bins: int = 200,
+                 seed: int = 0, stream=None):
+    """(X, T) for an iterable of edge lists (src, dst, n_nodes): one row per graph.
+    Graph k uses input seed seed + 2k and reference seed seed + 2k + 1."""
+    xs, ts = [], []
+    for k, (src, dst, n) in enumerate(graphs):
+        g, f = filtered_operator(src, dst, n, stream=stream)
+        xs.append(features(g, f, m_in, nz_in, seed + 2 * k, bins, stream=stream))
+        ts.append(target(g, f, m_ref, nz_ref, seed + 2 * k + 1, bins, stream=stream))
+    return torch.cat(xs).contiguous(), torch.cat(ts).contiguous()
+
+
+def train(x: torch.Tensor, t: torch.Tensor, m_in: int, nz_in: int, hidden=(512, 512), steps: int = 8000,
+          batch: int = 256, lr: float = 1e-3, lr_min: float = 1e-5, seed: int = 0, stream=None) -> Reconstructor:
+    """Adam on minibatches drawn uniformly with replacement, learning rate on a
+    cosine schedule from lr to lr_min."""
+    bins = t.shape[1]
+    net = nd.dos_mlp_create([x.shape[1], *hidden, bins], seed=seed)
+    gen = torch.Generator().manual_seed(seed)
+    idx = torch.randint(0, x.shape[0], (steps, batch), generator=gen, dtype=torch.int32).to(x.device)
+    for s in range(steps):
+        rate = lr_min + 0.5 * (lr - lr_min) * (1.0 + math.cos(math.pi * s / steps))
+        nd.dos_mlp_train_step(net, x, t, rate, idx=idx[s], stream=stream)
+    return Reconstructor(net, m_in, nz_in, bins)
+
+
+def reconstruct(rec: Reconstructor, g: nd.Graph, f: nd.Filter | None, seed: int, count_isolated: bool = True,
+                stream=None) -> torch.Tensor:
+    """Spectral histogram (float64 CUDA, rec.bins) of the whole graph: the
+    network's density of the filtered operator scaled by r / N_total, plus the
+    zero eigenvalues (removed twins, isolated nodes) as a point mass at 0."""
+    x = features(g, f, rec.m_in, rec.nz_in, seed, rec.bins, stream=stream)
+    p = nd.dos_mlp_forward(rec.net, x, stream=stream)
+    info = g.info()
+    removed = f.info()["removed"] if f is not None else 0
+    iso = info["n_isolated"] if count_isolated else 0
+    n_total = info["n"] + iso
+    zeros = removed + iso
+    spikes = [(0.0, zeros / n_total)] if zeros else []
+    return nd.dos_hist_assemble(p, scale=(info["n"] - removed) / n_total, spikes=spikes, stream=stream)[0]

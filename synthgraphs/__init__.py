@@ -42,6 +42,8 @@ __all__ = [
     "complete_bipartite",
     "path",
     "batch_graphs",
+    "chung_lu_twins_family",
+    "chung_lu_twins_member",
     "union",
 ]
 
@@ -268,3 +270,62 @@ def batch_graphs(count: int, seed: int, n_min: int = 200, n_max: int = 20000):
             s, d, nn = chung_lu(n, gam, md, gseed)
             desc = f"cl(n={n},gamma={gam:.2f},mean_deg={md:.2f})"
         yield s, d, nn, desc
+
+
+def _chung_lu_sorted(n: int, gamma: float, mean_degree: float, rng, i0: float = 10.0):
+    """Chung-Lu endpoint sampling as in chung_lu, drawn faster: each endpoint
+    list is found from sorted uniforms (a sequential search), then the second
+    list is randomly permuted.  Given the two endpoint multisets the pairing
+    is then uniformly random, as it is for independent pairs, so the edge
+    multiset has the same distribution (not the same draws) as chung_lu's.
+    Returns int32 endpoints."""
+    i = np.arange(n, dtype=np.float64)
+    w = (i + i0) ** (-1.0 / (gamma - 1.0))
+    w *= mean_degree * n / w.sum()
+    m = int(round(n * mean_degree / 2.0))
+    cdf = np.cumsum(w)
+    cdf /= cdf[-1]
+    u = rng.random(m)
+    u.sort()
+    src = np.minimum(np.searchsorted(cdf, u, side="right"), n - 1).astype(np.int32)
+    u = rng.random(m)
+    u.sort()
+    dst = rng.permutation(np.minimum(np.searchsorted(cdf, u, side="right"), n - 1).astype(np.int32))
+    return src, dst
+
+
+def chung_lu_twins_member(seed: int, n_min: int, n_max: int):
+    """One graph of the Chung-Lu-with-twins family (see chung_lu_twins_family),
+    as int32 edge lists (src, dst, n)."""
+    rng = _rng(seed)
+    n = int(rng.integers(n_min, n_max + 1))
+    gam = float(rng.uniform(2.1, 3.0))
+    md = float(rng.uniform(5.0, 30.0))
+    frac = float(rng.uniform(0.0, 0.1))
+    s, d = _chung_lu_sorted(n, gam, md, rng)
+    hosts = int(frac * n)
+    if hosts > 0:
+        live = np.zeros(n, bool)
+        nl = s != d
+        live[s[nl]] = True
+        live[d[nl]] = True
+        cand = np.nonzero(live)[0]
+        hosts = min(hosts, cand.size)
+        h = rng.choice(cand, size=hosts, replace=False).astype(np.int32)
+        leaves = n + np.arange(2 * hosts, dtype=np.int32)
+        s = np.concatenate([s, np.repeat(h, 2)])
+        d = np.concatenate([d, leaves])
+        n += 2 * hosts
+    return s, d, n
+
+
+def chung_lu_twins_family(count: int, seed: int, n_min: int = 10_000, n_max: int = 80_000):
+    """Training family for the learned reconstruction: Chung-Lu graphs with N
+    uniform in [n_min, n_max], exponent uniform in [2.1, 3.0], mean degree
+    uniform in [5, 30] (endpoints drawn as in _chung_lu_sorted), plus two
+    twin leaves on each of a fraction uniform in [0, 0.1] of N hosts drawn
+    among the non-isolated nodes.  Graph k is
+    chung_lu_twins_member(seed * 1_000_003 + k, ...), so members can be
+    generated independently (in parallel)."""
+    for k in range(count):
+        yield chung_lu_twins_member(seed * 1_000_003 + k, n_min, n_max)

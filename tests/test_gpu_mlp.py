@@ -265,3 +265,42 @@ def test_learned_reconstruction_beats_jackson_on_held_out_graphs():
     l1_mlp, l1_kpm = float(np.mean(l1_mlp)), float(np.mean(l1_kpm))
     print(f"held-out mean L1: learned {l1_mlp:.4f}, Jackson KPM {l1_kpm:.4f}")
     assert l1_mlp < 0.8 * l1_kpm
+
+
+def test_hist_assemble_matches_oracle():
+    rng = np.random.default_rng(4)
+    for b in (2, 7, 200):
+        p = rng.random((3, b)).astype(np.float32)
+        p /= p.sum(axis=1, keepdims=True)
+        spikes = [(0.0, 0.125), (-1.0, 0.01), (1.0 / np.sqrt(2), 0.02), (-0.5, 0.03)]
+        h = nd.dos_hist_assemble(torch.from_numpy(p).cuda(), scale=0.7, spikes=spikes).cpu().numpy()
+        pts = oracle.point_mass_histogram([s[0] for s in spikes], [s[1] for s in spikes], b)
+        ref = 0.7 * p.astype(np.float64) + pts
+        assert np.abs(h - ref).max() <= 1e-15
+
+
+def test_learned_reconstruct_assembles_filtered_density():
+    """learned.reconstruct = (r/N) * network output + zero spike, on a graph
+    with twins and isolated nodes; features equal the oracle's definition."""
+    from paper_1905_09758_gb300 import learned
+
+    s, d, n = sg.add_twin_leaves(*sg.chung_lu(3000, 2.5, 8.0, 5), 100, 6)
+    n += 7  # seven isolated nodes
+    g, f = learned.filtered_operator(torch.from_numpy(s), torch.from_numpy(d), n)
+    m_in, bins = 20, 40
+    net = nd.dos_mlp_create([bins + m_in - 1, 16, bins], seed=1)
+    rec = learned.Reconstructor(net, m_in, 4, bins)
+    h = learned.reconstruct(rec, g, f, seed=9).cpu().numpy()
+    x = learned.features(g, f, m_in, 4, 9, bins)
+    dd = nd.dos_moments(g, m_in, 4, 9, filter=f).cpu().numpy()
+    # the GPU histogram equals the oracle's to ~1e-12, so the float32 features
+    # agree to one rounding
+    x_ref = oracle.mlp_features(oracle.histogram(dd, bins)[None], dd[None], m_in)[0]
+    assert np.all(np.abs(x.cpu().numpy()[0] - x_ref) <= 2 * U * np.maximum(np.abs(x_ref), 1e-3))
+    p = nd.dos_mlp_forward(net, x).cpu().numpy()[0].astype(np.float64)
+    ref = oracle.build_csr(s, d, n)
+    _, removed = oracle.twin_classes(ref)
+    n_tot = ref.n + ref.n_isolated
+    want = (ref.n - removed) / n_tot * p + oracle.point_mass_histogram([0.0], [(removed + ref.n_isolated) / n_tot], bins)
+    assert np.abs(h - want).max() <= 1e-12
+    assert abs(h.sum() - 1.0) <= 1e-6
