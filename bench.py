@@ -81,6 +81,41 @@ def whole_job_gbs(world: int, bytes_per_rank: float, seconds: float) -> float:
     return world * bytes_per_rank / seconds / 1e9
 
 
+STEP_SOURCES = ("paper_1905_09758_gb300/csrc/kpm_kernels.cuh", "paper_1905_09758_gb300/csrc/kpm_f32.cu",
+                "paper_1905_09758_gb300/csrc/kpm.cu", "paper_1905_09758_gb300/csrc/common.cuh")
+TRAFFIC_PROFILE = "profiles/step_traffic_chung_lu_1M.md"
+
+
+def step_source_hash() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for rel in STEP_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def measured_traffic():
+    """DRAM bytes per fused step from the committed ncu summary, if it was
+    taken from the current step-kernel sources (else None)."""
+    path = os.path.join(ROOT, TRAFFIC_PROFILE)
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as f:
+        for line in f:
+            if line.startswith("- ") and ": " in line:
+                k, v = line[2:].split(": ", 1)
+                vals[k.strip()] = v.strip().strip("`")
+    if vals.get("step kernel sources sha256") != step_source_hash():
+        return None
+    try:
+        return float(vals["DRAM bytes per fused step (launch mix)"])
+    except (KeyError, ValueError):
+        return None
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -240,6 +275,7 @@ def run_ours(args):
     e2e_s = (time.perf_counter() - t0) / max(1, args.steps // 2)
 
     batched = None if args.no_batched else measure_batched(seed, dev, dist)
+    mixed = None if args.no_mixed else measure_mixed_precision(seed, dev, dist)
     ms, e2e_s = max_over_ranks(dist, [ms, e2e_s], dev)
     if rank != 0:
         if dist is not None:
@@ -274,7 +310,7 @@ def run_ours(args):
             "peak_kind": f"{peak_kind} hbm_gbs",
             "unit": "GB/s",
             "frac": round(achieved / peak, 4),
-            "traffic": None,
+            "traffic": measured_traffic(),
             "bytes_per_launch": round(per_launch_bytes),
             "avg_launch_ms": round(avg_launch_ms, 5),
             "launches": step_launches,
@@ -292,6 +328,8 @@ def run_ours(args):
     }
     if batched is not None:
         out["batched"] = batched
+    if mixed is not None:
+        out["mixed_precision"] = mixed
     if not args.no_time_to_l1:
         out["time_to_l1"] = time_to_l1(src_d, dst_d, n_nodes, seed, with_learned=not args.no_learned)
     if not args.no_cpu_baseline:
@@ -418,6 +456,64 @@ def time_to_l1(src_d, dst_d, n_nodes, seed, target=1e-2, with_learned=True):
         "plain_fp32_bench_setting": plain,
         "sweep": sweep,
     }
+
+
+# ---------------------------------------------------------------------------
+# mixed-precision probe storage on the Barabasi-Albert 20M-node graph
+# ---------------------------------------------------------------------------
+MIXED = {"graph": "Barabasi-Albert m=8, N=20,000,000 (1.6e8 edges)", "N": 20_000_000, "m": 8, "M": 1000, "Nz": 32}
+U_ROUND = {"bf16": 2.0 ** -8, "fp16": 2.0 ** -11}
+
+
+def measure_mixed_precision(seed, dev, dist, reps: int = 2) -> dict:
+    """DOS moments (M = 1000, Nz = 32, doubling: 500 fused steps) with FP32,
+    BF16 and FP16 probe storage on identical probes: average fused-step time
+    and algorithmic GB/s per storage type, and each low-precision run's
+    largest per-moment distance from the FP32 run."""
+    import torch
+
+    import paper_1905_09758_gb300 as nd
+    import synthgraphs as sg
+
+    src, dst, n_nodes = sg.barabasi_albert(MIXED["N"], MIXED["m"], seed + 20)
+    g = nd.dos_build_csr(torch.from_numpy(src), torch.from_numpy(dst), n_nodes)
+    del src, dst
+    info = g.info()
+    m, nz = MIXED["M"], MIXED["Nz"]
+    out = {"workload": "barabasi_albert_20M", **MIXED, "n_compact": info["n"], "nnz": info["nnz"], "storage": {}}
+    d32 = None
+    for prec in ("fp32", "bf16", "fp16"):
+        b = 4 if prec == "fp32" else 2
+        nd.dos_moments(g, m, nz, seed, prec=prec)  # warm (plan, attributes)
+        torch.cuda.synchronize()
+        best = None
+        for _ in range(reps):
+            nd.dos_profile_enable(True)
+            nd.dos_profile_read(reset=True)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record()
+            d = nd.dos_moments(g, m, nz, seed, prec=prec)
+            ev1.record()
+            torch.cuda.synchronize()
+            step_ms, launches = nd.dos_profile_read(reset=True)
+            nd.dos_profile_enable(False)
+            call_ms = ev0.elapsed_time(ev1)
+            if best is None or call_ms < best[0]:
+                best = (call_ms, step_ms / max(1, launches), d.cpu().numpy())
+        call_ms, step_avg, dm = best
+        bstep = 4.0 * info["nnz"] + 8.0 * (info["n"] + 1) + 4.0 * info["n"] + 3.0 * info["n"] * nz * b
+        row = {"call_ms": round(call_ms, 2), "avg_step_ms": round(step_avg, 4),
+               "step_gbs": round(bstep / (step_avg * 1e-3) / 1e9, 1), "plan": nd.dos_get_plan(g, nz, prec)}
+        if prec == "fp32":
+            d32 = dm
+        else:
+            diff = np.abs(dm - d32)
+            row["max_abs_diff_vs_fp32"] = float(f"{diff.max():.3e}")
+            row["max_diff_in_units_of_u"] = round(float(diff.max() / U_ROUND[prec]), 3)
+        out["storage"][prec] = row
+    out["note"] = ("identical probes; the small-graph tests bound |d - d_oracle| by 2u (u = 2^-8 BF16, 2^-11 FP16) "
+                   "against the FP64 oracle; here the distance to the FP32 run is reported")
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -564,6 +660,7 @@ def main():
     ap.add_argument("--no-time-to-l1", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--ref-steps-per-sample", type=int, default=3)
     args = ap.parse_args()
