@@ -31,6 +31,8 @@ __all__ = [
     "kpm_direct",
     "kpm_doubled",
     "twin_classes",
+    "closed_twin_classes",
+    "motif_classes",
     "project_probes",
     "jackson",
     "bin_edges",
@@ -287,6 +289,65 @@ def twin_classes(g: Csr):
         class_id[i] = first.setdefault(key, i)
     removed = int(g.n - len(first))
     return class_id, removed
+
+
+def closed_twin_classes(g: Csr):
+    """Classes of nodes with identical closed neighbourhoods N[i] = N(i) + {i}.
+
+    Such nodes i != j are adjacent (j is in N[i]) and share the degree d; for
+    them H (e_i - e_j) = -(e_i - e_j) / d (A (e_i - e_j) = e_j - e_i), so each
+    class of size c carries c - 1 eigenvalues -1/d on localized eigenvectors
+    (the lambda = -1/d motifs of §3.4, Fig. 3; d = 2: the triangle with two
+    degree-2 nodes, lambda = -1/2).  Exact relation: equal sorted closed
+    neighbour lists.
+    Returns class_id int32[N] (smallest member), the removed count
+    sum (c - 1), and {d: number of eigenvalues at -1/d}.
+    """
+    class_id = np.arange(g.n, dtype=np.int32)
+    first: dict[bytes, int] = {}
+    rp, col = g.row_ptr, g.col
+    for i in range(g.n):
+        nb = col[rp[i]:rp[i + 1]]
+        key = np.sort(np.append(nb, np.int32(i))).astype(np.int32).tobytes()
+        class_id[i] = first.setdefault(key, i)
+    removed = int(g.n - len(first))
+    spikes: dict[int, int] = {}
+    for i in np.nonzero(class_id != np.arange(g.n))[0]:
+        d = int(rp[i + 1] - rp[i])
+        spikes[d] = spikes.get(d, 0) + 1
+    return class_id, removed, spikes
+
+
+def motif_classes(g: Csr, open_twins: bool = True, closed_twins: bool = True):
+    """Open- and closed-twin classes together (§3.4).
+
+    The relations are disjoint: if N(i) = N(j) and N[i] = N[k] (k != i), then k
+    is in N(i) = N(j), so j ~ k, while j would have to lie in N[k] = N[i],
+    which holds neither j (not adjacent to i) nor i's other members.  So every
+    node is in at most one nontrivial class and one class-mean projection
+    filters both kinds.  Returns class_id, the removed count and the removed
+    eigenvalues as a list of (lambda, count) sorted by lambda.
+    """
+    ident = np.arange(g.n, dtype=np.int32)
+    cid = ident.copy()
+    removed = 0
+    spikes = []
+    in_open = np.zeros(g.n, bool)
+    if open_twins:
+        oc, r0 = twin_classes(g)
+        in_open = np.bincount(oc, minlength=g.n)[oc] >= 2
+        cid = np.where(in_open, oc, cid)
+        removed += r0
+        if r0:
+            spikes.append((0.0, r0))
+    if closed_twins:
+        cc, r1, sp = closed_twin_classes(g)
+        in_closed = np.bincount(cc, minlength=g.n)[cc] >= 2
+        assert not np.any(in_open & in_closed)
+        cid = np.where(in_closed, cc, cid)
+        removed += r1
+        spikes.extend((-1.0 / d, c) for d, c in sp.items())
+    return cid, removed, sorted(spikes)
 
 
 def project_probes(z: np.ndarray, class_id: np.ndarray) -> np.ndarray:

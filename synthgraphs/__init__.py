@@ -36,9 +36,11 @@ __all__ = [
     "chung_lu",
     "barabasi_albert",
     "add_twin_leaves",
+    "add_triangle_twins",
     "cycle",
     "complete",
     "star",
+    "windmill",
     "complete_bipartite",
     "path",
     "batch_graphs",
@@ -191,6 +193,37 @@ def add_twin_leaves(src, dst, n: int, n_hosts: int, seed: int):
     new_src = np.concatenate([src, np.repeat(hosts, 2)])
     new_dst = np.concatenate([dst, leaves])
     return new_src, new_dst, n + 2 * int(n_hosts)
+
+
+def add_triangle_twins(src, dst, n: int, n_hosts: int, seed: int):
+    """Hang a triangle on each of ``n_hosts`` hosts: two new nodes a, b joined
+    to the host and to each other.  a and b then have equal closed
+    neighbourhoods (the lambda = -1/2 motif of §3.4, Fig. 3).  Hosts are drawn
+    without replacement among the nodes with a non-loop edge; host k's new
+    nodes get ids n + 2k and n + 2k + 1.  Returns the extended edge list and
+    n + 2 * n_hosts.
+    """
+    rng = _rng(seed)
+    src = np.asarray(src, np.int64)
+    dst = np.asarray(dst, np.int64)
+    live = np.zeros(n, bool)
+    nl = src != dst
+    live[src[nl]] = True
+    live[dst[nl]] = True
+    hosts = rng.choice(np.nonzero(live)[0], size=int(n_hosts), replace=False).astype(np.int64)
+    a = n + 2 * np.arange(n_hosts, dtype=np.int64)
+    b = a + 1
+    new_src = np.concatenate([src, hosts, hosts, a])
+    new_dst = np.concatenate([dst, a, b, b])
+    return new_src, new_dst, n + 2 * int(n_hosts)
+
+
+def windmill(k: int):
+    """Windmill (friendship) graph: k triangles sharing the centre 0; outer
+    pair (2t+1, 2t+2) of each triangle are closed twins of degree 2."""
+    t = np.arange(k, dtype=np.int64)
+    a, b = 2 * t + 1, 2 * t + 2
+    return np.concatenate([np.zeros(k, np.int64), np.zeros(k, np.int64), a]), np.concatenate([a, b, b]), 2 * k + 1
 
 
 # ---------------------------------------------------------------------------

@@ -191,3 +191,70 @@ def test_filtered_density_recovers_spectrum_better():
     h_filt += oracle.point_mass_histogram([0.0], [removed / g.n], nb)
     assert abs(h_filt.sum() - 1.0) < 1e-12
     assert oracle.l1(h_filt, h_ex) < oracle.l1(h_plain, h_ex)
+
+
+# ---- closed twins (lambda = -1/d) -------------------------------------------
+def _remove_eigs(lam, spikes, tol=1e-9):
+    """spec(H) minus `count` copies of each spike value."""
+    keep = np.ones(lam.size, bool)
+    for x, c in spikes:
+        hit = np.nonzero(np.abs(lam - x) < tol)[0]
+        assert hit.size >= c, (x, c, hit.size)
+        keep[hit[:c]] = False
+    return lam[keep]
+
+
+def test_complete_graph_is_one_closed_class():
+    # K_n: spectrum {1, -1/(n-1) x (n-1)}, every node a closed twin of every other
+    for n in (2, 3, 7):
+        g = oracle.build_csr(*sg.complete(n))
+        cid, removed, spikes = oracle.closed_twin_classes(g)
+        assert np.all(cid == 0) and removed == n - 1 and spikes == {n - 1: n - 1}
+        lam, _ = oracle.exact_eigs(g)
+        assert np.sum(np.abs(lam + 1.0 / (n - 1)) < 1e-9) == n - 1
+
+
+def test_windmill_pairs_give_minus_half():
+    g = oracle.build_csr(*sg.windmill(5))
+    cid, removed, spikes = oracle.motif_classes(g)
+    assert removed == 5 and spikes == [(-0.5, 5)]
+    assert list(cid) == [0, 1, 1, 3, 3, 5, 5, 7, 7, 9, 9]
+    # spectrum {-1/2 x (k+1), 1/2 x (k-1), 1}: k of the -1/2 are localized on
+    # the twin pairs, one lives on the symmetric part and must stay
+    lam, _ = oracle.exact_eigs(g)
+    assert np.sum(np.abs(lam + 0.5) < 1e-9) == 6
+    p = _p_matrix(cid)
+    lam_r = np.linalg.eigvalsh(p.T @ oracle.dense_h(g) @ p)
+    assert np.allclose(np.sort(lam_r), np.sort(_remove_eigs(lam, spikes)), atol=1e-9)
+    assert np.sum(np.abs(lam_r + 0.5) < 1e-9) == 1
+
+
+def test_star_leaves_are_open_not_closed_twins():
+    g = oracle.build_csr(*sg.star(6))
+    assert oracle.closed_twin_classes(g)[1] == 0
+    assert oracle.motif_classes(g)[2] == [(0.0, 5)]
+
+
+def test_open_and_closed_filter_projection_spectrum():
+    src, dst, n = sg.chung_lu(300, 2.3, 4.0, 51)
+    src, dst, n = sg.add_twin_leaves(src, dst, n, 15, 52)
+    src, dst, n = sg.add_triangle_twins(src, dst, n, 12, 53)
+    g = oracle.build_csr(src, dst, n)
+    cid, removed, spikes = oracle.motif_classes(g)
+    sp = dict(spikes)
+    assert sp[-0.5] >= 12 and sp[0.0] >= 15 and removed == sum(sp.values())
+    lam, _ = oracle.exact_eigs(g)
+    p = _p_matrix(cid)
+    h = oracle.dense_h(g)
+    # the class-constant subspace is invariant: P P^T commutes with H
+    ppt = p @ p.T
+    assert np.allclose(ppt @ h, h @ ppt, atol=1e-12)
+    lam_r = np.linalg.eigvalsh(p.T @ h @ p)
+    assert lam_r.size == g.n - removed
+    assert np.allclose(np.sort(lam_r), np.sort(_remove_eigs(lam, spikes)), atol=1e-9)
+
+
+def test_closed_filter_on_graph_without_motifs_is_identity():
+    g = oracle.build_csr(*sg.cycle(9))
+    cid, removed, spikes = oracle.motif_classes(g)
+    assert removed == 0 and spikes == [] and np.array_equal(cid, np.arange(9))
