@@ -276,6 +276,7 @@ def run_ours(args):
 
     batched = None if args.no_batched else measure_batched(seed, dev, dist)
     mixed = None if args.no_mixed else measure_mixed_precision(seed, dev, dist)
+    motifs = None if args.no_motifs else measure_motifs(seed)
     ms, e2e_s = max_over_ranks(dist, [ms, e2e_s], dev)
     if rank != 0:
         if dist is not None:
@@ -330,6 +331,8 @@ def run_ours(args):
         out["batched"] = batched
     if mixed is not None:
         out["mixed_precision"] = mixed
+    if motifs is not None:
+        out["motif_filters"] = motifs
     if not args.no_time_to_l1:
         out["time_to_l1"] = time_to_l1(src_d, dst_d, n_nodes, seed, with_learned=not args.no_learned)
     if not args.no_cpu_baseline:
@@ -517,6 +520,51 @@ def measure_mixed_precision(seed, dev, dist, reps: int = 2) -> dict:
 
 
 # ---------------------------------------------------------------------------
+# motif filters: open twins (lambda = 0) and closed twins (lambda = -1/d)
+# ---------------------------------------------------------------------------
+MOTIFS = {"graph": "Chung-Lu gamma=2.5 mean_deg=20 N=1,000,000 + 50,000 twin-leaf pairs + 50,000 triangle twins",
+          "M": 100, "Nz": 16, "M_ref": 2000, "Nz_ref": 64, "bins": BINS}
+
+
+def measure_motifs(seed, reps: int = 3) -> dict:
+    """Filter time (open twins; open + closed twins) and the density's L1
+    distance at M = 100 to an unfiltered M = 2000 reference (independent
+    seed), without a filter, with open twins, and with both."""
+    import torch
+
+    import paper_1905_09758_gb300 as nd
+    import synthgraphs as sg
+
+    src, dst, n = sg.chung_lu(N_BASE, GAMMA, MEAN_DEG, seed)
+    src, dst, n = sg.add_twin_leaves(src, dst, n, N_TWIN_HOSTS, seed + 1)
+    src, dst, n = sg.add_triangle_twins(src, dst, n, 50_000, seed + 2)
+    g = nd.dos_build_csr(torch.from_numpy(src).cuda(), torch.from_numpy(dst).cuda(), n)
+    m, nz = MOTIFS["M"], MOTIFS["Nz"]
+    d_ref = nd.dos_moments(g, MOTIFS["M_ref"], MOTIFS["Nz_ref"], seed + 777)
+    h_ref = nd.density_with_spikes(d_ref, g, BINS).cpu().numpy()
+    out = {"workload": "chung_lu_1M_open_and_closed_twins", **MOTIFS, "n_compact": g.info()["n"],
+           "nnz": g.info()["nnz"], "filters": {}}
+    for name, motifs in (("none", None), ("open", ("open",)), ("open+closed", ("open", "closed"))):
+        times = []
+        f = None
+        for _ in range(reps if motifs else 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            f = nd.dos_motif_filter_ex(g, motifs) if motifs else None
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+        d = nd.dos_moments(g, m, nz, seed, filter=f)
+        h = nd.density_with_spikes(d, g, BINS, filter=f).cpu().numpy()
+        row = {"l1": round(float(np.abs(h - h_ref).sum()), 5)}
+        if motifs:
+            info = f.info()
+            row.update(filter_ms=round(1e3 * statistics.median(times), 2), removed=info["removed"],
+                       classes=info["n_classes"], spikes=[[round(x, 6), c] for x, c in nd.dos_filter_spikes(f)[:8]])
+        out["filters"][name] = row
+    return out
+
+
+# ---------------------------------------------------------------------------
 # learned reconstruction: trained on a graph family, applied to the workload
 # ---------------------------------------------------------------------------
 LEARN = {"train_graphs": 1600, "family": "Chung-Lu gamma U[2.1,3.0], mean degree U[5,30], N U[1e4,8e4], "
@@ -661,6 +709,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-motifs", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--ref-steps-per-sample", type=int, default=3)
     args = ap.parse_args()

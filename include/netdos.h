@@ -121,6 +121,39 @@ void dos_graph_destroy(dos_graph_t g);
  */
 int dos_motif_filter(dos_graph_t g, void* stream, dos_filter_t* out);
 
+/* Motif sets of dos_motif_filter_ex (bit mask). */
+enum {
+  DOS_MOTIF_OPEN_TWINS = 1,   /* N(i) = N(j): eigenvalue 0 (Fig. 3a) */
+  DOS_MOTIF_CLOSED_TWINS = 2  /* N[i] = N[j] (adjacent, degree d): eigenvalue -1/d */
+};
+
+/*
+ * dos_motif_filter_ex -- twin-motif classes for a set of motifs.
+ * Paper: §3.4 (Fig. 3: motifs with localized eigenvectors; detection by
+ * hashing; filtering by Z_r = P P^T Z).  Closed twins are nodes with equal
+ * closed neighbourhoods N[i] = N(i) + {i}; they are adjacent, share the degree
+ * d, and each class of size c carries c - 1 eigenvalues -1/d on the vectors
+ * e_i - e_j (d = 2: the triangle with two degree-2 nodes, -1/2).  The open
+ * and closed relations are disjoint, so the classes of both are filtered by
+ * one class-mean projection; dos_filter_info's removed counts both, and
+ * dos_filter_spikes lists the removed eigenvalues.  Hash collisions are
+ * resolved by exact comparison.
+ *   motifs  DOS_MOTIF_OPEN_TWINS | DOS_MOTIF_CLOSED_TWINS (nonzero).
+ *   out     receives the filter handle.  Synchronises `stream`.
+ * Errors: DOS_EINVAL (g NULL, empty or unknown motif set), DOS_ENOMEM,
+ * DOS_ECUDA.  dos_motif_filter(g, ...) = dos_motif_filter_ex(g,
+ * DOS_MOTIF_OPEN_TWINS, ...).
+ */
+int dos_motif_filter_ex(dos_graph_t g, uint32_t motifs, void* stream,
+                        dos_filter_t* out);
+
+/* Removed eigenvalues [host]: up to `capacity` pairs (lambda, count) in
+ * ascending lambda (0 for open twins, -1/d per degree d with closed twins);
+ * *n_spikes (may be NULL) receives the total number of pairs.
+ * Errors: DOS_EINVAL. */
+int dos_filter_spikes(dos_filter_t f, double* spikes, int capacity,
+                      int* n_spikes);
+
 /* Filter summary [host outputs; any may be NULL]: removed = sum over classes
  * of (size - 1) = number of eigenvalues at 0 the filter takes out,
  * n_classes = classes of size >= 2, r = N - removed. */
@@ -185,7 +218,7 @@ int ldos_moments(dos_graph_t g, int M, int Nz, uint64_t seed, int prec,
  *   spikes   [host] double[2 * n_spikes] pairs (lambda, mass) added as point
  *            masses (a point on an interior bin edge splits evenly between
  *            the two bins; +-1 go to the end bins); NULL if n_spikes == 0.
- *            n_spikes <= 16.  M <= 2^20.
+ *            n_spikes <= 64.  M <= 2^20.
  *   hist_out [device] double[B]: bin b gets
  *            scale * (g_0 d_0 I_0b + 2 sum_{m>=1} g_m d_m I_mb) + spikes,
  *            I_mb = integral over bin b of T_m(x) / (pi sqrt(1 - x^2)) dx.
@@ -349,7 +382,7 @@ int dos_mlp_features(const double* hist, int n_bins, const double* d,
                      void* stream);
 
 /* Density from the network's output: hist_out[r][b] = scale * probs[r][b]
- * plus point masses (lambda, mass) pairs in `spikes` [host, n_spikes <= 16],
+ * plus point masses (lambda, mass) pairs in `spikes` [host, n_spikes <= 64],
  * placed as by dos_density (a point within 1e-9 of an interior bin edge
  * splits evenly).  With a twin filter, scale = r / N and one spike at 0 of
  * mass (removed + isolated) / N, as for the filtered series (§3.4).

@@ -20,6 +20,7 @@ DOS_OK, DOS_EINVAL, DOS_ENOMEM, DOS_ECUDA, DOS_ETIMEOUT, DOS_EOVERFLOW = range(6
 PREC = {"fp32": 0, "bf16": 1, "fp16": 2}
 KERNEL = {"none": 0, "jackson": 1}
 DOS_INPUT_HOST = 1
+MOTIF = {"open": 1, "closed": 2}
 
 _STATUS_NAMES = {
     DOS_EINVAL: "DOS_EINVAL",
@@ -51,6 +52,8 @@ _SIGNATURES = {
     "dos_graph_export": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp], _i32),
     "dos_graph_destroy": ([_vp], None),
     "dos_motif_filter": ([_vp, _vp, C.POINTER(_vp)], _i32),
+    "dos_motif_filter_ex": ([_vp, _u32, _vp, C.POINTER(_vp)], _i32),
+    "dos_filter_spikes": ([_vp, _vp, _i32, _PI], _i32),
     "dos_filter_info": ([_vp, _P64, _P64, _P64], _i32),
     "dos_filter_export": ([_vp, _vp, _vp], _i32),
     "dos_filter_destroy": ([_vp], None),
@@ -302,9 +305,29 @@ def dos_graph_export(g: Graph, stream=None) -> dict:
 
 
 def dos_motif_filter(g: Graph, stream=None) -> Filter:
+    """Open-twin (lambda = 0) classes of the graph."""
     out = C.c_void_p()
     _check(lib().dos_motif_filter(g.handle, _stream(stream), C.byref(out)))
     return Filter(out.value, g)
+
+
+def dos_motif_filter_ex(g: Graph, motifs=("open", "closed"), stream=None) -> Filter:
+    """Twin classes for a set of motifs: "open" (lambda = 0), "closed" (lambda = -1/d)."""
+    mask = 0
+    for m in motifs:
+        mask |= MOTIF[m]
+    out = C.c_void_p()
+    _check(lib().dos_motif_filter_ex(g.handle, mask, _stream(stream), C.byref(out)))
+    return Filter(out.value, g)
+
+
+def dos_filter_spikes(f: Filter) -> list:
+    """Removed eigenvalues as [(lambda, count)], ascending lambda."""
+    n = C.c_int()
+    _check(lib().dos_filter_spikes(f.handle, None, 0, C.byref(n)))
+    buf = (C.c_double * max(1, 2 * n.value))()
+    _check(lib().dos_filter_spikes(f.handle, buf, n.value, None))
+    return [(buf[2 * k], int(buf[2 * k + 1])) for k in range(n.value)]
 
 
 def dos_filter_info(f: Filter) -> dict:
@@ -411,17 +434,27 @@ def density_with_spikes(d: torch.Tensor, g: Graph, n_bins: int, filter: Filter |
     """Histogram of the whole graph from moments d of the (filtered) operator.
 
     With a twin filter, d are the moments of P^T H P (r = N - removed
-    eigenvalues); the removed eigenvalues sit at 0 (§3.4).  Nodes without edges
-    contribute eigenvalue 0 too.  The series part is scaled by r / N_total and
-    the zero eigenvalues are added as one point mass at 0.
+    eigenvalues); the removed eigenvalues sit at 0 (open twins) and at -1/d
+    (closed twins of degree d) (§3.4).  Nodes without edges contribute
+    eigenvalue 0 too.  The series part is scaled by r / N_total and every
+    removed eigenvalue value becomes a point mass (count / N_total).
     """
+    scale, spikes = filtered_scale_and_spikes(g, filter, count_isolated)
+    return dos_density(d, n_bins, kernel=kernel, scale=scale, spikes=spikes, stream=stream)
+
+
+def filtered_scale_and_spikes(g: Graph, filter: Filter | None = None, count_isolated: bool = True):
+    """(r / N_total, [(lambda, count / N_total)]): the weight of the filtered
+    operator's density and the point masses of the eigenvalues it leaves out
+    (filtered twins, and isolated nodes at 0 when counted)."""
     info = g.info()
-    n_total = info["n"] + (info["n_isolated"] if count_isolated else 0)
+    iso = info["n_isolated"] if count_isolated else 0
+    n_total = info["n"] + iso
     removed = filter.info()["removed"] if filter is not None else 0
-    r = info["n"] - removed
-    zeros = removed + (info["n_isolated"] if count_isolated else 0)
-    spikes = [(0.0, zeros / n_total)] if zeros else []
-    return dos_density(d, n_bins, kernel=kernel, scale=r / n_total, spikes=spikes, stream=stream)
+    removed_eigs = dict(dos_filter_spikes(filter)) if filter is not None else {}
+    removed_eigs[0.0] = removed_eigs.get(0.0, 0) + iso
+    spikes = [(lam, c / n_total) for lam, c in sorted(removed_eigs.items()) if c]
+    return (info["n"] - removed) / n_total, spikes
 
 
 # ---------------------------------------------------------------------------

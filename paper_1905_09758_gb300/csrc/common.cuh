@@ -8,6 +8,7 @@
 
 #include <atomic>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "netdos.h"
@@ -138,6 +139,9 @@ struct Filter {
   // (-1 for singletons) and the class size
   int32_t* p_slot = nullptr;    // [n]
   int32_t* slot_size = nullptr; // [n_classes]
+  // removed eigenvalues (lambda, count), ascending lambda: 0 for open twins,
+  // -1/d for closed twins of degree d
+  std::vector<std::pair<double, int64_t>> spikes;
 };
 
 constexpr int kHeavyDeg = 2048;  // rows at or above this degree get a whole CTA

@@ -10,7 +10,7 @@
 namespace netdos {
 namespace {
 
-constexpr int kMaxSpikes = 16;
+constexpr int kMaxSpikes = 64;
 
 struct Spikes {
   int n;
@@ -92,7 +92,7 @@ using namespace netdos;
 
 static int read_spikes(const double* spikes, int n_spikes, Spikes* sp, const char* who) {
   if (n_spikes < 0 || n_spikes > kMaxSpikes || (n_spikes > 0 && !spikes))
-    return fail(DOS_EINVAL, std::string(who) + ": at most 16 spikes");
+    return fail(DOS_EINVAL, std::string(who) + ": at most 64 spikes");
   *sp = Spikes{};
   sp->n = n_spikes;
   for (int k = 0; k < n_spikes; ++k) {

@@ -1,15 +1,24 @@
-// dos_motif_filter: classes of nodes with identical neighbourhoods, the
-// lambda = 0 twin motif of §3.4 (Fig. 3a).
+// dos_motif_filter / dos_motif_filter_ex: classes of nodes with identical
+// neighbourhoods (§3.4, Fig. 3).
+//   open twins    N(i) = N(j):  eigenvectors e_i - e_j with eigenvalue 0;
+//   closed twins  N[i] = N[j] (N[i] = N(i) + {i}, so i ~ j and d_i = d_j = d):
+//                 A (e_i - e_j) = e_j - e_i, eigenvalue -1/d of H.
+// The two relations are disjoint (a node in a nontrivial open class has no
+// closed twin), so one class id per node and one class-mean projection of
+// the probes filters both.
 //
 // Detection follows the paper's hashing idea with an integer hash: each node
-// gets h_i = mix(d_i) + sum_{j in N(i)} mix(j) (mod 2^64), an order-free
-// function of its neighbour set, so twins always share a hash.  Nodes are
-// sorted by hash (stable in the node id); inside each run of equal hashes the
-// neighbour lists are compared exactly, so a hash collision never merges
-// different neighbourhoods.  Class id = smallest member (compact id).
+// gets h_i = mix(d_i) + sum_{j in N(i)} mix(j) (+ mix(i) for closed
+// neighbourhoods) (mod 2^64), an order-free function of the neighbour set, so
+// twins always share a hash.  Nodes are sorted by hash (stable in the node
+// id); inside each run of equal hashes the neighbour lists are compared
+// exactly, so a hash collision never merges different neighbourhoods.  Class
+// id = smallest member (compact id).
 #include <cub/device/device_radix_sort.cuh>
 #include <cub/device/device_scan.cuh>
 
+#include <algorithm>
+#include <utility>
 #include <vector>
 
 #include "common.cuh"
@@ -19,9 +28,10 @@ namespace {
 
 __device__ __forceinline__ uint64_t mix_id(uint64_t x) { return splitmix64(0x5bd1e9955bd1e995ull, x); }
 
-// warp per row: order-free neighbourhood hash
+// warp per row: order-free hash of the open (closed = 0) or closed (1)
+// neighbourhood
 __global__ void k_row_hash(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-                           const int32_t* __restrict__ deg, int64_t n, uint64_t* __restrict__ hash,
+                           const int32_t* __restrict__ deg, int64_t n, int closed, uint64_t* __restrict__ hash,
                            int32_t* __restrict__ idx) {
   const int lane = threadIdx.x & 31;
   const int64_t w0 = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
@@ -32,6 +42,7 @@ __global__ void k_row_hash(const int64_t* __restrict__ row_ptr, const int32_t* _
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xffffffffu, h, o);
     if (lane == 0) {
+      if (closed) h += mix_id(static_cast<uint64_t>(i)) + 0x9e3779b97f4a7c15ull;
       hash[i] = h + mix_id(0x8000000000000000ull | static_cast<uint64_t>(deg[i]));
       idx[i] = static_cast<int32_t>(i);
     }
@@ -61,11 +72,35 @@ __device__ __forceinline__ bool same_list(const int64_t* row_ptr, const int32_t*
   return true;
 }
 
+// N[a] = N[b] for a != b: a ~ b and N(a) - {b} = N(b) - {a} (sorted lists)
+__device__ __forceinline__ bool same_closed_list(const int64_t* row_ptr, const int32_t* col, int32_t a, int32_t b) {
+  const int64_t ba = row_ptr[a], bb = row_ptr[b];
+  const int64_t la = row_ptr[a + 1] - ba, lb = row_ptr[b + 1] - bb;
+  if (la != lb) return false;
+  bool adjacent = false;
+  int64_t i = 0, j = 0;
+  while (i < la || j < lb) {
+    if (i < la && col[ba + i] == b) {
+      adjacent = true;
+      ++i;
+      continue;
+    }
+    if (j < lb && col[bb + j] == a) {
+      ++j;
+      continue;
+    }
+    if (i >= la || j >= lb || col[ba + i] != col[bb + j]) return false;
+    ++i;
+    ++j;
+  }
+  return adjacent;
+}
+
 // warp per run: repeated leader election in id order; every unassigned member
 // equal to the leader joins its class
 __global__ void k_resolve_runs(const uint64_t* __restrict__ h, const int32_t* __restrict__ node, int64_t n,
                                const int64_t* __restrict__ run_start, int64_t n_runs,
-                               const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                               const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col, int closed,
                                int32_t* class_id) {
   const int lane = threadIdx.x & 31;
   const int64_t w0 = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
@@ -81,11 +116,41 @@ __global__ void k_resolve_runs(const uint64_t* __restrict__ h, const int32_t* __
       if (lane == 0) class_id[ln] = ln;
       for (int64_t k = lead + 1 + lane; k < b; k += 32) {
         const int32_t m = node[k];
-        if (*reinterpret_cast<volatile int32_t*>(class_id + m) == -1 && same_list(row_ptr, col, ln, m))
+        if (*reinterpret_cast<volatile int32_t*>(class_id + m) == -1 &&
+            (closed ? same_closed_list(row_ptr, col, ln, m) : same_list(row_ptr, col, ln, m)))
           class_id[m] = ln;
       }
       __syncwarp();
     }
+  }
+}
+
+__global__ void k_iota(int32_t* __restrict__ x, int64_t n) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    x[i] = static_cast<int32_t>(i);
+}
+
+// class sizes of one relation
+__global__ void k_sizes(const int32_t* __restrict__ cid, int64_t n, int32_t* __restrict__ size) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    atomicAdd(&size[cid[i]], 1);
+}
+
+// merge the closed classes into the open ones (disjoint relations) and count
+// the removed closed-twin eigenvalues -1/d per degree d
+__global__ void k_merge_closed(int32_t* __restrict__ class_id, const int32_t* __restrict__ open_size,
+                               const int32_t* __restrict__ closed_id, const int32_t* __restrict__ closed_size,
+                               const int32_t* __restrict__ deg, int64_t n, unsigned long long* __restrict__ per_deg,
+                               int* __restrict__ conflict) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int32_t c = closed_id[i];
+    if (closed_size[c] < 2) continue;
+    if (open_size[class_id[i]] >= 2) atomicOr(conflict, 1);  // cannot happen (disjoint relations)
+    class_id[i] = c;
+    if (c != i) atomicAdd(&per_deg[deg[i]], 1ull);
   }
 }
 
@@ -133,7 +198,46 @@ inline unsigned grid_for(int64_t work, int per_block = 256) {
 
 }  // namespace
 
-static int motif_filter_impl(const Graph* G, cudaStream_t s, Filter* F) {
+// Classes of one relation (open: closed = 0, closed: 1) into cid[n]: the
+// smallest member of each node's class, its own id if it has no twin.
+static int find_classes(const Graph* G, int closed, int32_t* cid, Temps& t) {
+  const int64_t n = G->n;
+  cudaStream_t s = t.s;
+  uint64_t *h = nullptr, *h_alt = nullptr;
+  int32_t *idx = nullptr, *idx_alt = nullptr;
+  int64_t* run_start = nullptr;
+  unsigned long long* n_runs_d = nullptr;
+  NDOS_CHECK(t.get(&h, n));
+  NDOS_CHECK(t.get(&h_alt, n));
+  NDOS_CHECK(t.get(&idx, n));
+  NDOS_CHECK(t.get(&idx_alt, n));
+  NDOS_CHECK(t.get(&run_start, n));
+  NDOS_CHECK(t.get(&n_runs_d, 1));
+  NDOS_CUDA(cudaMemsetAsync(n_runs_d, 0, sizeof(unsigned long long), s));
+  k_row_hash<<<grid_for(n * 32), 256, 0, s>>>(G->row_ptr, G->col, G->deg, n, closed, h, idx);
+  NDOS_LAUNCHED();
+  cub::DoubleBuffer<uint64_t> kb(h, h_alt);
+  cub::DoubleBuffer<int32_t> vb(idx, idx_alt);
+  size_t bytes = 0;
+  NDOS_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, bytes, kb, vb, n, 0, 64, s));
+  char* tmp = nullptr;
+  NDOS_CHECK(t.get(&tmp, bytes));
+  NDOS_CUDA(cub::DeviceRadixSort::SortPairs(tmp, bytes, kb, vb, n, 0, 64, s));
+  count_launch();
+  k_mark_runs<<<grid_for(n), 256, 0, s>>>(kb.Current(), vb.Current(), n, cid, run_start, n_runs_d);
+  NDOS_LAUNCHED();
+  unsigned long long n_runs = 0;
+  NDOS_CUDA(cudaMemcpyAsync(&n_runs, n_runs_d, sizeof(n_runs), cudaMemcpyDeviceToHost, s));
+  NDOS_CUDA(cudaStreamSynchronize(s));
+  if (n_runs > 0) {
+    k_resolve_runs<<<grid_for(static_cast<int64_t>(n_runs) * 32), 256, 0, s>>>(
+        kb.Current(), vb.Current(), n, run_start, static_cast<int64_t>(n_runs), G->row_ptr, G->col, closed, cid);
+    NDOS_LAUNCHED();
+  }
+  return DOS_OK;
+}
+
+static int motif_filter_impl(const Graph* G, uint32_t motifs, cudaStream_t s, Filter* F) {
   const int64_t n = G->n;
   Temps t(s);
   auto palloc = [](int32_t** p, int64_t count) -> int {
@@ -150,48 +254,62 @@ static int motif_filter_impl(const Graph* G, cudaStream_t s, Filter* F) {
     NDOS_CHECK(palloc(&F->slot_size, 1));
     return DOS_OK;
   }
-  uint64_t *h = nullptr, *h_alt = nullptr;
-  int32_t *idx = nullptr, *idx_alt = nullptr, *cnt = nullptr, *flag = nullptr, *slot_of = nullptr;
-  int64_t* run_start = nullptr;
-  unsigned long long* counters = nullptr;  // [0] runs, [1] removed
-  NDOS_CHECK(t.get(&h, n));
-  NDOS_CHECK(t.get(&h_alt, n));
-  NDOS_CHECK(t.get(&idx, n));
-  NDOS_CHECK(t.get(&idx_alt, n));
+  int32_t *cnt = nullptr, *flag = nullptr, *slot_of = nullptr;
+  unsigned long long* removed_d = nullptr;
   NDOS_CHECK(t.get(&cnt, n));
   NDOS_CHECK(t.get(&flag, n + 1));
   NDOS_CHECK(t.get(&slot_of, n + 1));
-  NDOS_CHECK(t.get(&run_start, n));
-  NDOS_CHECK(t.get(&counters, 2));
-  NDOS_CUDA(cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned long long), s));
+  NDOS_CHECK(t.get(&removed_d, 1));
+  NDOS_CUDA(cudaMemsetAsync(removed_d, 0, sizeof(unsigned long long), s));
   NDOS_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * n, s));
 
-  k_row_hash<<<grid_for(n * 32), 256, 0, s>>>(G->row_ptr, G->col, G->deg, n, h, idx);
-  NDOS_LAUNCHED();
-  cub::DoubleBuffer<uint64_t> kb(h, h_alt);
-  cub::DoubleBuffer<int32_t> vb(idx, idx_alt);
-  size_t bytes = 0;
-  NDOS_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, bytes, kb, vb, n, 0, 64, s));
-  char* tmp = nullptr;
-  NDOS_CHECK(t.get(&tmp, bytes));
-  NDOS_CUDA(cub::DeviceRadixSort::SortPairs(tmp, bytes, kb, vb, n, 0, 64, s));
-  count_launch();
-  k_mark_runs<<<grid_for(n), 256, 0, s>>>(kb.Current(), vb.Current(), n, F->class_id, run_start, counters);
-  NDOS_LAUNCHED();
-  unsigned long long n_runs = 0;
-  NDOS_CUDA(cudaMemcpyAsync(&n_runs, counters, sizeof(n_runs), cudaMemcpyDeviceToHost, s));
-  NDOS_CUDA(cudaStreamSynchronize(s));
-  if (n_runs > 0) {
-    k_resolve_runs<<<grid_for(static_cast<int64_t>(n_runs) * 32), 256, 0, s>>>(
-        kb.Current(), vb.Current(), n, run_start, static_cast<int64_t>(n_runs), G->row_ptr, G->col, F->class_id);
+  if (motifs & DOS_MOTIF_OPEN_TWINS) {
+    NDOS_CHECK(find_classes(G, 0, F->class_id, t));
+  } else {
+    k_iota<<<grid_for(n), 256, 0, s>>>(F->class_id, n);
     NDOS_LAUNCHED();
   }
-  k_class_counts<<<grid_for(n), 256, 0, s>>>(F->class_id, n, cnt, counters + 1);
+  int64_t removed_closed = 0;
+  if (motifs & DOS_MOTIF_CLOSED_TWINS) {
+    int32_t *closed_id = nullptr, *open_size = nullptr, *closed_size = nullptr;
+    unsigned long long* per_deg = nullptr;
+    int* conflict = nullptr;
+    NDOS_CHECK(t.get(&closed_id, n));
+    NDOS_CHECK(t.get(&open_size, n));
+    NDOS_CHECK(t.get(&closed_size, n));
+    NDOS_CHECK(t.get(&per_deg, n + 1));
+    NDOS_CHECK(t.get(&conflict, 1));
+    NDOS_CHECK(find_classes(G, 1, closed_id, t));
+    NDOS_CUDA(cudaMemsetAsync(open_size, 0, sizeof(int32_t) * n, s));
+    NDOS_CUDA(cudaMemsetAsync(closed_size, 0, sizeof(int32_t) * n, s));
+    NDOS_CUDA(cudaMemsetAsync(per_deg, 0, sizeof(unsigned long long) * (n + 1), s));
+    NDOS_CUDA(cudaMemsetAsync(conflict, 0, sizeof(int), s));
+    k_sizes<<<grid_for(n), 256, 0, s>>>(F->class_id, n, open_size);
+    NDOS_LAUNCHED();
+    k_sizes<<<grid_for(n), 256, 0, s>>>(closed_id, n, closed_size);
+    NDOS_LAUNCHED();
+    k_merge_closed<<<grid_for(n), 256, 0, s>>>(F->class_id, open_size, closed_id, closed_size, G->deg, n, per_deg,
+                                               conflict);
+    NDOS_LAUNCHED();
+    std::vector<unsigned long long> h_deg(static_cast<size_t>(n + 1));
+    int h_conflict = 0;
+    NDOS_CUDA(cudaMemcpyAsync(h_deg.data(), per_deg, sizeof(unsigned long long) * (n + 1), cudaMemcpyDeviceToHost, s));
+    NDOS_CUDA(cudaMemcpyAsync(&h_conflict, conflict, sizeof(int), cudaMemcpyDeviceToHost, s));
+    NDOS_CUDA(cudaStreamSynchronize(s));
+    if (h_conflict) return fail(DOS_ECUDA, "dos_motif_filter: a node in both an open and a closed twin class");
+    // one spike -1/d per degree d that has closed twins
+    for (int64_t d = 1; d <= n; ++d)
+      if (h_deg[d]) {
+        F->spikes.push_back({-1.0 / static_cast<double>(d), static_cast<int64_t>(h_deg[d])});
+        removed_closed += static_cast<int64_t>(h_deg[d]);
+      }
+  }
+  k_class_counts<<<grid_for(n), 256, 0, s>>>(F->class_id, n, cnt, removed_d);
   NDOS_LAUNCHED();
   k_leader_flags<<<grid_for(n), 256, 0, s>>>(cnt, n, flag);
   NDOS_LAUNCHED();
   NDOS_CUDA(cudaMemsetAsync(flag + n, 0, sizeof(int32_t), s));
-  bytes = 0;
+  size_t bytes = 0;
   NDOS_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, bytes, flag, slot_of, n + 1, s));
   char* tmp2 = nullptr;
   NDOS_CHECK(t.get(&tmp2, bytes));
@@ -200,10 +318,14 @@ static int motif_filter_impl(const Graph* G, cudaStream_t s, Filter* F) {
   int32_t n_classes = 0;
   unsigned long long removed = 0;
   NDOS_CUDA(cudaMemcpyAsync(&n_classes, slot_of + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-  NDOS_CUDA(cudaMemcpyAsync(&removed, counters + 1, sizeof(removed), cudaMemcpyDeviceToHost, s));
+  NDOS_CUDA(cudaMemcpyAsync(&removed, removed_d, sizeof(removed), cudaMemcpyDeviceToHost, s));
   NDOS_CUDA(cudaStreamSynchronize(s));
   F->n_classes = n_classes;
   F->removed = static_cast<int64_t>(removed);
+  const int64_t removed_open = F->removed - removed_closed;
+  if (removed_open > 0) F->spikes.push_back({0.0, removed_open});
+  std::sort(F->spikes.begin(), F->spikes.end(),
+            [](const std::pair<double, int64_t>& x, const std::pair<double, int64_t>& y) { return x.first < y.first; });
   NDOS_CHECK(palloc(&F->slot_size, n_classes));
   k_slots<<<grid_for(n), 256, 0, s>>>(F->class_id, cnt, slot_of, G->p_compact, n, F->p_slot, F->slot_size);
   NDOS_LAUNCHED();
@@ -215,18 +337,38 @@ static int motif_filter_impl(const Graph* G, cudaStream_t s, Filter* F) {
 
 using namespace netdos;
 
-extern "C" int dos_motif_filter(dos_graph_t g, void* stream, dos_filter_t* out) {
+extern "C" int dos_motif_filter_ex(dos_graph_t g, uint32_t motifs, void* stream, dos_filter_t* out) {
   clear_error();
   if (!out) return fail(DOS_EINVAL, "dos_motif_filter: out is NULL");
   *out = nullptr;
   if (!g) return fail(DOS_EINVAL, "dos_motif_filter: null graph");
+  const uint32_t known = DOS_MOTIF_OPEN_TWINS | DOS_MOTIF_CLOSED_TWINS;
+  if (motifs == 0 || (motifs & ~known)) return fail(DOS_EINVAL, "dos_motif_filter_ex: unknown or empty motif set");
   Filter* F = new Filter();
   F->g = reinterpret_cast<const Graph*>(g);
-  int st = motif_filter_impl(F->g, static_cast<cudaStream_t>(stream), F);
+  int st = motif_filter_impl(F->g, motifs, static_cast<cudaStream_t>(stream), F);
   if (st != DOS_OK) {
     dos_filter_destroy(reinterpret_cast<dos_filter_t>(F));
     return st;
   }
   *out = reinterpret_cast<dos_filter_t>(F);
+  return DOS_OK;
+}
+
+extern "C" int dos_motif_filter(dos_graph_t g, void* stream, dos_filter_t* out) {
+  return dos_motif_filter_ex(g, DOS_MOTIF_OPEN_TWINS, stream, out);
+}
+
+extern "C" int dos_filter_spikes(dos_filter_t f, double* spikes, int capacity, int* n_spikes) {
+  clear_error();
+  if (!f) return fail(DOS_EINVAL, "dos_filter_spikes: null filter");
+  if (capacity < 0 || (capacity > 0 && !spikes)) return fail(DOS_EINVAL, "dos_filter_spikes: bad buffer");
+  const Filter* F = reinterpret_cast<const Filter*>(f);
+  const int total = static_cast<int>(F->spikes.size());
+  if (n_spikes) *n_spikes = total;
+  for (int k = 0; k < total && k < capacity; ++k) {
+    spikes[2 * k] = F->spikes[k].first;
+    spikes[2 * k + 1] = static_cast<double>(F->spikes[k].second);
+  }
   return DOS_OK;
 }

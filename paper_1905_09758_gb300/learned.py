@@ -91,13 +91,8 @@ def reconstruct(rec: Reconstructor, g: nd.Graph, f: nd.Filter | None, seed: int,
                 stream=None) -> torch.Tensor:
     """Spectral histogram (float64 CUDA, rec.bins) of the whole graph: the
     network's density of the filtered operator scaled by r / N_total, plus the
-    zero eigenvalues (removed twins, isolated nodes) as a point mass at 0."""
+    eigenvalues the filter removed (and isolated nodes at 0) as point masses."""
     x = features(g, f, rec.m_in, rec.nz_in, seed, rec.bins, stream=stream)
     p = nd.dos_mlp_forward(rec.net, x, stream=stream)
-    info = g.info()
-    removed = f.info()["removed"] if f is not None else 0
-    iso = info["n_isolated"] if count_isolated else 0
-    n_total = info["n"] + iso
-    zeros = removed + iso
-    spikes = [(0.0, zeros / n_total)] if zeros else []
-    return nd.dos_hist_assemble(p, scale=(info["n"] - removed) / n_total, spikes=spikes, stream=stream)[0]
+    scale, spikes = nd.filtered_scale_and_spikes(g, f, count_isolated)
+    return nd.dos_hist_assemble(p, scale=scale, spikes=spikes, stream=stream)[0]

@@ -269,3 +269,56 @@ def test_all_rows_heavy_complete_graph():
     # a stochastic estimate: error ~ 1/sqrt(N Nz) per moment
     assert np.abs(d - exact).max() < 0.05
     assert nd.dos_device_status() == 0
+
+
+# ---- closed twins (lambda = -1/d) --------------------------------------------
+def _closed_graphs():
+    yield "windmill", sg.windmill(7)
+    yield "k12", sg.complete(12)
+    s, d, n = sg.chung_lu(6000, 2.5, 6.0, 17)
+    s, d, n = sg.add_twin_leaves(s, d, n, 200, 18)
+    yield "cl_both", sg.add_triangle_twins(s, d, n, 300, 19)
+    yield "ba_tri", sg.add_triangle_twins(*sg.barabasi_albert(4000, 2, 20), 150, 21)
+
+
+CLOSED = dict(_closed_graphs())
+
+
+@pytest.mark.parametrize("name", list(CLOSED))
+def test_closed_twin_filter_bit_exact_and_moments(name):
+    src, dst, n = CLOSED[name]
+    ref = oracle.build_csr(src, dst, n)
+    g = _gpu_graph(src, dst, n)
+    f = nd.dos_motif_filter_ex(g, ("open", "closed"))
+    cid_ref, removed, spikes = oracle.motif_classes(ref)
+    assert np.array_equal(nd.dos_filter_export(f).cpu().numpy(), cid_ref)
+    assert f.info()["removed"] == removed and f.info()["r"] == ref.n - removed
+    assert nd.dos_filter_spikes(f) == spikes
+    # closed only
+    fc = nd.dos_motif_filter_ex(g, ("closed",))
+    cc, rc, sc = oracle.motif_classes(ref, open_twins=False)
+    assert np.array_equal(nd.dos_filter_export(fc).cpu().numpy(), cc)
+    assert fc.info()["removed"] == rc and nd.dos_filter_spikes(fc) == sc
+    # filtered moments on the projected probes
+    m, nz = 40, 24
+    d = nd.dos_moments(g, m, nz, 13, filter=f).cpu().numpy()
+    z = oracle.project_probes(oracle.probes(13, ref.old_id, nz), cid_ref)
+    d_ref = oracle.kpm_doubled(ref, z, m) / ((ref.n - removed) * nz)
+    assert np.abs(d - d_ref).max() <= TOL_D
+    # the assembled density: (r/N) KPM(d^r) + a point mass per removed eigenvalue
+    b = 40
+    h = nd.density_with_spikes(torch.from_numpy(d).cuda(), g, b, filter=f).cpu().numpy()
+    n_tot = ref.n + ref.n_isolated
+    pts = [x for x, _ in spikes] + [0.0]
+    wts = [c / n_tot for _, c in spikes] + [ref.n_isolated / n_tot]
+    want = (ref.n - removed) / n_tot * oracle.histogram(d, b) + oracle.point_mass_histogram(pts, wts, b)
+    assert np.abs(h - want).max() <= 1e-12
+
+
+def test_motif_filter_ex_rejects_bad_sets():
+    g = _gpu_graph(*sg.windmill(3))
+    for bad in (0, 4, 7):
+        with pytest.raises(nd.DosError) as e:
+            out = nd._binding.C.c_void_p()
+            nd._binding._check(nd.lib().dos_motif_filter_ex(g.handle, bad, None, nd._binding.C.byref(out)))
+        assert e.value.status == nd.DOS_EINVAL
