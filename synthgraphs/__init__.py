@@ -41,6 +41,7 @@ __all__ = [
     "complete",
     "star",
     "windmill",
+    "spider",
     "complete_bipartite",
     "path",
     "batch_graphs",
@@ -216,6 +217,21 @@ def add_triangle_twins(src, dst, n: int, n_hosts: int, seed: int):
     new_src = np.concatenate([src, hosts, hosts, a])
     new_dst = np.concatenate([dst, a, b, b])
     return new_src, new_dst, n + 2 * int(n_hosts)
+
+
+def spider(legs: int, length: int = 2):
+    """Spider: centre 0 with `legs` paths of `length` nodes each; legs of
+    length 2 are pendant 2-paths sharing the host 0 (the +-1/sqrt(2) motif)."""
+    src, dst = [], []
+    nxt = 1
+    for _ in range(legs):
+        prev = 0
+        for _ in range(length):
+            src.append(prev)
+            dst.append(nxt)
+            prev = nxt
+            nxt += 1
+    return np.asarray(src, np.int64), np.asarray(dst, np.int64), nxt
 
 
 def windmill(k: int):

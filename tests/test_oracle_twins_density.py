@@ -258,3 +258,49 @@ def test_closed_filter_on_graph_without_motifs_is_identity():
     g = oracle.build_csr(*sg.cycle(9))
     cid, removed, spikes = oracle.motif_classes(g)
     assert removed == 0 and spikes == [] and np.array_equal(cid, np.arange(9))
+
+
+# ---- pendant 2-paths (lambda = +-1/sqrt 2) -------------------------------------
+R2 = 1.0 / np.sqrt(2.0)
+
+
+def test_path_p5_has_one_pendant_pair():
+    # P5 = a2-a1-u-b1-b2: normalized adjacency eigenvalues cos(pi k / 4)
+    g = oracle.build_csr(*sg.path(5))
+    cid, removed, pairs = oracle.pendant_path_classes(g)
+    assert removed == 2 and pairs == 1
+    lam, _ = oracle.exact_eigs(g)
+    assert np.allclose(np.sort(lam), np.sort(np.cos(np.pi * np.arange(5) / 4)), atol=1e-12)
+    _, _, spikes = oracle.motif_classes(g, pendant_paths=True)
+    assert spikes == [(-R2, 1), (R2, 1)]
+
+
+def test_spider_pendant_classes_and_projection():
+    for legs in (2, 3, 5):
+        g = oracle.build_csr(*sg.spider(legs))
+        cid, removed, spikes = oracle.motif_classes(g, pendant_paths=True)
+        assert removed == 2 * (legs - 1) and spikes == [(-R2, legs - 1), (R2, legs - 1)]
+        lam, _ = oracle.exact_eigs(g)
+        p = _p_matrix(cid)
+        h = oracle.dense_h(g)
+        assert np.allclose(p @ p.T @ h, h @ p @ p.T, atol=1e-12)
+        lam_r = np.linalg.eigvalsh(p.T @ h @ p)
+        assert np.allclose(np.sort(lam_r), np.sort(_remove_eigs(lam, spikes)), atol=1e-9)
+
+
+def test_tree_with_all_three_relations_disjoint():
+    # a Barabasi-Albert tree (m = 1) plus twin leaves and triangles
+    src, dst, n = sg.barabasi_albert(400, 1, 61)
+    src, dst, n = sg.add_twin_leaves(src, dst, n, 10, 62)
+    src, dst, n = sg.add_triangle_twins(src, dst, n, 10, 63)
+    g = oracle.build_csr(src, dst, n)
+    cid, removed, spikes = oracle.motif_classes(g, pendant_paths=True)
+    sp = dict(spikes)
+    assert sp[R2] == sp[-R2] >= 1 and sp[-0.5] >= 10 and sp[0.0] >= 10
+    lam, _ = oracle.exact_eigs(g)
+    p = _p_matrix(cid)
+    h = oracle.dense_h(g)
+    assert np.allclose(p @ p.T @ h, h @ p @ p.T, atol=1e-12)
+    lam_r = np.linalg.eigvalsh(p.T @ h @ p)
+    assert lam_r.size == g.n - removed
+    assert np.allclose(np.sort(lam_r), np.sort(_remove_eigs(lam, spikes)), atol=1e-9)
