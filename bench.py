@@ -524,12 +524,14 @@ def measure_mixed_precision(seed, dev, dist, reps: int = 2) -> dict:
 # ---------------------------------------------------------------------------
 MOTIFS = {"graph": "Chung-Lu gamma=2.5 mean_deg=20 N=1,000,000 + 50,000 twin-leaf pairs + 50,000 triangle twins",
           "M": 100, "Nz": 16, "M_ref": 2000, "Nz_ref": 64, "bins": BINS}
+# reference: unfiltered KPM at M_ref (independent seed), favouring no filter
 
 
 def measure_motifs(seed, reps: int = 3) -> dict:
-    """Filter time (open twins; open + closed twins) and the density's L1
-    distance at M = 100 to an unfiltered M = 2000 reference (independent
-    seed), without a filter, with open twins, and with both."""
+    """Filter time and the density's L1 distance at M = 100 to an unfiltered
+    M = 2000 reference (independent seed) for motif sets: on the Chung-Lu
+    graph with twin leaves and triangles (open / closed twins), and on a
+    Barabasi-Albert tree (m = 1; pendant 2-paths, the paper's Fig. 6 case)."""
     import torch
 
     import paper_1905_09758_gb300 as nd
@@ -538,13 +540,30 @@ def measure_motifs(seed, reps: int = 3) -> dict:
     src, dst, n = sg.chung_lu(N_BASE, GAMMA, MEAN_DEG, seed)
     src, dst, n = sg.add_twin_leaves(src, dst, n, N_TWIN_HOSTS, seed + 1)
     src, dst, n = sg.add_triangle_twins(src, dst, n, 50_000, seed + 2)
+    out = {"chung_lu": motif_leg(src, dst, n, seed, (("none", None), ("open", ("open",)),
+                                                      ("open+closed", ("open", "closed"))), reps),
+           "barabasi_albert_tree": None}
+    out["chung_lu"]["graph"] = MOTIFS["graph"]
+    src, dst, n = sg.barabasi_albert(N_BASE, 1, seed + 3)
+    out["barabasi_albert_tree"] = motif_leg(src, dst, n, seed, (("none", None), ("open", ("open",)),
+                                                                 ("open+pendant", ("open", "pendant")),
+                                                                 ("all", ("open", "closed", "pendant"))), reps)
+    out["barabasi_albert_tree"]["graph"] = "Barabasi-Albert m=1 (a tree), N=1,000,000"
+    return out
+
+
+def motif_leg(src, dst, n, seed, variants, reps) -> dict:
+    import torch
+
+    import paper_1905_09758_gb300 as nd
+
     g = nd.dos_build_csr(torch.from_numpy(src).cuda(), torch.from_numpy(dst).cuda(), n)
     m, nz = MOTIFS["M"], MOTIFS["Nz"]
     d_ref = nd.dos_moments(g, MOTIFS["M_ref"], MOTIFS["Nz_ref"], seed + 777)
     h_ref = nd.density_with_spikes(d_ref, g, BINS).cpu().numpy()
-    out = {"workload": "chung_lu_1M_open_and_closed_twins", **MOTIFS, "n_compact": g.info()["n"],
+    out = {"M": m, "Nz": nz, "M_ref": MOTIFS["M_ref"], "Nz_ref": MOTIFS["Nz_ref"], "n_compact": g.info()["n"],
            "nnz": g.info()["nnz"], "filters": {}}
-    for name, motifs in (("none", None), ("open", ("open",)), ("open+closed", ("open", "closed"))):
+    for name, motifs in variants:
         times = []
         f = None
         for _ in range(reps if motifs else 1):

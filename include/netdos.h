@@ -124,7 +124,8 @@ int dos_motif_filter(dos_graph_t g, void* stream, dos_filter_t* out);
 /* Motif sets of dos_motif_filter_ex (bit mask). */
 enum {
   DOS_MOTIF_OPEN_TWINS = 1,   /* N(i) = N(j): eigenvalue 0 (Fig. 3a) */
-  DOS_MOTIF_CLOSED_TWINS = 2  /* N[i] = N[j] (adjacent, degree d): eigenvalue -1/d */
+  DOS_MOTIF_CLOSED_TWINS = 2, /* N[i] = N[j] (adjacent, degree d): eigenvalue -1/d */
+  DOS_MOTIF_PENDANT_PATHS = 4 /* >= 2 pendant 2-paths at one host: +-1/sqrt(2) */
 };
 
 /*
@@ -133,12 +134,15 @@ enum {
  * hashing; filtering by Z_r = P P^T Z).  Closed twins are nodes with equal
  * closed neighbourhoods N[i] = N(i) + {i}; they are adjacent, share the degree
  * d, and each class of size c carries c - 1 eigenvalues -1/d on the vectors
- * e_i - e_j (d = 2: the triangle with two degree-2 nodes, -1/2).  The open
- * and closed relations are disjoint, so the classes of both are filtered by
- * one class-mean projection; dos_filter_info's removed counts both, and
+ * e_i - e_j (d = 2: the triangle with two degree-2 nodes, -1/2).  Pendant
+ * 2-paths are u - a1 - a2 with d(a1) = 2, d(a2) = 1; c >= 2 of them at one
+ * host u carry c - 1 eigenvalues at each of +-1/sqrt(2) on vectors summing
+ * to zero over the first nodes and over the ends, which become two classes.
+ * The relations are disjoint, so all classes are filtered by one class-mean
+ * projection; dos_filter_info's removed counts all of them, and
  * dos_filter_spikes lists the removed eigenvalues.  Hash collisions are
  * resolved by exact comparison.
- *   motifs  DOS_MOTIF_OPEN_TWINS | DOS_MOTIF_CLOSED_TWINS (nonzero).
+ *   motifs  any nonzero OR of the DOS_MOTIF_* values.
  *   out     receives the filter handle.  Synchronises `stream`.
  * Errors: DOS_EINVAL (g NULL, empty or unknown motif set), DOS_ENOMEM,
  * DOS_ECUDA.  dos_motif_filter(g, ...) = dos_motif_filter_ex(g,
@@ -148,7 +152,8 @@ int dos_motif_filter_ex(dos_graph_t g, uint32_t motifs, void* stream,
                         dos_filter_t* out);
 
 /* Removed eigenvalues [host]: up to `capacity` pairs (lambda, count) in
- * ascending lambda (0 for open twins, -1/d per degree d with closed twins);
+ * ascending lambda (0 for open twins, -1/d per degree d with closed twins,
+ * +-1/sqrt(2) for pendant 2-paths);
  * *n_spikes (may be NULL) receives the total number of pairs.
  * Errors: DOS_EINVAL. */
 int dos_filter_spikes(dos_filter_t f, double* spikes, int capacity,

@@ -3,9 +3,12 @@
 //   open twins    N(i) = N(j):  eigenvectors e_i - e_j with eigenvalue 0;
 //   closed twins  N[i] = N[j] (N[i] = N(i) + {i}, so i ~ j and d_i = d_j = d):
 //                 A (e_i - e_j) = e_j - e_i, eigenvalue -1/d of H.
-// The two relations are disjoint (a node in a nontrivial open class has no
-// closed twin), so one class id per node and one class-mean projection of
-// the probes filters both.
+//   pendant 2-paths u - a1 - a2 (d(a1) = 2, d(a2) = 1), c >= 2 at one host u:
+//                 the first nodes form one class and the ends another; the
+//                 vectors summing to zero over each carry c - 1 eigenvalues
+//                 at each of +-1/sqrt(2).
+// The relations are disjoint (no node is in two nontrivial classes), so one
+// class id per node and one class-mean projection of the probes filters all.
 //
 // Detection follows the paper's hashing idea with an integer hash: each node
 // gets h_i = mix(d_i) + sum_{j in N(i)} mix(j) (+ mix(i) for closed
@@ -18,6 +21,7 @@
 #include <cub/device/device_scan.cuh>
 
 #include <algorithm>
+#include <cmath>
 #include <utility>
 #include <vector>
 
@@ -151,6 +155,47 @@ __global__ void k_merge_closed(int32_t* __restrict__ class_id, const int32_t* __
     if (open_size[class_id[i]] >= 2) atomicOr(conflict, 1);  // cannot happen (disjoint relations)
     class_id[i] = c;
     if (c != i) atomicAdd(&per_deg[deg[i]], 1ull);
+  }
+}
+
+// pendant 2-paths: host_of[a2] = u for every end a2 of a path u - a1 - a2
+// (else -1); per host the path count and the smallest first node and end
+__global__ void k_pendant_scan(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                               const int32_t* __restrict__ deg, int64_t n, int32_t* __restrict__ host_of,
+                               int32_t* __restrict__ cnt, int32_t* __restrict__ min1, int32_t* __restrict__ min2) {
+  for (int64_t a2 = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; a2 < n;
+       a2 += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    int32_t u = -1;
+    if (deg[a2] == 1) {
+      const int32_t a1 = col[row_ptr[a2]];
+      if (deg[a1] == 2) {
+        const int64_t e = row_ptr[a1];
+        u = col[e] == static_cast<int32_t>(a2) ? col[e + 1] : col[e];
+        atomicAdd(&cnt[u], 1);
+        atomicMin(&min1[u], a1);
+        atomicMin(&min2[u], static_cast<int32_t>(a2));
+      }
+    }
+    host_of[a2] = u;
+  }
+}
+
+// classes of the paths at hosts with >= 2 of them; pairs = sum (c - 1)
+__global__ void k_pendant_assign(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col, int64_t n,
+                                 const int32_t* __restrict__ host_of, const int32_t* __restrict__ cnt,
+                                 const int32_t* __restrict__ min1, const int32_t* __restrict__ min2,
+                                 const int32_t* __restrict__ size, int32_t* __restrict__ class_id,
+                                 unsigned long long* __restrict__ pairs, int* __restrict__ conflict) {
+  for (int64_t a2 = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; a2 < n;
+       a2 += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int32_t u = host_of[a2];
+    if (u < 0 || cnt[u] < 2) continue;
+    const int32_t a1 = col[row_ptr[a2]];
+    // cannot happen (disjoint relations): either node already in a nontrivial class
+    if (size[class_id[a1]] >= 2 || size[class_id[a2]] >= 2) atomicOr(conflict, 1);
+    class_id[a1] = min1[u];
+    class_id[a2] = min2[u];
+    if (a1 != min1[u]) atomicAdd(pairs, 1ull);
   }
 }
 
@@ -304,6 +349,44 @@ static int motif_filter_impl(const Graph* G, uint32_t motifs, cudaStream_t s, Fi
         removed_closed += static_cast<int64_t>(h_deg[d]);
       }
   }
+  int64_t removed_paths = 0;
+  if (motifs & DOS_MOTIF_PENDANT_PATHS) {
+    int32_t *host_of = nullptr, *pcnt = nullptr, *min1 = nullptr, *min2 = nullptr, *size = nullptr;
+    unsigned long long* pairs_d = nullptr;
+    int* conflict = nullptr;
+    NDOS_CHECK(t.get(&host_of, n));
+    NDOS_CHECK(t.get(&pcnt, n));
+    NDOS_CHECK(t.get(&min1, n));
+    NDOS_CHECK(t.get(&min2, n));
+    NDOS_CHECK(t.get(&size, n));
+    NDOS_CHECK(t.get(&pairs_d, 1));
+    NDOS_CHECK(t.get(&conflict, 1));
+    NDOS_CUDA(cudaMemsetAsync(pcnt, 0, sizeof(int32_t) * n, s));
+    NDOS_CUDA(cudaMemsetAsync(min1, 0x7f, sizeof(int32_t) * n, s));  // 0x7f7f7f7f > any id
+    NDOS_CUDA(cudaMemsetAsync(min2, 0x7f, sizeof(int32_t) * n, s));
+    NDOS_CUDA(cudaMemsetAsync(size, 0, sizeof(int32_t) * n, s));
+    NDOS_CUDA(cudaMemsetAsync(pairs_d, 0, sizeof(unsigned long long), s));
+    NDOS_CUDA(cudaMemsetAsync(conflict, 0, sizeof(int), s));
+    k_sizes<<<grid_for(n), 256, 0, s>>>(F->class_id, n, size);
+    NDOS_LAUNCHED();
+    k_pendant_scan<<<grid_for(n), 256, 0, s>>>(G->row_ptr, G->col, G->deg, n, host_of, pcnt, min1, min2);
+    NDOS_LAUNCHED();
+    k_pendant_assign<<<grid_for(n), 256, 0, s>>>(G->row_ptr, G->col, n, host_of, pcnt, min1, min2, size,
+                                                 F->class_id, pairs_d, conflict);
+    NDOS_LAUNCHED();
+    unsigned long long pairs = 0;
+    int h_conflict = 0;
+    NDOS_CUDA(cudaMemcpyAsync(&pairs, pairs_d, sizeof(pairs), cudaMemcpyDeviceToHost, s));
+    NDOS_CUDA(cudaMemcpyAsync(&h_conflict, conflict, sizeof(int), cudaMemcpyDeviceToHost, s));
+    NDOS_CUDA(cudaStreamSynchronize(s));
+    if (h_conflict) return fail(DOS_ECUDA, "dos_motif_filter: a pendant-path node already in a twin class");
+    if (pairs) {
+      const double r2 = 1.0 / std::sqrt(2.0);
+      F->spikes.push_back({-r2, static_cast<int64_t>(pairs)});
+      F->spikes.push_back({r2, static_cast<int64_t>(pairs)});
+    }
+    removed_paths = 2 * static_cast<int64_t>(pairs);
+  }
   k_class_counts<<<grid_for(n), 256, 0, s>>>(F->class_id, n, cnt, removed_d);
   NDOS_LAUNCHED();
   k_leader_flags<<<grid_for(n), 256, 0, s>>>(cnt, n, flag);
@@ -322,7 +405,7 @@ static int motif_filter_impl(const Graph* G, uint32_t motifs, cudaStream_t s, Fi
   NDOS_CUDA(cudaStreamSynchronize(s));
   F->n_classes = n_classes;
   F->removed = static_cast<int64_t>(removed);
-  const int64_t removed_open = F->removed - removed_closed;
+  const int64_t removed_open = F->removed - removed_closed - removed_paths;
   if (removed_open > 0) F->spikes.push_back({0.0, removed_open});
   std::sort(F->spikes.begin(), F->spikes.end(),
             [](const std::pair<double, int64_t>& x, const std::pair<double, int64_t>& y) { return x.first < y.first; });
@@ -342,7 +425,7 @@ extern "C" int dos_motif_filter_ex(dos_graph_t g, uint32_t motifs, void* stream,
   if (!out) return fail(DOS_EINVAL, "dos_motif_filter: out is NULL");
   *out = nullptr;
   if (!g) return fail(DOS_EINVAL, "dos_motif_filter: null graph");
-  const uint32_t known = DOS_MOTIF_OPEN_TWINS | DOS_MOTIF_CLOSED_TWINS;
+  const uint32_t known = DOS_MOTIF_OPEN_TWINS | DOS_MOTIF_CLOSED_TWINS | DOS_MOTIF_PENDANT_PATHS;
   if (motifs == 0 || (motifs & ~known)) return fail(DOS_EINVAL, "dos_motif_filter_ex: unknown or empty motif set");
   Filter* F = new Filter();
   F->g = reinterpret_cast<const Graph*>(g);

@@ -317,8 +317,45 @@ def test_closed_twin_filter_bit_exact_and_moments(name):
 
 def test_motif_filter_ex_rejects_bad_sets():
     g = _gpu_graph(*sg.windmill(3))
-    for bad in (0, 4, 7):
+    for bad in (0, 8, 15):
         with pytest.raises(nd.DosError) as e:
             out = nd._binding.C.c_void_p()
             nd._binding._check(nd.lib().dos_motif_filter_ex(g.handle, bad, None, nd._binding.C.byref(out)))
         assert e.value.status == nd.DOS_EINVAL
+
+
+# ---- pendant 2-paths (lambda = +-1/sqrt 2) -------------------------------------
+def _pendant_graphs():
+    yield "p5", sg.path(5)
+    yield "spider6", sg.spider(6)
+    s, d, n = sg.barabasi_albert(5000, 1, 71)
+    s, d, n = sg.add_twin_leaves(s, d, n, 100, 72)
+    yield "ba_tree_all", sg.add_triangle_twins(s, d, n, 100, 73)
+    yield "cl_sparse", sg.chung_lu(8000, 2.3, 2.5, 74)
+
+
+PENDANT = dict(_pendant_graphs())
+
+
+@pytest.mark.parametrize("name", list(PENDANT))
+def test_pendant_path_filter_bit_exact_and_moments(name):
+    src, dst, n = PENDANT[name]
+    ref = oracle.build_csr(src, dst, n)
+    g = _gpu_graph(src, dst, n)
+    f = nd.dos_motif_filter_ex(g, ("open", "closed", "pendant"))
+    cid_ref, removed, spikes = oracle.motif_classes(ref, pendant_paths=True)
+    assert np.array_equal(nd.dos_filter_export(f).cpu().numpy(), cid_ref)
+    assert f.info()["removed"] == removed
+    assert nd.dos_filter_spikes(f) == spikes
+    m, nz = 30, 16
+    d = nd.dos_moments(g, m, nz, 21, filter=f).cpu().numpy()
+    z = oracle.project_probes(oracle.probes(21, ref.old_id, nz), cid_ref)
+    d_ref = oracle.kpm_doubled(ref, z, m) / ((ref.n - removed) * nz)
+    assert np.abs(d - d_ref).max() <= TOL_D
+    b = 60
+    h = nd.density_with_spikes(torch.from_numpy(d).cuda(), g, b, filter=f).cpu().numpy()
+    n_tot = ref.n + ref.n_isolated
+    pts = [x for x, _ in spikes] + [0.0]
+    wts = [c / n_tot for _, c in spikes] + [ref.n_isolated / n_tot]
+    want = (ref.n - removed) / n_tot * oracle.histogram(d, b) + oracle.point_mass_histogram(pts, wts, b)
+    assert np.abs(h - want).max() <= 1e-12
