@@ -35,11 +35,18 @@ Parity status of each function (what pins it, see ``tests/test_oracle_*.py``):
 * ``jackson``, ``bin_integrals``,
   ``histogram``                    -- pinned by g_0 = 1, kernel positivity,
                                       unit mass, and independent quadrature.
+* ``lanczos``, ``gauss_rules``, ``gql_moments``, ``gql_histogram``
+                                   -- pinned by Gauss exactness (the rule's Chebyshev
+                                      moments equal the KPM moments of the same probes
+                                      up to degree 2M - 1), K_n and C_n closed forms,
+                                      unit weights and the PDOS of e_k probes.
 * ``mlp_*``                        -- pinned by central finite differences.
 """
 from .kpm import *  # noqa: F401,F403
 from .kpm import __all__ as _kpm_all
+from .gql import *  # noqa: F401,F403
+from .gql import __all__ as _gql_all
 from .mlp import *  # noqa: F401,F403
 from .mlp import __all__ as _mlp_all
 
-__all__ = list(_kpm_all) + list(_mlp_all)
+__all__ = list(_kpm_all) + list(_gql_all) + list(_mlp_all)
