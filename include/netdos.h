@@ -260,6 +260,50 @@ int dos_moments_noalloc(dos_graph_t g, int M, int Nz, uint64_t seed,
                         double* d_out, void* stream);
 
 /* ---------------------------------------------------------------------
+ * Gauss quadrature and Lanczos (GQL), the second estimator of §3.2.
+ * --------------------------------------------------------------------- */
+
+/*
+ * dos_lanczos -- M Lanczos steps on H from each of Nz Rademacher probes (the
+ * probes of dos_moments for the same seed), FP32 vectors, FP64 reductions,
+ * no reorthogonalisation.  Paper: §3.2 (H Z_M = Z_M Gamma_M + r_M e_M^T).
+ *   alpha_out [device] double[Nz * M]: alpha_out[p * M + k] = alpha_k of probe p
+ *   beta_out  [device] double[Nz * M]: beta_out[p * M + k] = ||w_{k+1}||, the
+ *             coupling of steps k and k + 1 (the last one is the residual)
+ *   steps_out [device] int32[Nz]: steps run; a probe stops early when
+ *             beta_k <= 1e-5 ||z|| (its Krylov space is exhausted; below that
+ *             the FP32 residual is rounding noise); entries past its steps
+ *             are 0.
+ *   M in [1, 4096], Nz in [1, 128].  Stream-ordered.
+ * Errors: DOS_EINVAL, DOS_ENOMEM, DOS_ECUDA.
+ */
+int dos_lanczos(dos_graph_t g, int M, int Nz, uint64_t seed, double* alpha_out,
+                double* beta_out, int32_t* steps_out, void* stream);
+
+/* The Gauss rule of each probe (§3.2): nodes_out[p * M + i] = eigenvalue tau_i
+ * of Gamma_M (ascending), weights_out[p * M + i] = |p_i1|^2 (Christoffel
+ * numbers; they sum to 1); slots past steps[p] hold 0.  Inputs as produced
+ * by dos_lanczos [device].  Stream-ordered.  Errors: DOS_EINVAL. */
+int dos_gauss_rules(const double* alpha, const double* beta,
+                    const int32_t* steps, int M, int Nz, double* nodes_out,
+                    double* weights_out, void* stream);
+
+/* Chebyshev moments of the probe-averaged Gauss rules, d_out[m] =
+ * (1/Nz) sum_p e_1^T T_m(Gamma_p) e_1, m < m_count [device double[m_count]];
+ * equal to the KPM moments of the same probes for m <= 2 steps - 1 (Gauss
+ * exactness).  Stream-ordered.  Errors: DOS_EINVAL, DOS_ENOMEM. */
+int dos_gql_moments(const double* alpha, const double* beta,
+                    const int32_t* steps, int M, int Nz, int m_count,
+                    double* d_out, void* stream);
+
+/* GQL density: bin masses of the rules' point masses averaged over probes,
+ * hist_out [device] double[n_bins] over n_bins equal bins of [-1, 1] (a node
+ * within 1e-9 of an interior edge splits evenly).  Stream-ordered.
+ * Errors: DOS_EINVAL. */
+int dos_gql_histogram(const double* nodes, const double* weights, int M,
+                      int Nz, int n_bins, double* hist_out, void* stream);
+
+/* ---------------------------------------------------------------------
  * Batches of graphs (one operator for many small graphs).
  * --------------------------------------------------------------------- */
 

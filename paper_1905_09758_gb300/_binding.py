@@ -83,6 +83,10 @@ _SIGNATURES = {
     "dos_mlp_features": ([_vp, _i32, _vp, _i32, _i32, _i64, _vp, _vp], _i32),
     "dos_hist_normalize": ([_vp, _i32, _i64, _vp, _vp], _i32),
     "dos_hist_assemble": ([_vp, _i32, _i64, _dbl, _vp, _i32, _vp, _vp], _i32),
+    "dos_lanczos": ([_vp, _i32, _i32, _u64, _vp, _vp, _vp, _vp], _i32),
+    "dos_gauss_rules": ([_vp, _vp, _vp, _i32, _i32, _vp, _vp, _vp], _i32),
+    "dos_gql_moments": ([_vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp], _i32),
+    "dos_gql_histogram": ([_vp, _vp, _i32, _i32, _i32, _vp, _vp], _i32),
 }
 
 
@@ -597,3 +601,53 @@ def dos_hist_assemble(probs: torch.Tensor, scale: float = 1.0, spikes=(), hist_o
     _check(lib().dos_hist_assemble(_ptr(probs), int(B), int(rows), float(scale), arr if sp else None, len(sp) // 2,
                                    _ptr(hist_out), _stream(stream)))
     return hist_out
+
+
+# ---------------------------------------------------------------------------
+# Gauss quadrature and Lanczos (§3.2)
+# ---------------------------------------------------------------------------
+def dos_lanczos(g: Graph, M: int, Nz: int, seed: int, stream=None):
+    """Lanczos coefficients of each probe: alpha, beta float64 (Nz, M) and steps int32 (Nz,), CUDA."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    alpha = torch.empty((Nz, M), dtype=torch.float64, device=dev)
+    beta = torch.empty((Nz, M), dtype=torch.float64, device=dev)
+    steps = torch.empty(Nz, dtype=torch.int32, device=dev)
+    _check(lib().dos_lanczos(g.handle, int(M), int(Nz), int(seed) & (2**64 - 1), _ptr(alpha), _ptr(beta),
+                             _ptr(steps), _stream(stream)))
+    return alpha, beta, steps
+
+
+def _lanczos_args(alpha, beta, steps):
+    _need_cuda(alpha, torch.float64, "alpha")
+    _need_cuda(beta, torch.float64, "beta", alpha.numel())
+    _need_cuda(steps, torch.int32, "steps", alpha.shape[0])
+    return alpha.shape[0], alpha.shape[1]
+
+
+def dos_gauss_rules(alpha, beta, steps, stream=None):
+    """Nodes and weights (Nz, M) of each probe's Gauss rule (0 past its steps)."""
+    nz, m = _lanczos_args(alpha, beta, steps)
+    nodes = torch.empty((nz, m), dtype=torch.float64, device=alpha.device)
+    weights = torch.empty((nz, m), dtype=torch.float64, device=alpha.device)
+    _check(lib().dos_gauss_rules(_ptr(alpha), _ptr(beta), _ptr(steps), m, nz, _ptr(nodes), _ptr(weights),
+                                 _stream(stream)))
+    return nodes, weights
+
+
+def dos_gql_moments(alpha, beta, steps, m_count: int, stream=None) -> torch.Tensor:
+    """Chebyshev moments of the probe-averaged Gauss rules (float64 CUDA, m_count)."""
+    nz, m = _lanczos_args(alpha, beta, steps)
+    d = torch.empty(m_count, dtype=torch.float64, device=alpha.device)
+    _check(lib().dos_gql_moments(_ptr(alpha), _ptr(beta), _ptr(steps), m, nz, int(m_count), _ptr(d),
+                                 _stream(stream)))
+    return d
+
+
+def dos_gql_histogram(nodes, weights, n_bins: int, stream=None) -> torch.Tensor:
+    """Bin masses of the probe-averaged Gauss rules (float64 CUDA, n_bins)."""
+    _need_cuda(nodes, torch.float64, "nodes")
+    _need_cuda(weights, torch.float64, "weights", nodes.numel())
+    nz, m = nodes.shape
+    h = torch.empty(n_bins, dtype=torch.float64, device=nodes.device)
+    _check(lib().dos_gql_histogram(_ptr(nodes), _ptr(weights), m, nz, int(n_bins), _ptr(h), _stream(stream)))
+    return h

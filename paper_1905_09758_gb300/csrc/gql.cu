@@ -1,0 +1,538 @@
+// Gauss quadrature and Lanczos (GQL, §3.2): per-probe Lanczos on H, the Gauss
+// rule of each probe's spectral measure, its Chebyshev moments and its
+// histogram.
+//
+// Lanczos runs on all Nz probes at once, FP32 vectors and FP64 reductions,
+// in the scaled space of the Chebyshev kernels (U = S v, S = D^{-1/2}):
+//     (S H v)_i = (1/d_i) sum_{j in N(i)} U_j,  u^T H u = sum_i d_i U_i (S H u)_i,
+//     ||v||^2 = sum_i d_i U_i^2.
+// The stored vectors are unnormalised: W_1 = S z, W_{k+1} = S (H u_k - alpha_k u_k
+// - beta_{k-1} u_{k-1}) with u_k = S^{-1} W_k / beta_{k-1}, beta_0 = ||z||.  A
+// step is two passes:
+//   apply   Y = S H u_k (gather: a CTA per heavy row, a warp per other row,
+//           in the degree-sorted row order) and the alpha_k partials;
+//   update  W_{k+1} = Y - (alpha_k / beta_{k-1}) W_k - (beta_{k-1} / beta_{k-2}) W_{k-1}
+//           (in place over W_{k-1}) and the ||w||^2 partials,
+// each followed by a fixed-order FP64 reduction over CTAs, one thread per
+// probe.  A probe stops when beta_k <= 1e-5 ||z||: its Krylov space is
+// exhausted and what is left is FP32 rounding noise (relative ~1e-7); its
+// later vectors are zero and its rule keeps the steps it ran.
+// No reorthogonalisation (the paper names none).
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+
+namespace netdos {
+namespace {
+
+constexpr int kLzThreads = 256;
+constexpr int kLzWarps = kLzThreads / 32;
+
+struct LanczosState {
+  double* alpha;       // [nz][m] output
+  double* beta;        // [nz][m] output (beta[p][k]: ||w_{k+1}||)
+  int32_t* steps;      // [nz] output
+  double* b_prev;      // beta_{k-1} per probe (beta_0 = ||z||)
+  double* b_prev2;     // beta_{k-2} per probe
+  float* inv_b;        // 1 / beta_{k-1}, 0 once stopped
+  float* c1;           // alpha_k / beta_{k-1}
+  float* c2;           // beta_{k-1} / beta_{k-2} (0 at k = 1)
+  double* part;        // [grid][nzp] partial sums
+};
+
+// W_1 = S z in the degree-sorted row order (a symmetric relabelling leaves
+// the Lanczos coefficients unchanged): row-major N x nzp, z_pj = +-1 from the
+// probe hash keyed by the original id, 0 in the padding columns
+__global__ void k_lz_init(const int32_t* __restrict__ p_orig, const int32_t* __restrict__ p_compact,
+                          const float* __restrict__ s32, int64_t n, int nz, int nzp, uint64_t seed,
+                          float* __restrict__ w_cur, float* __restrict__ w_prev) {
+  const int64_t total = n * nzp;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / nzp;
+    const int j = static_cast<int>(e - i * nzp);
+    float v = 0.f;
+    if (j < nz) {
+      const uint64_t word = probe_word(seed, static_cast<uint32_t>(p_orig[i]), static_cast<uint32_t>(j >> 6));
+      const float si = s32[p_compact[i]];
+      v = ((word >> (j & 63)) & 1ull) ? -si : si;
+    }
+    w_cur[e] = v;
+    w_prev[e] = 0.f;
+  }
+}
+
+__global__ void k_lz_state0(int nz, int nzp, double norm0, LanczosState st) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nzp) return;
+  const bool real = p < nz;
+  st.b_prev[p] = norm0;
+  st.b_prev2[p] = 1.0;
+  st.inv_b[p] = real ? static_cast<float>(1.0 / norm0) : 0.f;
+  st.c2[p] = 0.f;
+  if (real) st.steps[p] = 0;
+}
+
+// Gather of one row's neighbour rows, chunk `ch` of slot `slot`, over the
+// neighbours [e_lo, e_hi) taken `stride` apart in batches of 32: column
+// indices are loaded coalesced and handed to the slots by shuffles, so the
+// gathers of a batch are independent loads.
+template <int Q>
+__device__ __forceinline__ void lz_gather(const int32_t* __restrict__ col, const float* __restrict__ w, int nzp,
+                                          int64_t e_lo, int64_t e_hi, int64_t stride, int lane, int slot, int ch,
+                                          float4& acc) {
+  constexpr int P = 32 / Q;
+  for (int64_t e0 = e_lo; e0 < e_hi; e0 += stride) {
+    const int cnt = static_cast<int>(e_hi - e0 < 32 ? e_hi - e0 : 32);
+    const int32_t mine = lane < cnt ? col[e0 + lane] : 0;
+#pragma unroll
+    for (int u = 0; u < 32 / P; ++u) {
+      const int src = slot + u * P;
+      const int32_t c = __shfl_sync(0xffffffffu, mine, src);
+      if (src < cnt) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(w + static_cast<size_t>(c) * nzp) + ch);
+        acc.x += v.x;
+        acc.y += v.y;
+        acc.z += v.z;
+        acc.w += v.w;
+      }
+    }
+  }
+}
+
+// Epilogue of one row (lanes of slot 0): Y = acc / d * inv_b, and the row's
+// alpha contributions d (W_own inv_b) Y.
+__device__ __forceinline__ void lz_row_out(int64_t i, float dd, const float4& acc, const float4& ib, int nzp, int ch,
+                                           const float* __restrict__ w_cur, float* __restrict__ y, double& a0,
+                                           double& a1, double& a2, double& a3) {
+  const float sc = 1.0f / dd;
+  const float4 out = make_float4(acc.x * sc * ib.x, acc.y * sc * ib.y, acc.z * sc * ib.z, acc.w * sc * ib.w);
+  reinterpret_cast<float4*>(y + static_cast<size_t>(i) * nzp)[ch] = out;
+  const float4 own = reinterpret_cast<const float4*>(w_cur + static_cast<size_t>(i) * nzp)[ch];
+  a0 += static_cast<double>(dd * (own.x * ib.x) * out.x);
+  a1 += static_cast<double>(dd * (own.y * ib.y) * out.y);
+  a2 += static_cast<double>(dd * (own.z * ib.z) * out.z);
+  a3 += static_cast<double>(dd * (own.w * ib.w) * out.w);
+}
+
+// apply, rows [row0, n) (degree < kHeavyDeg): Y = S H u_k and the alpha
+// partials.  A warp per row: Q = nzp / 4 lanes hold one 16-byte chunk each,
+// 32 / Q neighbour slots.  Partials of CTA b go to part[b].
+template <int Q>
+__global__ void __launch_bounds__(kLzThreads) k_lz_apply(const int64_t* __restrict__ row_ptr,
+                                                         const int32_t* __restrict__ col,
+                                                         const int32_t* __restrict__ deg, int64_t row0, int64_t n,
+                                                         int nzp, const float* __restrict__ w_cur,
+                                                         const float* __restrict__ inv_b, float* __restrict__ y,
+                                                         double* __restrict__ part) {
+  __shared__ double red[kLzWarps][4 * Q];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int slot = lane / Q, ch = lane % Q;
+  const float4 ib = reinterpret_cast<const float4*>(inv_b)[ch];
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  const int64_t w0 = static_cast<int64_t>(blockIdx.x) * kLzWarps + warp;
+  const int64_t nw = static_cast<int64_t>(gridDim.x) * kLzWarps;
+  for (int64_t i = row0 + w0; i < n; i += nw) {
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    lz_gather<Q>(col, w_cur, nzp, row_ptr[i], row_ptr[i + 1], 32, lane, slot, ch, acc);
+#pragma unroll
+    for (int o = Q; o < 32; o <<= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+      acc.z += __shfl_xor_sync(0xffffffffu, acc.z, o);
+      acc.w += __shfl_xor_sync(0xffffffffu, acc.w, o);
+    }
+    if (slot == 0) lz_row_out(i, static_cast<float>(deg[i]), acc, ib, nzp, ch, w_cur, y, a0, a1, a2, a3);
+  }
+  if (slot == 0) {
+    red[warp][4 * ch + 0] = a0;
+    red[warp][4 * ch + 1] = a1;
+    red[warp][4 * ch + 2] = a2;
+    red[warp][4 * ch + 3] = a3;
+  }
+  __syncthreads();
+  for (int p = threadIdx.x; p < 4 * Q; p += kLzThreads) {
+    double sum = 0.0;
+    for (int w = 0; w < kLzWarps; ++w) sum += red[w][p];
+    part[static_cast<size_t>(blockIdx.x) * nzp + p] = sum;
+  }
+}
+
+// apply, heavy rows [0, n_heavy): a CTA per row, the warps take interleaved
+// batches of 32 neighbours; the warps' sums are added in warp order.
+// Partials of row r go to part[r].
+template <int Q>
+__global__ void __launch_bounds__(kLzThreads) k_lz_apply_heavy(const int64_t* __restrict__ row_ptr,
+                                                               const int32_t* __restrict__ col,
+                                                               const int32_t* __restrict__ deg, int nzp,
+                                                               const float* __restrict__ w_cur,
+                                                               const float* __restrict__ inv_b, float* __restrict__ y,
+                                                               double* __restrict__ part) {
+  __shared__ float4 wsum[kLzWarps][Q];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int slot = lane / Q, ch = lane % Q;
+  const int64_t i = blockIdx.x;
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  lz_gather<Q>(col, w_cur, nzp, row_ptr[i] + 32 * warp, row_ptr[i + 1], 32 * kLzWarps, lane, slot, ch, acc);
+#pragma unroll
+  for (int o = Q; o < 32; o <<= 1) {
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    acc.z += __shfl_xor_sync(0xffffffffu, acc.z, o);
+    acc.w += __shfl_xor_sync(0xffffffffu, acc.w, o);
+  }
+  if (slot == 0) wsum[warp][ch] = acc;
+  __syncthreads();
+  if (warp == 0 && slot == 0) {
+    float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int w = 0; w < kLzWarps; ++w) {
+      t.x += wsum[w][ch].x;
+      t.y += wsum[w][ch].y;
+      t.z += wsum[w][ch].z;
+      t.w += wsum[w][ch].w;
+    }
+    const float4 ib = reinterpret_cast<const float4*>(inv_b)[ch];
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    lz_row_out(i, static_cast<float>(deg[i]), t, ib, nzp, ch, w_cur, y, a0, a1, a2, a3);
+    double* o = part + static_cast<size_t>(i) * nzp + 4 * ch;
+    o[0] = a0;
+    o[1] = a1;
+    o[2] = a2;
+    o[3] = a3;
+  }
+}
+
+// update: W_{k+1} = Y - c1 W_k - c2 W_{k-1} over W_{k-1}, ||w||^2 partials.
+// Thread t handles chunk t % Q of rows t / Q, t / Q + stride, ...
+template <int Q>
+__global__ void __launch_bounds__(kLzThreads) k_lz_update(const int32_t* __restrict__ deg, int64_t n, int nzp,
+                                                          const float* __restrict__ y, const float* __restrict__ w_cur,
+                                                          float* __restrict__ w_pn, const float* __restrict__ c1,
+                                                          const float* __restrict__ c2, double* __restrict__ part) {
+  constexpr int RPB = kLzThreads / Q;  // rows per block pass
+  __shared__ double red[RPB][4 * Q];
+  const int ch = threadIdx.x % Q, r = threadIdx.x / Q;
+  const float4 a = reinterpret_cast<const float4*>(c1)[ch];
+  const float4 b = reinterpret_cast<const float4*>(c2)[ch];
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  for (int64_t i = static_cast<int64_t>(blockIdx.x) * RPB + r; i < n; i += static_cast<int64_t>(gridDim.x) * RPB) {
+    const size_t off = static_cast<size_t>(i) * nzp;
+    const float4 yy = reinterpret_cast<const float4*>(y + off)[ch];
+    const float4 wc = reinterpret_cast<const float4*>(w_cur + off)[ch];
+    float4* pn = reinterpret_cast<float4*>(w_pn + off) + ch;
+    const float4 wp = *pn;
+    const float4 o = make_float4(yy.x - a.x * wc.x - b.x * wp.x, yy.y - a.y * wc.y - b.y * wp.y,
+                                 yy.z - a.z * wc.z - b.z * wp.z, yy.w - a.w * wc.w - b.w * wp.w);
+    *pn = o;
+    const float dd = static_cast<float>(deg[i]);
+    s0 += static_cast<double>(dd * o.x * o.x);
+    s1 += static_cast<double>(dd * o.y * o.y);
+    s2 += static_cast<double>(dd * o.z * o.z);
+    s3 += static_cast<double>(dd * o.w * o.w);
+  }
+  red[r][4 * ch + 0] = s0;
+  red[r][4 * ch + 1] = s1;
+  red[r][4 * ch + 2] = s2;
+  red[r][4 * ch + 3] = s3;
+  __syncthreads();
+  for (int p = threadIdx.x; p < 4 * Q; p += kLzThreads) {
+    double s = 0.0;
+    for (int rr = 0; rr < RPB; ++rr) s += red[rr][p];
+    part[static_cast<size_t>(blockIdx.x) * nzp + p] = s;
+  }
+}
+
+// sum over CTAs of one probe's partials: a warp per probe, lanes over CTAs,
+// then a fixed shuffle tree (deterministic)
+__device__ __forceinline__ double warp_sum_partials(const double* part, int grid, int nzp, int p, int lane) {
+  double a = 0.0;
+  for (int c = lane; c < grid; c += 32) a += part[static_cast<size_t>(c) * nzp + p];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  return a;
+}
+
+// alpha_k = sum of the apply partials; coefficients of the update.  Grid:
+// one 32-thread block per padded probe.
+__global__ void k_lz_alpha(int nz, int nzp, int m, int k, int grid, LanczosState st) {
+  const int p = blockIdx.x, lane = threadIdx.x;
+  const double a = warp_sum_partials(st.part, grid, nzp, p, lane);
+  if (lane != 0) return;
+  if (p >= nz) {
+    st.c1[p] = 0.f;
+    st.c2[p] = 0.f;
+    return;
+  }
+  const bool live = st.inv_b[p] != 0.f;
+  if (live) st.alpha[static_cast<size_t>(p) * m + k] = a;
+  st.c1[p] = live ? static_cast<float>(a / st.b_prev[p]) : 0.f;
+  st.c2[p] = live && k > 0 ? static_cast<float>(st.b_prev[p] / st.b_prev2[p]) : 0.f;
+}
+
+// beta_k = ||w_{k+1}||; stop a probe whose Krylov space is exhausted
+__global__ void k_lz_beta(int nz, int nzp, int m, int k, int grid, double stop, LanczosState st) {
+  const int p = blockIdx.x, lane = threadIdx.x;
+  if (p >= nz) return;
+  const double s = warp_sum_partials(st.part, grid, nzp, p, lane);
+  if (lane != 0 || st.inv_b[p] == 0.f) return;  // stopped earlier
+  const double b = sqrt(s);
+  st.beta[static_cast<size_t>(p) * m + k] = b;
+  st.steps[p] = k + 1;
+  st.b_prev2[p] = st.b_prev[p];
+  st.b_prev[p] = b;
+  st.inv_b[p] = b > stop ? static_cast<float>(1.0 / b) : 0.f;
+}
+
+// ---- the Gauss rule of each probe ---------------------------------------------
+// Number of eigenvalues of tridiag(b; a; b) (size k) below x (Sturm sequence).
+__device__ int sturm_below(const double* a, const double* b, int k, double x) {
+  int cnt = 0;
+  double q = 1.0;
+  for (int j = 0; j < k; ++j) {
+    const double off = j > 0 ? b[j - 1] * b[j - 1] : 0.0;
+    q = (a[j] - x) - (j > 0 ? off / q : 0.0);
+    if (q == 0.0) q = -1e-300;
+    if (q < 0.0) ++cnt;
+  }
+  return cnt;
+}
+
+// one thread per (probe, node index i): node i by bisection (the point where
+// the Sturm count passes i), its weight by the Christoffel number
+// w_i = 1 / sum_j p_j(tau_i)^2 of the orthonormal polynomials of the rule
+// (p_0 = 1, b_j p_{j+1} = (x - a_j) p_j - b_{j-1} p_{j-1}); slots past the
+// probe's steps get node and weight 0
+__global__ void k_gauss_rules(const double* __restrict__ alpha, const double* __restrict__ beta,
+                              const int32_t* __restrict__ steps, int m, int nz, double* __restrict__ nodes,
+                              double* __restrict__ weights) {
+  const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (t >= static_cast<int64_t>(nz) * m) return;
+  const int p = static_cast<int>(t / m), i = static_cast<int>(t % m);
+  const double* a = alpha + static_cast<size_t>(p) * m;
+  const double* b = beta + static_cast<size_t>(p) * m;
+  const int k = steps[p];
+  if (i >= k) {
+    nodes[t] = 0.0;
+    weights[t] = 0.0;
+    return;
+  }
+  double lo = a[0], hi = a[0];
+  for (int j = 0; j < k; ++j) {  // Gershgorin interval
+    const double r = (j > 0 ? fabs(b[j - 1]) : 0.0) + (j + 1 < k ? fabs(b[j]) : 0.0);
+    lo = fmin(lo, a[j] - r);
+    hi = fmax(hi, a[j] + r);
+  }
+  for (int it = 0; it < 200 && hi - lo > 1e-15 * fmax(1.0, fabs(lo) + fabs(hi)); ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (sturm_below(a, b, k, mid) > i) hi = mid; else lo = mid;
+  }
+  const double x = 0.5 * (lo + hi);
+  double p_prev = 0.0, p_cur = 1.0, sum = 1.0;
+  for (int j = 0; j + 1 < k; ++j) {
+    const double nxt = ((x - a[j]) * p_cur - (j > 0 ? b[j - 1] * p_prev : 0.0)) / b[j];
+    p_prev = p_cur;
+    p_cur = nxt;
+    sum += p_cur * p_cur;
+  }
+  nodes[t] = x;
+  weights[t] = 1.0 / sum;
+}
+
+// Chebyshev moments of the averaged rules, d_m = (1/nz) sum_p e_1^T T_m(G_p) e_1,
+// by the Chebyshev recurrence on the tridiagonal G_p applied to e_1 (one
+// thread per probe, per-probe results summed in probe order by k_sum_probes)
+__global__ void k_gql_moments(const double* __restrict__ alpha, const double* __restrict__ beta,
+                              const int32_t* __restrict__ steps, int m, int nz, int mc, double* __restrict__ scratch,
+                              double* __restrict__ per_probe) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nz) return;
+  const double* a = alpha + static_cast<size_t>(p) * m;
+  const double* b = beta + static_cast<size_t>(p) * m;
+  const int k = steps[p];
+  double* t_prev = scratch + static_cast<size_t>(p) * 2 * m;
+  double* t_cur = t_prev + m;
+  for (int j = 0; j < k; ++j) {
+    t_prev[j] = 0.0;
+    t_cur[j] = 0.0;
+  }
+  t_prev[0] = 1.0;  // T_0 e_1
+  double* out = per_probe + static_cast<size_t>(p) * mc;
+  out[0] = 1.0;
+  if (mc > 1) {
+    // T_1 e_1 = G e_1
+    t_cur[0] = a[0];
+    if (k > 1) t_cur[1] = b[0];
+    out[1] = t_cur[0];
+  }
+  for (int mm = 2; mm < mc; ++mm) {
+    // t_next = 2 G t_cur - t_prev, written over t_prev
+    const int top = mm < k ? mm : k - 1;  // support of T_mm e_1
+    for (int j = 0; j <= top; ++j) {
+      const double gj =
+          a[j] * t_cur[j] + (j > 0 ? b[j - 1] * t_cur[j - 1] : 0.0) + (j + 1 < k ? b[j] * t_cur[j + 1] : 0.0);
+      t_prev[j] = 2.0 * gj - t_prev[j];
+    }
+    double* tmp = t_prev;
+    t_prev = t_cur;
+    t_cur = tmp;
+    out[mm] = t_cur[0];
+  }
+}
+
+__global__ void k_sum_probes(const double* __restrict__ per_probe, int nz, int mc, double* __restrict__ d) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= mc) return;
+  double s = 0.0;
+  for (int p = 0; p < nz; ++p) s += per_probe[static_cast<size_t>(p) * mc + m];
+  d[m] = s / nz;
+}
+
+// histogram of the averaged rules' point masses: bin b sums, in node order,
+// weight / nz of every node in it (a node within 1e-9 of an interior edge
+// splits evenly, nodes at or beyond +-1 go to the end bins)
+__global__ void k_gql_hist(const double* __restrict__ nodes, const double* __restrict__ weights, int64_t count,
+                           int nz, int B, double* __restrict__ h) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  const double w = 2.0 / B;
+  double v = 0.0;
+  for (int64_t q = 0; q < count; ++q) {
+    const double wt = weights[q];
+    if (wt == 0.0) continue;
+    const double x = fmin(fmax(nodes[q], -1.0), 1.0);
+    const int e = static_cast<int>(rint((x + 1.0) / w));
+    if (e > 0 && e < B && fabs(x - (-1.0 + w * e)) <= 1e-9) {
+      if (b == e - 1 || b == e) v += 0.5 * wt;
+    } else {
+      int bb = static_cast<int>(floor((x + 1.0) / w));
+      bb = bb < 0 ? 0 : (bb >= B ? B - 1 : bb);
+      if (b == bb) v += wt;
+    }
+  }
+  h[b] = v / nz;
+}
+
+inline unsigned blocks_for(int64_t work, int per = 256) {
+  int64_t b = (work + per - 1) / per;
+  const int64_t cap = static_cast<int64_t>(num_sms()) * 16;
+  return static_cast<unsigned>(std::max<int64_t>(1, std::min(b, cap)));
+}
+
+template <int Q>
+int lanczos_steps(const Graph* G, int m, int nz, int nzp, float* w_cur, float* w_pn, float* y, LanczosState st,
+                  int grid, double stop, cudaStream_t s) {
+  const unsigned gp = static_cast<unsigned>(nzp);  // a warp per padded probe
+  const int64_t nh = G->n_heavy;
+  const int parts = grid + static_cast<int>(nh);  // apply partials: light CTAs, then heavy rows
+  for (int k = 0; k < m; ++k) {
+    if (nh > 0) {
+      k_lz_apply_heavy<Q><<<static_cast<unsigned>(nh), kLzThreads, 0, s>>>(G->p_row_ptr, G->p_col, G->p_deg, nzp,
+                                                                          w_cur, st.inv_b, y,
+                                                                          st.part + static_cast<size_t>(grid) * nzp);
+      NDOS_LAUNCHED();
+    }
+    k_lz_apply<Q><<<grid, kLzThreads, 0, s>>>(G->p_row_ptr, G->p_col, G->p_deg, nh, G->n, nzp, w_cur, st.inv_b, y,
+                                             st.part);
+    NDOS_LAUNCHED();
+    k_lz_alpha<<<gp, 32, 0, s>>>(nz, nzp, m, k, parts, st);
+    NDOS_LAUNCHED();
+    k_lz_update<Q><<<grid, kLzThreads, 0, s>>>(G->p_deg, G->n, nzp, y, w_cur, w_pn, st.c1, st.c2, st.part);
+    NDOS_LAUNCHED();
+    k_lz_beta<<<gp, 32, 0, s>>>(nz, nzp, m, k, grid, stop, st);
+    NDOS_LAUNCHED();
+    std::swap(w_cur, w_pn);
+  }
+  return DOS_OK;
+}
+
+}  // namespace
+}  // namespace netdos
+
+using namespace netdos;
+
+extern "C" int dos_lanczos(dos_graph_t g, int M, int Nz, uint64_t seed, double* alpha_out, double* beta_out,
+                           int32_t* steps_out, void* stream) {
+  clear_error();
+  if (!g || !alpha_out || !beta_out || !steps_out) return fail(DOS_EINVAL, "dos_lanczos: null argument");
+  const Graph* G = reinterpret_cast<const Graph*>(g);
+  if (G->n == 0) return fail(DOS_EINVAL, "dos_lanczos: graph has no edges");
+  if (M < 1 || M > 4096) return fail(DOS_EINVAL, "dos_lanczos: M must be in [1, 4096]");
+  if (Nz < 1 || Nz > 128) return fail(DOS_EINVAL, "dos_lanczos: Nz must be in [1, 128]");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // chunks per row: a power of two >= Nz / 4
+  int q = 1;
+  while (4 * q < Nz) q *= 2;
+  const int nzp = 4 * q;
+  const int64_t n = G->n;
+  const int grid = static_cast<int>(std::min<int64_t>(static_cast<int64_t>(num_sms()) * 8,
+                                                      std::max<int64_t>(1, (n + kLzWarps - 1) / kLzWarps)));
+  Temps t(s);
+  float *w_cur = nullptr, *w_pn = nullptr, *y = nullptr, *fl = nullptr;
+  double *dbl = nullptr, *part = nullptr;
+  NDOS_CHECK(t.get(&w_cur, n * nzp));
+  NDOS_CHECK(t.get(&w_pn, n * nzp));
+  NDOS_CHECK(t.get(&y, n * nzp));
+  NDOS_CHECK(t.get(&fl, 3 * nzp));
+  NDOS_CHECK(t.get(&dbl, 2 * nzp));
+  NDOS_CHECK(t.get(&part, (static_cast<int64_t>(grid) + G->n_heavy) * nzp));
+  LanczosState st{alpha_out, beta_out, steps_out, dbl, dbl + nzp, fl, fl + nzp, fl + 2 * nzp, part};
+  NDOS_CUDA(cudaMemsetAsync(alpha_out, 0, sizeof(double) * Nz * M, s));
+  NDOS_CUDA(cudaMemsetAsync(beta_out, 0, sizeof(double) * Nz * M, s));
+  k_lz_init<<<blocks_for(n * nzp), 256, 0, s>>>(G->p_orig, G->p_compact, G->s32, n, Nz, nzp, seed, w_cur, w_pn);
+  NDOS_LAUNCHED();
+  const double norm0 = std::sqrt(static_cast<double>(n));  // ||z||^2 = N for +-1 probes
+  k_lz_state0<<<(nzp + 127) / 128, 128, 0, s>>>(Nz, nzp, norm0, st);
+  NDOS_LAUNCHED();
+  const double stop = 1e-5 * norm0;  // FP32 vectors: a smaller residual is rounding noise
+  int st_code = DOS_OK;
+  switch (q) {
+    case 1: st_code = lanczos_steps<1>(G, M, Nz, nzp, w_cur, w_pn, y, st, grid, stop, s); break;
+    case 2: st_code = lanczos_steps<2>(G, M, Nz, nzp, w_cur, w_pn, y, st, grid, stop, s); break;
+    case 4: st_code = lanczos_steps<4>(G, M, Nz, nzp, w_cur, w_pn, y, st, grid, stop, s); break;
+    case 8: st_code = lanczos_steps<8>(G, M, Nz, nzp, w_cur, w_pn, y, st, grid, stop, s); break;
+    case 16: st_code = lanczos_steps<16>(G, M, Nz, nzp, w_cur, w_pn, y, st, grid, stop, s); break;
+    default: st_code = lanczos_steps<32>(G, M, Nz, nzp, w_cur, w_pn, y, st, grid, stop, s); break;
+  }
+  NDOS_CHECK(st_code);
+  return DOS_OK;
+}
+
+extern "C" int dos_gauss_rules(const double* alpha, const double* beta, const int32_t* steps, int M, int Nz,
+                               double* nodes_out, double* weights_out, void* stream) {
+  clear_error();
+  if (!alpha || !beta || !steps || !nodes_out || !weights_out || M < 1 || Nz < 1)
+    return fail(DOS_EINVAL, "dos_gauss_rules: bad argument");
+  const int64_t work = static_cast<int64_t>(Nz) * M;
+  k_gauss_rules<<<static_cast<unsigned>((work + 127) / 128), 128, 0, static_cast<cudaStream_t>(stream)>>>(
+      alpha, beta, steps, M, Nz, nodes_out, weights_out);
+  NDOS_LAUNCHED();
+  return DOS_OK;
+}
+
+extern "C" int dos_gql_moments(const double* alpha, const double* beta, const int32_t* steps, int M, int Nz,
+                               int m_count, double* d_out, void* stream) {
+  clear_error();
+  if (!alpha || !beta || !steps || !d_out || M < 1 || Nz < 1 || m_count < 1 || m_count > (1 << 20))
+    return fail(DOS_EINVAL, "dos_gql_moments: bad argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Temps t(s);
+  double *scratch = nullptr, *per = nullptr;
+  NDOS_CHECK(t.get(&scratch, static_cast<int64_t>(Nz) * 2 * M));
+  NDOS_CHECK(t.get(&per, static_cast<int64_t>(Nz) * m_count));
+  k_gql_moments<<<(Nz + 63) / 64, 64, 0, s>>>(alpha, beta, steps, M, Nz, m_count, scratch, per);
+  NDOS_LAUNCHED();
+  k_sum_probes<<<(m_count + 127) / 128, 128, 0, s>>>(per, Nz, m_count, d_out);
+  NDOS_LAUNCHED();
+  return DOS_OK;
+}
+
+extern "C" int dos_gql_histogram(const double* nodes, const double* weights, int M, int Nz, int n_bins,
+                                 double* hist_out, void* stream) {
+  clear_error();
+  if (!nodes || !weights || !hist_out || M < 1 || Nz < 1 || n_bins < 1 || n_bins > (1 << 20))
+    return fail(DOS_EINVAL, "dos_gql_histogram: bad argument");
+  k_gql_hist<<<(n_bins + 127) / 128, 128, 0, static_cast<cudaStream_t>(stream)>>>(
+      nodes, weights, static_cast<int64_t>(M) * Nz, Nz, n_bins, hist_out);
+  NDOS_LAUNCHED();
+  return DOS_OK;
+}
