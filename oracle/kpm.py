@@ -33,7 +33,7 @@ __all__ = [
     "twin_classes",
     "closed_twin_classes",
     "motif_classes",
-    "pendant_path_classes",
+    "pendant_twin_classes",
     "project_probes",
     "jackson",
     "bin_edges",
@@ -319,46 +319,50 @@ def closed_twin_classes(g: Csr):
     return class_id, removed, spikes
 
 
-def pendant_path_classes(g: Csr):
-    """Classes of pendant 2-paths sharing a host (the +-1/sqrt(2) motif, §3.4).
+def pendant_twin_classes(g: Csr):
+    """Classes of pendant twins (§3.4, Fig. 3: the +-1/sqrt 2 and +-1/2 motifs).
 
-    A pendant 2-path at host u is u - a1 - a2 with d(a1) = 2 and d(a2) = 1.  If
-    u carries c >= 2 of them, the vectors that sum to zero over the first nodes
-    {a1, b1, ...} and over the ends {a2, b2, ...} form an invariant subspace
-    of H on which H acts as [[0, 1/sqrt 2], [1/sqrt 2, 0]] per pair: c - 1
-    eigenvalues +1/sqrt(2) and c - 1 at -1/sqrt(2).  Filtering them is a
-    class-mean projection with the first nodes as one class and the ends as
-    another.  Returns class_id (smallest member), the removed count 2 (c - 1)
-    summed over hosts, and the number of removed pairs.
+    A node a of degree d >= 2 with exactly one leaf neighbour a' (d(a') = 1) is
+    eligible; eligible a, b are pendant twins if N(a) - {a'} = N(b) - {b'} (so
+    d(a) = d(b) = d and a, b are not adjacent).  For a class of c such nodes
+    the vectors that sum to zero over the nodes and over their leaves form an
+    invariant subspace of H on which H acts as [[0, 1/sqrt d], [1/sqrt d, 0]]
+    per pair (H_{a a'} = 1/sqrt(d), the common neighbours cancel): c - 1
+    eigenvalues at each of +-1/sqrt(d).  d = 2 is the pendant 2-path
+    u - a - a' (+-1/sqrt 2), d = 4 the +-1/2 motif with three common
+    neighbours.  The nodes form one class and their leaves another.
+    Returns class_id (smallest member), the removed count 2 sum (c - 1), and
+    {d: number of removed pairs}.
     """
     class_id = np.arange(g.n, dtype=np.int32)
     rp, col = g.row_ptr, g.col
     deg = np.diff(rp)
-    paths: dict[int, list] = {}
-    for a2 in range(g.n):
-        if deg[a2] != 1:
+    groups: dict[bytes, list] = {}
+    for a in range(g.n):
+        if deg[a] < 2:
             continue
-        a1 = int(col[rp[a2]])
-        if deg[a1] != 2:
+        nb = col[rp[a]:rp[a + 1]]
+        leaves = nb[deg[nb] == 1]
+        if leaves.size != 1:
             continue
-        nb = col[rp[a1]:rp[a1 + 1]]
-        u = int(nb[0] if nb[1] == a2 else nb[1])
-        paths.setdefault(u, []).append((a1, a2))
-    pairs = 0
-    for u, lst in paths.items():
+        rest = nb[nb != leaves[0]]
+        groups.setdefault(rest.astype(np.int32).tobytes(), []).append((a, int(leaves[0])))
+    pairs: dict[int, int] = {}
+    for lst in groups.values():
         if len(lst) < 2:
             continue
         f1 = min(a for a, _ in lst)
-        f2 = min(b for _, b in lst)
-        for a, b in lst:
+        f2 = min(x for _, x in lst)
+        for a, x in lst:
             class_id[a] = f1
-            class_id[b] = f2
-        pairs += len(lst) - 1
-    return class_id, 2 * pairs, pairs
+            class_id[x] = f2
+        d = int(deg[lst[0][0]])
+        pairs[d] = pairs.get(d, 0) + len(lst) - 1
+    return class_id, 2 * sum(pairs.values()), pairs
 
 
-def motif_classes(g: Csr, open_twins: bool = True, closed_twins: bool = True, pendant_paths: bool = False):
-    """Open-twin, closed-twin and (optionally) pendant-path classes together (§3.4).
+def motif_classes(g: Csr, open_twins: bool = True, closed_twins: bool = True, pendant_twins: bool = False):
+    """Open-twin, closed-twin and (optionally) pendant-twin classes together (§3.4).
 
     The relations are disjoint: if N(i) = N(j) and N[i] = N[k] (k != i), then k
     is in N(i) = N(j), so j ~ k, while j would have to lie in N[k] = N[i],
@@ -388,14 +392,15 @@ def motif_classes(g: Csr, open_twins: bool = True, closed_twins: bool = True, pe
         cid = np.where(in_closed, cc, cid)
         removed += r1
         spikes.extend((-1.0 / d, c) for d, c in sp.items())
-    if pendant_paths:
-        pc, r2, pairs = pendant_path_classes(g)
-        in_path = np.bincount(pc, minlength=g.n)[pc] >= 2
-        assert not np.any(taken & in_path)
-        cid = np.where(in_path, pc, cid)
+    if pendant_twins:
+        pc, r2, pairs = pendant_twin_classes(g)
+        in_pt = np.bincount(pc, minlength=g.n)[pc] >= 2
+        assert not np.any(taken & in_pt)
+        cid = np.where(in_pt, pc, cid)
         removed += r2
-        if pairs:
-            spikes.extend([(-1.0 / np.sqrt(2.0), pairs), (1.0 / np.sqrt(2.0), pairs)])
+        for d, c in pairs.items():
+            r = 1.0 / np.sqrt(float(d))
+            spikes.extend([(-r, c), (r, c)])
     return cid, removed, sorted(spikes)
 
 

@@ -37,6 +37,7 @@ __all__ = [
     "barabasi_albert",
     "add_twin_leaves",
     "add_triangle_twins",
+    "add_pendant_twins",
     "cycle",
     "complete",
     "star",
@@ -232,6 +233,31 @@ def spider(legs: int, length: int = 2):
             prev = nxt
             nxt += 1
     return np.asarray(src, np.int64), np.asarray(dst, np.int64), nxt
+
+
+def add_pendant_twins(src, dst, n: int, n_groups: int, k_common: int, seed: int):
+    """Add ``n_groups`` pairs of pendant twins: two new nodes a, b joined to the
+    same ``k_common`` existing nodes (drawn without replacement among the
+    nodes with a non-loop edge) and each to a new leaf of its own, so
+    N(a) - {a'} = N(b) - {b'} and d(a) = d(b) = k_common + 1 (eigenvalues
+    +-1/sqrt(k_common + 1), §3.4 Fig. 3).  Group g's nodes get ids
+    n + 4g .. n + 4g + 3 (a, b, a', b').  Returns the extended edge list and
+    n + 4 n_groups."""
+    rng = _rng(seed)
+    src = np.asarray(src, np.int64)
+    dst = np.asarray(dst, np.int64)
+    live = np.zeros(n, bool)
+    nl = src != dst
+    live[src[nl]] = True
+    live[dst[nl]] = True
+    cand = np.nonzero(live)[0]
+    s_new, d_new = [src], [dst]
+    for gi in range(int(n_groups)):
+        a, b, la, lb = n + 4 * gi, n + 4 * gi + 1, n + 4 * gi + 2, n + 4 * gi + 3
+        common = rng.choice(cand, size=int(k_common), replace=False).astype(np.int64)
+        s_new += [np.full(k_common, a), np.full(k_common, b), np.array([a, b], np.int64)]
+        d_new += [common, common, np.array([la, lb], np.int64)]
+    return np.concatenate(s_new), np.concatenate(d_new), n + 4 * int(n_groups)
 
 
 def windmill(k: int):

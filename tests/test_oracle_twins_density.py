@@ -260,25 +260,25 @@ def test_closed_filter_on_graph_without_motifs_is_identity():
     assert removed == 0 and spikes == [] and np.array_equal(cid, np.arange(9))
 
 
-# ---- pendant 2-paths (lambda = +-1/sqrt 2) -------------------------------------
+# ---- pendant twins (lambda = +-1/sqrt d: pendant 2-paths, the +-1/2 motif) -----
 R2 = 1.0 / np.sqrt(2.0)
 
 
 def test_path_p5_has_one_pendant_pair():
     # P5 = a2-a1-u-b1-b2: normalized adjacency eigenvalues cos(pi k / 4)
     g = oracle.build_csr(*sg.path(5))
-    cid, removed, pairs = oracle.pendant_path_classes(g)
-    assert removed == 2 and pairs == 1
+    cid, removed, pairs = oracle.pendant_twin_classes(g)
+    assert removed == 2 and pairs == {2: 1}
     lam, _ = oracle.exact_eigs(g)
     assert np.allclose(np.sort(lam), np.sort(np.cos(np.pi * np.arange(5) / 4)), atol=1e-12)
-    _, _, spikes = oracle.motif_classes(g, pendant_paths=True)
+    _, _, spikes = oracle.motif_classes(g, pendant_twins=True)
     assert spikes == [(-R2, 1), (R2, 1)]
 
 
 def test_spider_pendant_classes_and_projection():
     for legs in (2, 3, 5):
         g = oracle.build_csr(*sg.spider(legs))
-        cid, removed, spikes = oracle.motif_classes(g, pendant_paths=True)
+        cid, removed, spikes = oracle.motif_classes(g, pendant_twins=True)
         assert removed == 2 * (legs - 1) and spikes == [(-R2, legs - 1), (R2, legs - 1)]
         lam, _ = oracle.exact_eigs(g)
         p = _p_matrix(cid)
@@ -294,9 +294,48 @@ def test_tree_with_all_three_relations_disjoint():
     src, dst, n = sg.add_twin_leaves(src, dst, n, 10, 62)
     src, dst, n = sg.add_triangle_twins(src, dst, n, 10, 63)
     g = oracle.build_csr(src, dst, n)
-    cid, removed, spikes = oracle.motif_classes(g, pendant_paths=True)
+    cid, removed, spikes = oracle.motif_classes(g, pendant_twins=True)
     sp = dict(spikes)
     assert sp[R2] == sp[-R2] >= 1 and sp[-0.5] >= 10 and sp[0.0] >= 10
+    lam, _ = oracle.exact_eigs(g)
+    p = _p_matrix(cid)
+    h = oracle.dense_h(g)
+    assert np.allclose(p @ p.T @ h, h @ p @ p.T, atol=1e-12)
+    lam_r = np.linalg.eigvalsh(p.T @ h @ p)
+    assert lam_r.size == g.n - removed
+    assert np.allclose(np.sort(lam_r), np.sort(_remove_eigs(lam, spikes)), atol=1e-9)
+
+
+def test_pendant_twins_of_degree_four_give_plus_minus_half():
+    # Fig. 3's second +-1/2 example: nodes 0 and 1 share the neighbours 2, 3, 4
+    # and each carries one leaf (5 on 0, 6 on 1); the shared nodes hang on a
+    # small cycle so nothing else is symmetric
+    src = [0, 0, 0, 1, 1, 1, 0, 1, 2, 3, 4, 7, 8]
+    dst = [2, 3, 4, 2, 3, 4, 5, 6, 7, 8, 9, 8, 9]
+    g = oracle.build_csr(np.array(src), np.array(dst), 10)
+    cid, removed, pairs = oracle.pendant_twin_classes(g)
+    assert removed == 2 and pairs == {4: 1}
+    assert cid[1] == 0 and cid[6] == 5
+    cid, removed, spikes = oracle.motif_classes(g, pendant_twins=True)
+    assert (-0.5, 1) in spikes and (0.5, 1) in spikes
+    lam, _ = oracle.exact_eigs(g)
+    p = _p_matrix(cid)
+    h = oracle.dense_h(g)
+    assert np.allclose(p @ p.T @ h, h @ p @ p.T, atol=1e-12)
+    lam_r = np.linalg.eigvalsh(p.T @ h @ p)
+    assert np.allclose(np.sort(lam_r), np.sort(_remove_eigs(lam, spikes)), atol=1e-9)
+
+
+def test_random_graph_with_pendant_twins_of_mixed_degree():
+    src, dst, n = sg.chung_lu(300, 2.4, 6.0, 81)
+    for k, seed in ((1, 82), (2, 83), (3, 84)):
+        src, dst, n = sg.add_pendant_twins(src, dst, n, 4, k, seed)
+    g = oracle.build_csr(src, dst, n)
+    _, _, pairs = oracle.pendant_twin_classes(g)
+    # later groups may take an earlier group's leaf as a common neighbour and
+    # so break that pair; most survive
+    assert all(pairs.get(d, 0) >= 2 for d in (2, 3, 4))
+    cid, removed, spikes = oracle.motif_classes(g, pendant_twins=True)
     lam, _ = oracle.exact_eigs(g)
     p = _p_matrix(cid)
     h = oracle.dense_h(g)
