@@ -125,7 +125,7 @@ int dos_motif_filter(dos_graph_t g, void* stream, dos_filter_t* out);
 enum {
   DOS_MOTIF_OPEN_TWINS = 1,   /* N(i) = N(j): eigenvalue 0 (Fig. 3a) */
   DOS_MOTIF_CLOSED_TWINS = 2, /* N[i] = N[j] (adjacent, degree d): eigenvalue -1/d */
-  DOS_MOTIF_PENDANT_PATHS = 4 /* >= 2 pendant 2-paths at one host: +-1/sqrt(2) */
+  DOS_MOTIF_PENDANT_TWINS = 4 /* degree-d nodes equal but for one leaf each: +-1/sqrt(d) */
 };
 
 /*
@@ -134,10 +134,12 @@ enum {
  * hashing; filtering by Z_r = P P^T Z).  Closed twins are nodes with equal
  * closed neighbourhoods N[i] = N(i) + {i}; they are adjacent, share the degree
  * d, and each class of size c carries c - 1 eigenvalues -1/d on the vectors
- * e_i - e_j (d = 2: the triangle with two degree-2 nodes, -1/2).  Pendant
- * 2-paths are u - a1 - a2 with d(a1) = 2, d(a2) = 1; c >= 2 of them at one
- * host u carry c - 1 eigenvalues at each of +-1/sqrt(2) on vectors summing
- * to zero over the first nodes and over the ends, which become two classes.
+ * e_i - e_j (d = 2: the triangle with two degree-2 nodes, -1/2; degree m:
+ * the -1/m motif).  Pendant twins are nodes of degree d >= 2 with exactly one
+ * leaf neighbour each and equal neighbourhoods apart from it (d = 2: pendant
+ * 2-paths u - a - a'; d = 4: the +-1/2 motif); a class of c carries c - 1
+ * eigenvalues at each of +-1/sqrt(d) on vectors summing to zero over the
+ * nodes and over their leaves, which become two classes.
  * The relations are disjoint, so all classes are filtered by one class-mean
  * projection; dos_filter_info's removed counts all of them, and
  * dos_filter_spikes lists the removed eigenvalues.  Hash collisions are
@@ -153,7 +155,7 @@ int dos_motif_filter_ex(dos_graph_t g, uint32_t motifs, void* stream,
 
 /* Removed eigenvalues [host]: up to `capacity` pairs (lambda, count) in
  * ascending lambda (0 for open twins, -1/d per degree d with closed twins,
- * +-1/sqrt(2) for pendant 2-paths);
+ * +-1/sqrt(d) per degree d with pendant twins);
  * *n_spikes (may be NULL) receives the total number of pairs.
  * Errors: DOS_EINVAL. */
 int dos_filter_spikes(dos_filter_t f, double* spikes, int capacity,

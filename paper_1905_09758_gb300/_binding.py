@@ -317,7 +317,7 @@ def dos_motif_filter(g: Graph, stream=None) -> Filter:
 
 def dos_motif_filter_ex(g: Graph, motifs=("open", "closed"), stream=None) -> Filter:
     """Motif classes for a set of motifs: "open" twins (lambda = 0), "closed"
-    twins (lambda = -1/d), "pendant" 2-paths (lambda = +-1/sqrt 2)."""
+    twins (lambda = -1/d), "pendant" twins (lambda = +-1/sqrt d)."""
     mask = 0
     for m in motifs:
         mask |= MOTIF[m]

@@ -3,16 +3,18 @@
 //   open twins    N(i) = N(j):  eigenvectors e_i - e_j with eigenvalue 0;
 //   closed twins  N[i] = N[j] (N[i] = N(i) + {i}, so i ~ j and d_i = d_j = d):
 //                 A (e_i - e_j) = e_j - e_i, eigenvalue -1/d of H.
-//   pendant 2-paths u - a1 - a2 (d(a1) = 2, d(a2) = 1), c >= 2 at one host u:
-//                 the first nodes form one class and the ends another; the
-//                 vectors summing to zero over each carry c - 1 eigenvalues
-//                 at each of +-1/sqrt(2).
+//   pendant twins  nodes of degree d >= 2 with exactly one leaf neighbour and
+//                 equal neighbourhoods apart from it: the nodes form one class
+//                 and their leaves another; the vectors summing to zero over
+//                 each carry c - 1 eigenvalues at each of +-1/sqrt(d) (d = 2:
+//                 pendant 2-paths, +-1/sqrt 2; d = 4: the +-1/2 motif).
 // The relations are disjoint (no node is in two nontrivial classes), so one
 // class id per node and one class-mean projection of the probes filters all.
 //
 // Detection follows the paper's hashing idea with an integer hash: each node
 // gets h_i = mix(d_i) + sum_{j in N(i)} mix(j) (+ mix(i) for closed
-// neighbourhoods) (mod 2^64), an order-free function of the neighbour set, so
+// neighbourhoods; the leaf left out for pendant twins) (mod 2^64), an
+// order-free function of the neighbour set, so
 // twins always share a hash.  Nodes are sorted by hash (stable in the node
 // id); inside each run of equal hashes the neighbour lists are compared
 // exactly, so a hash collision never merges different neighbourhoods.  Class
@@ -32,21 +34,38 @@ namespace {
 
 __device__ __forceinline__ uint64_t mix_id(uint64_t x) { return splitmix64(0x5bd1e9955bd1e995ull, x); }
 
-// warp per row: order-free hash of the open (closed = 0) or closed (1)
-// neighbourhood
+// pendant-twin eligibility: d >= 2 and exactly one leaf neighbour
+__device__ __forceinline__ bool pendant_eligible(const int32_t* deg, const int32_t* nleaf, int64_t i) {
+  return deg[i] >= 2 && nleaf[i] == 1;
+}
+
+// warp per row: order-free hash of the open (mode 0), closed (1) or
+// leaf-reduced (2, pendant twins) neighbourhood; a node that cannot be a
+// pendant twin gets a hash of its own (mode 2)
 __global__ void k_row_hash(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-                           const int32_t* __restrict__ deg, int64_t n, int closed, uint64_t* __restrict__ hash,
+                           const int32_t* __restrict__ deg, int64_t n, int mode, const int32_t* __restrict__ nleaf,
+                           const int32_t* __restrict__ leaf_of, uint64_t* __restrict__ hash,
                            int32_t* __restrict__ idx) {
   const int lane = threadIdx.x & 31;
   const int64_t w0 = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
   const int64_t nw = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
   for (int64_t i = w0; i < n; i += nw) {
+    if (mode == 2 && !pendant_eligible(deg, nleaf, i)) {
+      if (lane == 0) {
+        hash[i] = 0x8000000000000000ull | static_cast<uint64_t>(i);
+        idx[i] = static_cast<int32_t>(i);
+      }
+      continue;
+    }
+    const int32_t skip = mode == 2 ? leaf_of[i] : -1;
     uint64_t h = 0;
-    for (int64_t e = row_ptr[i] + lane; e < row_ptr[i + 1]; e += 32) h += mix_id(static_cast<uint64_t>(col[e]));
+    for (int64_t e = row_ptr[i] + lane; e < row_ptr[i + 1]; e += 32)
+      if (col[e] != skip) h += mix_id(static_cast<uint64_t>(col[e]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xffffffffu, h, o);
     if (lane == 0) {
-      if (closed) h += mix_id(static_cast<uint64_t>(i)) + 0x9e3779b97f4a7c15ull;
+      if (mode == 1) h += mix_id(static_cast<uint64_t>(i)) + 0x9e3779b97f4a7c15ull;
+      if (mode == 2) h += 0x3c6ef372fe94f82bull;
       hash[i] = h + mix_id(0x8000000000000000ull | static_cast<uint64_t>(deg[i]));
       idx[i] = static_cast<int32_t>(i);
     }
@@ -100,12 +119,38 @@ __device__ __forceinline__ bool same_closed_list(const int64_t* row_ptr, const i
   return adjacent;
 }
 
+// pendant twins: both eligible, N(a) - {leaf a} = N(b) - {leaf b}
+__device__ __forceinline__ bool same_reduced_list(const int64_t* row_ptr, const int32_t* col, const int32_t* deg,
+                                                  const int32_t* nleaf, const int32_t* leaf_of, int32_t a, int32_t b) {
+  if (!pendant_eligible(deg, nleaf, a) || !pendant_eligible(deg, nleaf, b)) return false;
+  const int64_t ba = row_ptr[a], bb = row_ptr[b];
+  const int64_t la = row_ptr[a + 1] - ba, lb = row_ptr[b + 1] - bb;
+  if (la != lb) return false;
+  const int32_t sa = leaf_of[a], sb = leaf_of[b];
+  int64_t i = 0, j = 0;
+  while (i < la || j < lb) {
+    if (i < la && col[ba + i] == sa) {
+      ++i;
+      continue;
+    }
+    if (j < lb && col[bb + j] == sb) {
+      ++j;
+      continue;
+    }
+    if (i >= la || j >= lb || col[ba + i] != col[bb + j]) return false;
+    ++i;
+    ++j;
+  }
+  return true;
+}
+
 // warp per run: repeated leader election in id order; every unassigned member
 // equal to the leader joins its class
 __global__ void k_resolve_runs(const uint64_t* __restrict__ h, const int32_t* __restrict__ node, int64_t n,
                                const int64_t* __restrict__ run_start, int64_t n_runs,
-                               const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col, int closed,
-                               int32_t* class_id) {
+                               const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                               const int32_t* __restrict__ deg, int mode, const int32_t* __restrict__ nleaf,
+                               const int32_t* __restrict__ leaf_of, int32_t* class_id) {
   const int lane = threadIdx.x & 31;
   const int64_t w0 = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
   const int64_t nw = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
@@ -120,9 +165,11 @@ __global__ void k_resolve_runs(const uint64_t* __restrict__ h, const int32_t* __
       if (lane == 0) class_id[ln] = ln;
       for (int64_t k = lead + 1 + lane; k < b; k += 32) {
         const int32_t m = node[k];
-        if (*reinterpret_cast<volatile int32_t*>(class_id + m) == -1 &&
-            (closed ? same_closed_list(row_ptr, col, ln, m) : same_list(row_ptr, col, ln, m)))
-          class_id[m] = ln;
+        if (*reinterpret_cast<volatile int32_t*>(class_id + m) != -1) continue;
+        const bool same = mode == 0   ? same_list(row_ptr, col, ln, m)
+                          : mode == 1 ? same_closed_list(row_ptr, col, ln, m)
+                                      : same_reduced_list(row_ptr, col, deg, nleaf, leaf_of, ln, m);
+        if (same) class_id[m] = ln;
       }
       __syncwarp();
     }
@@ -158,44 +205,44 @@ __global__ void k_merge_closed(int32_t* __restrict__ class_id, const int32_t* __
   }
 }
 
-// pendant 2-paths: host_of[a2] = u for every end a2 of a path u - a1 - a2
-// (else -1); per host the path count and the smallest first node and end
-__global__ void k_pendant_scan(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-                               const int32_t* __restrict__ deg, int64_t n, int32_t* __restrict__ host_of,
-                               int32_t* __restrict__ cnt, int32_t* __restrict__ min1, int32_t* __restrict__ min2) {
-  for (int64_t a2 = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; a2 < n;
-       a2 += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    int32_t u = -1;
-    if (deg[a2] == 1) {
-      const int32_t a1 = col[row_ptr[a2]];
-      if (deg[a1] == 2) {
-        const int64_t e = row_ptr[a1];
-        u = col[e] == static_cast<int32_t>(a2) ? col[e + 1] : col[e];
-        atomicAdd(&cnt[u], 1);
-        atomicMin(&min1[u], a1);
-        atomicMin(&min2[u], static_cast<int32_t>(a2));
-      }
-    }
-    host_of[a2] = u;
+// leaves per node, and one leaf of each node (meaningful where the count is 1)
+__global__ void k_leaf_info(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                            const int32_t* __restrict__ deg, int64_t n, int32_t* __restrict__ nleaf,
+                            int32_t* __restrict__ leaf_of) {
+  for (int64_t x = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; x < n;
+       x += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    if (deg[x] != 1) continue;
+    const int32_t a = col[row_ptr[x]];
+    atomicAdd(&nleaf[a], 1);
+    leaf_of[a] = static_cast<int32_t>(x);
   }
 }
 
-// classes of the paths at hosts with >= 2 of them; pairs = sum (c - 1)
-__global__ void k_pendant_assign(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col, int64_t n,
-                                 const int32_t* __restrict__ host_of, const int32_t* __restrict__ cnt,
-                                 const int32_t* __restrict__ min1, const int32_t* __restrict__ min2,
-                                 const int32_t* __restrict__ size, int32_t* __restrict__ class_id,
-                                 unsigned long long* __restrict__ pairs, int* __restrict__ conflict) {
-  for (int64_t a2 = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; a2 < n;
-       a2 += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int32_t u = host_of[a2];
-    if (u < 0 || cnt[u] < 2) continue;
-    const int32_t a1 = col[row_ptr[a2]];
+// smallest leaf of each pendant-twin class (classes of size >= 2)
+__global__ void k_leaf_min(const int32_t* __restrict__ pid, const int32_t* __restrict__ psize,
+                           const int32_t* __restrict__ leaf_of, int64_t n, int32_t* __restrict__ leaf_min) {
+  for (int64_t a = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; a < n;
+       a += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    if (psize[pid[a]] >= 2) atomicMin(&leaf_min[pid[a]], leaf_of[a]);
+}
+
+// merge the pendant-twin classes (nodes, and their leaves as a second class)
+// and count the removed pairs per degree
+__global__ void k_merge_pendant(int32_t* __restrict__ class_id, const int32_t* __restrict__ size,
+                                const int32_t* __restrict__ pid, const int32_t* __restrict__ psize,
+                                const int32_t* __restrict__ leaf_of, const int32_t* __restrict__ leaf_min,
+                                const int32_t* __restrict__ deg, int64_t n, unsigned long long* __restrict__ per_deg,
+                                int* __restrict__ conflict) {
+  for (int64_t a = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; a < n;
+       a += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int32_t c = pid[a];
+    if (psize[c] < 2) continue;
+    const int32_t x = leaf_of[a];
     // cannot happen (disjoint relations): either node already in a nontrivial class
-    if (size[class_id[a1]] >= 2 || size[class_id[a2]] >= 2) atomicOr(conflict, 1);
-    class_id[a1] = min1[u];
-    class_id[a2] = min2[u];
-    if (a1 != min1[u]) atomicAdd(pairs, 1ull);
+    if (size[class_id[a]] >= 2 || size[class_id[x]] >= 2) atomicOr(conflict, 1);
+    class_id[a] = c;
+    class_id[x] = leaf_min[c];
+    if (c != a) atomicAdd(&per_deg[deg[a]], 1ull);
   }
 }
 
@@ -243,9 +290,11 @@ inline unsigned grid_for(int64_t work, int per_block = 256) {
 
 }  // namespace
 
-// Classes of one relation (open: closed = 0, closed: 1) into cid[n]: the
-// smallest member of each node's class, its own id if it has no twin.
-static int find_classes(const Graph* G, int closed, int32_t* cid, Temps& t) {
+// Classes of one relation (mode 0 open twins, 1 closed twins, 2 pendant
+// twins, which need nleaf / leaf_of) into cid[n]: the smallest member of each
+// node's class, its own id if it has no twin.
+static int find_classes(const Graph* G, int mode, int32_t* cid, Temps& t, const int32_t* nleaf = nullptr,
+                        const int32_t* leaf_of = nullptr) {
   const int64_t n = G->n;
   cudaStream_t s = t.s;
   uint64_t *h = nullptr, *h_alt = nullptr;
@@ -259,7 +308,7 @@ static int find_classes(const Graph* G, int closed, int32_t* cid, Temps& t) {
   NDOS_CHECK(t.get(&run_start, n));
   NDOS_CHECK(t.get(&n_runs_d, 1));
   NDOS_CUDA(cudaMemsetAsync(n_runs_d, 0, sizeof(unsigned long long), s));
-  k_row_hash<<<grid_for(n * 32), 256, 0, s>>>(G->row_ptr, G->col, G->deg, n, closed, h, idx);
+  k_row_hash<<<grid_for(n * 32), 256, 0, s>>>(G->row_ptr, G->col, G->deg, n, mode, nleaf, leaf_of, h, idx);
   NDOS_LAUNCHED();
   cub::DoubleBuffer<uint64_t> kb(h, h_alt);
   cub::DoubleBuffer<int32_t> vb(idx, idx_alt);
@@ -276,7 +325,8 @@ static int find_classes(const Graph* G, int closed, int32_t* cid, Temps& t) {
   NDOS_CUDA(cudaStreamSynchronize(s));
   if (n_runs > 0) {
     k_resolve_runs<<<grid_for(static_cast<int64_t>(n_runs) * 32), 256, 0, s>>>(
-        kb.Current(), vb.Current(), n, run_start, static_cast<int64_t>(n_runs), G->row_ptr, G->col, closed, cid);
+        kb.Current(), vb.Current(), n, run_start, static_cast<int64_t>(n_runs), G->row_ptr, G->col, G->deg, mode, nleaf,
+        leaf_of, cid);
     NDOS_LAUNCHED();
   }
   return DOS_OK;
@@ -350,42 +400,51 @@ static int motif_filter_impl(const Graph* G, uint32_t motifs, cudaStream_t s, Fi
       }
   }
   int64_t removed_paths = 0;
-  if (motifs & DOS_MOTIF_PENDANT_PATHS) {
-    int32_t *host_of = nullptr, *pcnt = nullptr, *min1 = nullptr, *min2 = nullptr, *size = nullptr;
-    unsigned long long* pairs_d = nullptr;
+  if (motifs & DOS_MOTIF_PENDANT_TWINS) {
+    int32_t *nleaf = nullptr, *leaf_of = nullptr, *pid = nullptr, *psize = nullptr, *size = nullptr,
+            *leaf_min = nullptr;
+    unsigned long long* per_deg = nullptr;
     int* conflict = nullptr;
-    NDOS_CHECK(t.get(&host_of, n));
-    NDOS_CHECK(t.get(&pcnt, n));
-    NDOS_CHECK(t.get(&min1, n));
-    NDOS_CHECK(t.get(&min2, n));
+    NDOS_CHECK(t.get(&nleaf, n));
+    NDOS_CHECK(t.get(&leaf_of, n));
+    NDOS_CHECK(t.get(&pid, n));
+    NDOS_CHECK(t.get(&psize, n));
     NDOS_CHECK(t.get(&size, n));
-    NDOS_CHECK(t.get(&pairs_d, 1));
+    NDOS_CHECK(t.get(&leaf_min, n));
+    NDOS_CHECK(t.get(&per_deg, n + 1));
     NDOS_CHECK(t.get(&conflict, 1));
-    NDOS_CUDA(cudaMemsetAsync(pcnt, 0, sizeof(int32_t) * n, s));
-    NDOS_CUDA(cudaMemsetAsync(min1, 0x7f, sizeof(int32_t) * n, s));  // 0x7f7f7f7f > any id
-    NDOS_CUDA(cudaMemsetAsync(min2, 0x7f, sizeof(int32_t) * n, s));
+    NDOS_CUDA(cudaMemsetAsync(nleaf, 0, sizeof(int32_t) * n, s));
+    NDOS_CUDA(cudaMemsetAsync(leaf_of, 0, sizeof(int32_t) * n, s));
+    NDOS_CUDA(cudaMemsetAsync(psize, 0, sizeof(int32_t) * n, s));
     NDOS_CUDA(cudaMemsetAsync(size, 0, sizeof(int32_t) * n, s));
-    NDOS_CUDA(cudaMemsetAsync(pairs_d, 0, sizeof(unsigned long long), s));
+    NDOS_CUDA(cudaMemsetAsync(leaf_min, 0x7f, sizeof(int32_t) * n, s));  // 0x7f7f7f7f > any id
+    NDOS_CUDA(cudaMemsetAsync(per_deg, 0, sizeof(unsigned long long) * (n + 1), s));
     NDOS_CUDA(cudaMemsetAsync(conflict, 0, sizeof(int), s));
+    k_leaf_info<<<grid_for(n), 256, 0, s>>>(G->row_ptr, G->col, G->deg, n, nleaf, leaf_of);
+    NDOS_LAUNCHED();
+    NDOS_CHECK(find_classes(G, 2, pid, t, nleaf, leaf_of));
+    k_sizes<<<grid_for(n), 256, 0, s>>>(pid, n, psize);
+    NDOS_LAUNCHED();
     k_sizes<<<grid_for(n), 256, 0, s>>>(F->class_id, n, size);
     NDOS_LAUNCHED();
-    k_pendant_scan<<<grid_for(n), 256, 0, s>>>(G->row_ptr, G->col, G->deg, n, host_of, pcnt, min1, min2);
+    k_leaf_min<<<grid_for(n), 256, 0, s>>>(pid, psize, leaf_of, n, leaf_min);
     NDOS_LAUNCHED();
-    k_pendant_assign<<<grid_for(n), 256, 0, s>>>(G->row_ptr, G->col, n, host_of, pcnt, min1, min2, size,
-                                                 F->class_id, pairs_d, conflict);
+    k_merge_pendant<<<grid_for(n), 256, 0, s>>>(F->class_id, size, pid, psize, leaf_of, leaf_min, G->deg, n, per_deg,
+                                                conflict);
     NDOS_LAUNCHED();
-    unsigned long long pairs = 0;
+    std::vector<unsigned long long> h_deg(static_cast<size_t>(n + 1));
     int h_conflict = 0;
-    NDOS_CUDA(cudaMemcpyAsync(&pairs, pairs_d, sizeof(pairs), cudaMemcpyDeviceToHost, s));
+    NDOS_CUDA(cudaMemcpyAsync(h_deg.data(), per_deg, sizeof(unsigned long long) * (n + 1), cudaMemcpyDeviceToHost, s));
     NDOS_CUDA(cudaMemcpyAsync(&h_conflict, conflict, sizeof(int), cudaMemcpyDeviceToHost, s));
     NDOS_CUDA(cudaStreamSynchronize(s));
-    if (h_conflict) return fail(DOS_ECUDA, "dos_motif_filter: a pendant-path node already in a twin class");
-    if (pairs) {
-      const double r2 = 1.0 / std::sqrt(2.0);
-      F->spikes.push_back({-r2, static_cast<int64_t>(pairs)});
-      F->spikes.push_back({r2, static_cast<int64_t>(pairs)});
-    }
-    removed_paths = 2 * static_cast<int64_t>(pairs);
+    if (h_conflict) return fail(DOS_ECUDA, "dos_motif_filter: a pendant-twin node already in a twin class");
+    for (int64_t d = 2; d <= n; ++d)
+      if (h_deg[d]) {
+        const double r = 1.0 / std::sqrt(static_cast<double>(d));
+        F->spikes.push_back({-r, static_cast<int64_t>(h_deg[d])});
+        F->spikes.push_back({r, static_cast<int64_t>(h_deg[d])});
+        removed_paths += 2 * static_cast<int64_t>(h_deg[d]);
+      }
   }
   k_class_counts<<<grid_for(n), 256, 0, s>>>(F->class_id, n, cnt, removed_d);
   NDOS_LAUNCHED();
@@ -425,7 +484,7 @@ extern "C" int dos_motif_filter_ex(dos_graph_t g, uint32_t motifs, void* stream,
   if (!out) return fail(DOS_EINVAL, "dos_motif_filter: out is NULL");
   *out = nullptr;
   if (!g) return fail(DOS_EINVAL, "dos_motif_filter: null graph");
-  const uint32_t known = DOS_MOTIF_OPEN_TWINS | DOS_MOTIF_CLOSED_TWINS | DOS_MOTIF_PENDANT_PATHS;
+  const uint32_t known = DOS_MOTIF_OPEN_TWINS | DOS_MOTIF_CLOSED_TWINS | DOS_MOTIF_PENDANT_TWINS;
   if (motifs == 0 || (motifs & ~known)) return fail(DOS_EINVAL, "dos_motif_filter_ex: unknown or empty motif set");
   Filter* F = new Filter();
   F->g = reinterpret_cast<const Graph*>(g);

@@ -324,10 +324,16 @@ def test_motif_filter_ex_rejects_bad_sets():
         assert e.value.status == nd.DOS_EINVAL
 
 
-# ---- pendant 2-paths (lambda = +-1/sqrt 2) -------------------------------------
+# ---- pendant twins (lambda = +-1/sqrt d) ----------------------------------------
 def _pendant_graphs():
     yield "p5", sg.path(5)
     yield "spider6", sg.spider(6)
+    yield "fig3_deg4", (np.array([0, 0, 0, 1, 1, 1, 0, 1, 2, 3, 4, 7, 8]),
+                        np.array([2, 3, 4, 2, 3, 4, 5, 6, 7, 8, 9, 8, 9]), 10)
+    s, d, n = sg.chung_lu(5000, 2.4, 6.0, 81)
+    for k, seed in ((1, 82), (2, 83), (3, 84), (7, 85)):
+        s, d, n = sg.add_pendant_twins(s, d, n, 40, k, seed)
+    yield "cl_pendant_mixed", (s, d, n)
     s, d, n = sg.barabasi_albert(5000, 1, 71)
     s, d, n = sg.add_twin_leaves(s, d, n, 100, 72)
     yield "ba_tree_all", sg.add_triangle_twins(s, d, n, 100, 73)
@@ -338,12 +344,12 @@ PENDANT = dict(_pendant_graphs())
 
 
 @pytest.mark.parametrize("name", list(PENDANT))
-def test_pendant_path_filter_bit_exact_and_moments(name):
+def test_pendant_twin_filter_bit_exact_and_moments(name):
     src, dst, n = PENDANT[name]
     ref = oracle.build_csr(src, dst, n)
     g = _gpu_graph(src, dst, n)
     f = nd.dos_motif_filter_ex(g, ("open", "closed", "pendant"))
-    cid_ref, removed, spikes = oracle.motif_classes(ref, pendant_paths=True)
+    cid_ref, removed, spikes = oracle.motif_classes(ref, pendant_twins=True)
     assert np.array_equal(nd.dos_filter_export(f).cpu().numpy(), cid_ref)
     assert f.info()["removed"] == removed
     assert nd.dos_filter_spikes(f) == spikes
