@@ -41,6 +41,10 @@ Parity status of each function (what pins it, see ``tests/test_oracle_*.py``):
                                       moments equal the KPM moments of the same probes
                                       up to degree 2M - 1), K_n and C_n closed forms,
                                       unit weights and the PDOS of e_k probes.
+* ``operator_matrix``, ``gershgorin_interval``, ``exact_operator_moments``,
+  ``kpm_operator``                 -- pinned by closed-form spectra of A and L (K_n,
+                                      C_n, stars), Gershgorin containment, and identity
+                                      probes giving the exact traces.
 * ``mlp_*``                        -- pinned by central finite differences.
 """
 from .kpm import *  # noqa: F401,F403
@@ -49,5 +53,7 @@ from .gql import *  # noqa: F401,F403
 from .gql import __all__ as _gql_all
 from .mlp import *  # noqa: F401,F403
 from .mlp import __all__ as _mlp_all
+from .operators import *  # noqa: F401,F403
+from .operators import __all__ as _op_all
 
-__all__ = list(_kpm_all) + list(_gql_all) + list(_mlp_all)
+__all__ = list(_kpm_all) + list(_gql_all) + list(_op_all) + list(_mlp_all)
