@@ -278,6 +278,7 @@ def run_ours(args):
     mixed = None if args.no_mixed else measure_mixed_precision(seed, dev, dist)
     motifs = None if args.no_motifs else measure_motifs(seed)
     gql = None if args.no_gql else measure_gql(seed)
+    ops = None if args.no_operators else measure_operators(seed)
     ms, e2e_s = max_over_ranks(dist, [ms, e2e_s], dev)
     if rank != 0:
         if dist is not None:
@@ -336,6 +337,8 @@ def run_ours(args):
         out["motif_filters"] = motifs
     if gql is not None:
         out["gql"] = gql
+    if ops is not None:
+        out["operators"] = ops
     if not args.no_time_to_l1:
         out["time_to_l1"] = time_to_l1(src_d, dst_d, n_nodes, seed, with_learned=not args.no_learned)
     if not args.no_cpu_baseline:
@@ -659,6 +662,38 @@ def measure_gql(seed, reps: int = 3) -> dict:
 
 
 # ---------------------------------------------------------------------------
+# other graph operators (Eq. (5) shift and scale)
+# ---------------------------------------------------------------------------
+def measure_operators(seed, m: int = 200, nz: int = 16, reps: int = 3) -> dict:
+    """DOS moments of A, D - A (Gershgorin interval), I - H and H on the
+    1.1M-node graph (M = 200, Nz = 16): call time and algorithmic GB/s of the
+    fused steps (same bytes per step as H's)."""
+    import torch
+
+    import paper_1905_09758_gb300 as nd
+
+    src, dst, n = make_edges(seed)
+    g = nd.dos_build_csr(torch.from_numpy(src).cuda(), torch.from_numpy(dst).cuda(), n)
+    info = g.info()
+    b_step = step_bytes(info["n"], info["nnz"], nz, False)
+    out = {"workload": "chung_lu_1M_twins_50k (unfiltered)", "M": m, "Nz": nz, "operators": {}}
+    for op in ("normalized_adjacency", "adjacency", "laplacian", "normalized_laplacian"):
+        nd.dos_moments_op(g, op, m, nz, seed)
+        torch.cuda.synchronize()
+        best = None
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            d, iv = nd.dos_moments_op(g, op, m, nz, seed)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            best = dt if best is None or dt < best else best
+        out["operators"][op] = {"interval": [round(iv[0], 3), round(iv[1], 3)], "call_ms": round(1e3 * best, 3),
+                                "step_gbs": round((m // 2) * b_step / best / 1e9, 1),
+                                "d1": round(float(d[1]), 6)}
+    return out
+
+
+# ---------------------------------------------------------------------------
 # learned reconstruction: trained on a graph family, applied to the workload
 # ---------------------------------------------------------------------------
 LEARN = {"train_graphs": 1600, "family": "Chung-Lu gamma U[2.1,3.0], mean degree U[5,30], N U[1e4,8e4], "
@@ -805,6 +840,7 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-motifs", action="store_true")
     ap.add_argument("--no-gql", action="store_true")
+    ap.add_argument("--no-operators", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--ref-steps-per-sample", type=int, default=3)
     args = ap.parse_args()

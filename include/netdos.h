@@ -194,6 +194,36 @@ void dos_filter_destroy(dos_filter_t f);
 int dos_moments(dos_graph_t g, dos_filter_t f, int M, int Nz, uint64_t seed,
                 int prec, double* d_out, void* stream);
 
+/* Graph operators of dos_moments_op (§2.1). */
+enum {
+  DOS_OP_NORMALIZED_ADJACENCY = 0, /* H = D^{-1/2} A D^{-1/2}, spectrum in [-1, 1] */
+  DOS_OP_ADJACENCY = 1,            /* A */
+  DOS_OP_LAPLACIAN = 2,            /* L = D - A */
+  DOS_OP_NORMALIZED_LAPLACIAN = 3  /* I - H, spectrum in [0, 2] */
+};
+
+/*
+ * dos_moments_op -- DOS moments of another graph operator X.
+ * Paper: §2.1 (the operators), Eq. (5) (an interval [a, b] holding the
+ * spectrum is mapped onto [-1, 1]: X~ = (X - c) / r, c = (a + b) / 2,
+ * r = (b - a) / 2), then §3.1 as dos_moments on X~ (doubling, Eq. (6), (9),
+ * (11)).  d_m = tr T_m(X~) / N estimated from Nz Rademacher probes (the
+ * probes of dos_moments for the same seed).
+ *   op   DOS_OP_*.  H: [a, b] = [-1, 1] (= dos_moments without a filter);
+ *        I - H: [0, 2], its moments are (-1)^m those of H; the random-walk
+ *        matrix D^{-1} A = D^{-1/2} H D^{1/2} has the spectrum of H.
+ *        A and D - A: [a, b] = [lo, hi] if lo < hi, else the Gershgorin
+ *        interval [-d_max, d_max] (A) or [0, 2 d_max] (D - A).
+ *   d_out        [device] double[M]
+ *   interval_out [host] double[2] receives [a, b] (may be NULL).
+ *   prec as dos_moments.  Stream-ordered (the Gershgorin interval
+ *   synchronises `stream`).
+ * Errors: DOS_EINVAL (unknown operator, ...), as dos_moments otherwise.
+ */
+int dos_moments_op(dos_graph_t g, int op, double lo, double hi, int M, int Nz,
+                   uint64_t seed, int prec, double* d_out,
+                   double* interval_out, void* stream);
+
 /*
  * ldos_moments -- per-node (pointwise) moments, and the DOS moments from them.
  * Paper: §2.2 Eq. (2) (LDOS), Eq. (10) (d_mk = T_m(H)_kk), Eq. (12) (diagonal

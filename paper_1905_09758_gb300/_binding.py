@@ -21,6 +21,7 @@ PREC = {"fp32": 0, "bf16": 1, "fp16": 2}
 KERNEL = {"none": 0, "jackson": 1}
 DOS_INPUT_HOST = 1
 MOTIF = {"open": 1, "closed": 2, "pendant": 4}
+OPERATOR = {"normalized_adjacency": 0, "adjacency": 1, "laplacian": 2, "normalized_laplacian": 3}
 
 _STATUS_NAMES = {
     DOS_EINVAL: "DOS_EINVAL",
@@ -84,6 +85,7 @@ _SIGNATURES = {
     "dos_hist_normalize": ([_vp, _i32, _i64, _vp, _vp], _i32),
     "dos_hist_assemble": ([_vp, _i32, _i64, _dbl, _vp, _i32, _vp, _vp], _i32),
     "dos_lanczos": ([_vp, _i32, _i32, _u64, _vp, _vp, _vp, _vp], _i32),
+    "dos_moments_op": ([_vp, _i32, _dbl, _dbl, _i32, _i32, _u64, _i32, _vp, _vp, _vp], _i32),
     "dos_gauss_rules": ([_vp, _vp, _vp, _i32, _i32, _vp, _vp, _vp], _i32),
     "dos_gql_moments": ([_vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp], _i32),
     "dos_gql_histogram": ([_vp, _vp, _i32, _i32, _i32, _vp, _vp], _i32),
@@ -651,3 +653,23 @@ def dos_gql_histogram(nodes, weights, n_bins: int, stream=None) -> torch.Tensor:
     h = torch.empty(n_bins, dtype=torch.float64, device=nodes.device)
     _check(lib().dos_gql_histogram(_ptr(nodes), _ptr(weights), m, nz, int(n_bins), _ptr(h), _stream(stream)))
     return h
+
+
+# ---------------------------------------------------------------------------
+# other graph operators (Eq. (5) shift and scale)
+# ---------------------------------------------------------------------------
+def dos_moments_op(g: Graph, op: str, M: int, Nz: int, seed: int, prec: str = "fp32", interval=None,
+                   d_out: torch.Tensor | None = None, stream=None):
+    """DOS moments of (X - c) / r for X = "adjacency", "laplacian",
+    "normalized_laplacian" or "normalized_adjacency"; interval [a, b] (None:
+    Gershgorin for A and D - A).  Returns (d float64 CUDA (M,), (a, b))."""
+    if op not in OPERATOR:
+        raise ValueError(f"unknown operator {op!r}; one of {sorted(OPERATOR)}")
+    if d_out is None:
+        d_out = torch.empty(M, dtype=torch.float64, device=torch.device("cuda", torch.cuda.current_device()))
+    _need_cuda(d_out, torch.float64, "d_out", M)
+    lo, hi = (0.0, 0.0) if interval is None else (float(interval[0]), float(interval[1]))
+    iv = (C.c_double * 2)()
+    _check(lib().dos_moments_op(g.handle, OPERATOR[op], lo, hi, int(M), int(Nz), int(seed) & (2**64 - 1), PREC[prec],
+                                _ptr(d_out), iv, _stream(stream)))
+    return d_out, (iv[0], iv[1])

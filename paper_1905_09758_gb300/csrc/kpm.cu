@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(256) k_reduce_partials(const double* __restric
 // DOS (doubled): raw[0] = <V0,V0>, step k: raw[1+2k] = <V_{k+1},V_{k+1}>,
 // raw[2+2k] = <V_{k+1},V_k>.  LDOS (direct): raw[m] = mu_m.
 __global__ void k_moments_from_raw(const double* __restrict__ raw, int M, int doubled, double norm,
-                                   const int* __restrict__ err, double* __restrict__ d) {
+                                   const int* __restrict__ err, int negate_odd, double* __restrict__ d) {
   const bool failed = err && *err != 0;  // a bounded wait gave up: no valid moments
   for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) {
     if (failed) {
@@ -74,8 +74,19 @@ __global__ void k_moments_from_raw(const double* __restrict__ raw, int M, int do
       const int k = (m - 1) / 2;
       mu = 2.0 * raw[2 + 2 * k] - raw[2];
     }
-    d[m] = mu / norm;
+    d[m] = (negate_odd && (m & 1) ? -mu : mu) / norm;
   }
+}
+
+// largest degree (the first degree-sorted row of a single graph; a batch
+// orders rows graph by graph inside the degree classes)
+__global__ void k_max_deg(const int32_t* __restrict__ deg, int64_t n, int* __restrict__ out) {
+  int v = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    v = max(v, deg[i]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, v);
 }
 
 __global__ void k_fill_f32(float* __restrict__ p, int64_t n, float v) {
@@ -202,9 +213,17 @@ int make_plan(const Graph* G, int Nz, int prec, int mode, Plan* out) {
   return DOS_OK;
 }
 
+// operator of a KPM run: kind (0 H, 1 A, 2 D - A), shift c and 1/r (Eq. (5)),
+// and whether odd moments change sign (I - H = -(H) after the shift by 1)
+struct OpSpec {
+  int kind = 0;
+  double c = 0.0, inv_r = 1.0;
+  int negate_odd = 0;
+};
+
 template <typename T>
 static int run_steps(const Graph* G, const Filter* F, const Plan& plan, int M, int Nz, uint64_t seed, int mode,
-                     double* d_out, float* C_out, cudaStream_t s) {
+                     double* d_out, float* C_out, cudaStream_t s, const OpSpec& op = OpSpec()) {
   constexpr int V = VecT<T>::N;
   const int64_t n = G->n;
   const int steps = mode == kModeDos ? M / 2 : M - 1;
@@ -245,6 +264,7 @@ static int run_steps(const Graph* G, const Filter* F, const Plan& plan, int M, i
   ip.nz_pad = plan.nz_pad;
   ip.seed = seed;
   ip.partial = partial;
+  ip.unscaled = op.kind != 0 ? 1 : 0;
   if (F && F->n_classes > 0 && st == DOS_OK) {
     if ((st = dalloc_t(&csum, static_cast<size_t>(F->n_classes) * plan.nz_pad, s)) == DOS_OK) {
       cu(cudaMemsetAsync(csum, 0, sizeof(float) * F->n_classes * plan.nz_pad, s), "cudaMemsetAsync");
@@ -286,6 +306,9 @@ static int run_steps(const Graph* G, const Filter* F, const Plan& plan, int M, i
   prm.inv_nz = 1.0f / static_cast<float>(Nz);
   prm.seed = seed;
   prm.ldos_atomic = plan.tiles > 1 ? 1 : 0;
+  prm.op = op.kind;
+  prm.op_c = static_cast<float>(op.c);
+  prm.op_inv_r = static_cast<float>(op.inv_r);
   const bool prof = profiling_on();
   SideStreams side;
   if (st == DOS_OK) st = side_streams(&side);
@@ -296,7 +319,7 @@ static int run_steps(const Graph* G, const Filter* F, const Plan& plan, int M, i
     prm.partial = partial + static_cast<size_t>(1 + static_cast<int64_t>(k) * n_dots) * width;
     prm.ldos = mode == kModeLdos ? C_out + static_cast<size_t>(k + 1) * n : nullptr;
     if (prof) profile_begin(s);
-    st = launch_step<T>(plan, mode, prm, s, side);
+    st = launch_step<T>(plan, mode == kModeDos && op.kind != 0 ? kModeDosOp : mode, prm, s, side);
     if (prof) profile_end(s);
   }
   if (st == DOS_OK) {
@@ -306,7 +329,7 @@ static int run_steps(const Graph* G, const Filter* F, const Plan& plan, int M, i
   }
   if (st == DOS_OK && d_out) {
     const double r = F ? static_cast<double>(n - F->removed) : static_cast<double>(n);
-    k_moments_from_raw<<<1, 256, 0, s>>>(raw, M, mode == kModeDos ? 1 : 0, r * Nz, prm.err, d_out);
+    k_moments_from_raw<<<1, 256, 0, s>>>(raw, M, mode == kModeDos ? 1 : 0, r * Nz, prm.err, op.negate_odd, d_out);
     count_launch();
     cu(cudaGetLastError(), "k_moments_from_raw");
   }
@@ -315,7 +338,7 @@ static int run_steps(const Graph* G, const Filter* F, const Plan& plan, int M, i
 }
 
 static int run_kpm(const Graph* G, const Filter* F, int M, int Nz, uint64_t seed, int prec, int mode,
-                   double* d_out, float* C_out, cudaStream_t s) {
+                   double* d_out, float* C_out, cudaStream_t s, const OpSpec& op = OpSpec()) {
   if (!G) return fail(DOS_EINVAL, "null graph");
   if (G->n < 1) return fail(DOS_EINVAL, "graph has no edges");
   if (M < 1 || M > (1 << 20)) return fail(DOS_EINVAL, "M must be in [1, 2^20]");
@@ -326,11 +349,11 @@ static int run_kpm(const Graph* G, const Filter* F, int M, int Nz, uint64_t seed
   NDOS_CHECK(make_plan(G, Nz, prec, mode, &plan));
   switch (prec) {
     case DOS_BF16:
-      return run_steps<__nv_bfloat16>(G, F, plan, M, Nz, seed, mode, d_out, C_out, s);
+      return run_steps<__nv_bfloat16>(G, F, plan, M, Nz, seed, mode, d_out, C_out, s, op);
     case DOS_FP16:
-      return run_steps<__half>(G, F, plan, M, Nz, seed, mode, d_out, C_out, s);
+      return run_steps<__half>(G, F, plan, M, Nz, seed, mode, d_out, C_out, s, op);
     default:
-      return run_steps<float>(G, F, plan, M, Nz, seed, mode, d_out, C_out, s);
+      return run_steps<float>(G, F, plan, M, Nz, seed, mode, d_out, C_out, s, op);
   }
 }
 
@@ -354,6 +377,57 @@ int ldos_moments(dos_graph_t g, int M, int Nz, uint64_t seed, int prec, float* C
   if (!C_out) return fail(DOS_EINVAL, "ldos_moments: C_out is NULL");
   return run_kpm(reinterpret_cast<const Graph*>(g), nullptr, M, Nz, seed, prec, kModeLdos, d_out, C_out,
                  static_cast<cudaStream_t>(stream));
+}
+
+int dos_moments_op(dos_graph_t g, int op, double lo, double hi, int M, int Nz, uint64_t seed, int prec,
+                   double* d_out, double* interval_out, void* stream) {
+  clear_error();
+  if (!g || !d_out) return fail(DOS_EINVAL, "dos_moments_op: null argument");
+  const Graph* G = reinterpret_cast<const Graph*>(g);
+  if (G->n < 1) return fail(DOS_EINVAL, "dos_moments_op: graph has no edges");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  OpSpec spec;
+  double a = -1.0, b = 1.0;
+  switch (op) {
+    case DOS_OP_NORMALIZED_ADJACENCY:
+      break;
+    case DOS_OP_NORMALIZED_LAPLACIAN:  // I - H on [0, 2]: (I - H) - 1 = -H
+      a = 0.0;
+      b = 2.0;
+      spec.negate_odd = 1;
+      break;
+    case DOS_OP_ADJACENCY:
+    case DOS_OP_LAPLACIAN: {
+      spec.kind = op == DOS_OP_ADJACENCY ? 1 : 2;
+      if (lo < hi) {
+        a = lo;
+        b = hi;
+      } else {  // Gershgorin discs: [-d_max, d_max] for A, [0, 2 d_max] for D - A
+        Temps t(s);
+        int* dmax_d = nullptr;
+        NDOS_CHECK(t.get(&dmax_d, 1));
+        NDOS_CUDA(cudaMemsetAsync(dmax_d, 0, sizeof(int), s));
+        const unsigned blocks = static_cast<unsigned>(std::min<int64_t>((G->n + 255) / 256, 1024));
+        k_max_deg<<<blocks, 256, 0, s>>>(G->p_deg, G->n, dmax_d);
+        NDOS_LAUNCHED();
+        int dmax = 0;
+        NDOS_CUDA(cudaMemcpyAsync(&dmax, dmax_d, sizeof(int), cudaMemcpyDeviceToHost, s));
+        NDOS_CUDA(cudaStreamSynchronize(s));
+        a = op == DOS_OP_ADJACENCY ? -static_cast<double>(dmax) : 0.0;
+        b = op == DOS_OP_ADJACENCY ? static_cast<double>(dmax) : 2.0 * dmax;
+      }
+      spec.c = 0.5 * (a + b);
+      spec.inv_r = 2.0 / (b - a);
+      break;
+    }
+    default:
+      return fail(DOS_EINVAL, "dos_moments_op: unknown operator");
+  }
+  if (interval_out) {
+    interval_out[0] = a;
+    interval_out[1] = b;
+  }
+  return run_kpm(G, nullptr, M, Nz, seed, prec, kModeDos, d_out, nullptr, s, spec);
 }
 
 int dos_set_plan(int tile_width, int ctas_per_sm) {

@@ -36,7 +36,10 @@ namespace netdos {
 constexpr int kStepThreads = 256;
 constexpr int kStepWarps = kStepThreads / 32;
 
-enum StepMode { kModeDos = 0, kModeLdos = 1 };
+// DOS: fused moment dots on H; LDOS: per-node products on H; DOS_OP: fused
+// moment dots on another operator (A or D - A, shifted and scaled), a
+// separate instance so that the H kernels carry no operator code
+enum StepMode { kModeDos = 0, kModeLdos = 1, kModeDosOp = 2 };
 
 template <typename T>
 struct VecT;
@@ -194,6 +197,12 @@ struct StepParams {
   int64_t part_width;
   int64_t mid_part_off;    // medium CTAs write partial[mid_part_off + tile * grid + blockIdx.x]
   int64_t light_part_off;  // light CTAs write partial[light_part_off + blockIdx.x]
+  // operator of the kModeDosOp instances: 1 the adjacency A, 2 the Laplacian
+  // D - A, shifted and scaled to (X - op_c) * op_inv_r (Eq. (5)) on unscaled
+  // vectors (U = V, dot weight 1); the other modes run on H (U = S V, dot
+  // weight d_i)
+  int op;
+  float op_c, op_inv_r;
   float* ldos;      // LDOS: C_out + m * n_compact, indexed by compact id
   int ldos_atomic;  // 1 when several tiles add into the same C entry
   int* err;         // device error word
@@ -214,13 +223,22 @@ __device__ __forceinline__ void step_epilogue(const StepParams& prm, bool active
     const size_t off = (static_cast<size_t>(tile) * prm.n + p) * TW + ql * V;
     uint4* pn = reinterpret_cast<uint4*>(reinterpret_cast<T*>(prm.u_pn) + off);
     float u[V];
-    const float sc = (prm.first ? 1.0f : 2.0f) / fd;
+    if (MODE != kModeDosOp) {
+      const float sc = (prm.first ? 1.0f : 2.0f) / fd;
 #pragma unroll
-    for (int v = 0; v < V; ++v) u[v] = fmaf(acc[v], sc, -prev[v]);
+      for (int v = 0; v < V; ++v) u[v] = fmaf(acc[v], sc, -prev[v]);
+    } else {
+      // X~ U = ca * (A U) + co * U row-wise: A: (1/r, -c/r); D - A: (-1/r, (d_i - c)/r)
+      const float mult = prm.first ? 1.0f : 2.0f;
+      const float ca = (prm.op == 1 ? prm.op_inv_r : -prm.op_inv_r) * mult;
+      const float co = (prm.op == 1 ? -prm.op_c : fd - prm.op_c) * prm.op_inv_r * mult;
+#pragma unroll
+      for (int v = 0; v < V; ++v) u[v] = fmaf(acc[v], ca, fmaf(own[v], co, -prev[v]));
+    }
     const uint4 packed = pack16<T>(u);
     st_stream(pn, packed);
     unpack16<T>(packed, u);  // the dots use the stored (rounded) values
-    if (MODE == kModeDos) {
+    if (MODE != kModeLdos) {
 #pragma unroll
       for (int v = 0; v < V; ++v) {
         prod0 = fmaf(u[v], u[v], prod0);
@@ -240,9 +258,9 @@ __device__ __forceinline__ void step_epilogue(const StepParams& prm, bool active
 #pragma unroll
   for (int s = 1; s < Q; s <<= 1) {
     prod0 += __shfl_xor_sync(0xffffffffu, prod0, s);
-    if (MODE == kModeDos) prod1 += __shfl_xor_sync(0xffffffffu, prod1, s);
+    if (MODE != kModeLdos) prod1 += __shfl_xor_sync(0xffffffffu, prod1, s);
   }
-  if (MODE == kModeDos && prm.gid) {
+  if (MODE != kModeLdos && prm.gid) {
     // batch: per-graph sums.  Rows are grouped by graph, so a warp's rows
     // nearly always share one graph: reduce in the warp and issue one atomic
     // per dot instead of one per row (the rows of a graph all hit the same
@@ -250,8 +268,9 @@ __device__ __forceinline__ void step_epilogue(const StepParams& prm, bool active
     const int32_t g = active ? prm.gid[p] : -1;
     const int32_t g0 = __shfl_sync(0xffffffffu, g, 0);
     const bool uniform = __all_sync(0xffffffffu, !active || g == g0);
-    double a0 = active && owner ? static_cast<double>(fd * prod0) : 0.0;
-    double a1 = active && owner ? static_cast<double>(fd * prod1) : 0.0;
+    const float wd = MODE == kModeDosOp ? 1.0f : fd;  // <V_a, V_b> = sum_i w_i <U_a, U_b>_i
+    double a0 = active && owner ? static_cast<double>(wd * prod0) : 0.0;
+    double a1 = active && owner ? static_cast<double>(wd * prod1) : 0.0;
     if (uniform) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
@@ -269,9 +288,10 @@ __device__ __forceinline__ void step_epilogue(const StepParams& prm, bool active
     return;
   }
   if (active && owner) {
-    if (MODE == kModeDos) {
-      dd0 += static_cast<double>(fd * prod0);
-      dd1 += static_cast<double>(fd * prod1);
+    if (MODE != kModeLdos) {
+      const float wd = MODE == kModeDosOp ? 1.0f : fd;  // <V_a, V_b> = sum_i w_i <U_a, U_b>_i
+      dd0 += static_cast<double>(wd * prod0);
+      dd1 += static_cast<double>(wd * prod1);
     } else {
       const float vsum = prod0 * sqrtf(fd);  // sum_j z_j (V_{k+1})_j of this tile
       dd0 += static_cast<double>(vsum);
@@ -372,7 +392,7 @@ __global__ void __launch_bounds__(kStepThreads) k_cheb_heavy(const StepParams pr
     if (warp == 0) {
       if (!prm.first)
         unpack16<T>(ld_stream(reinterpret_cast<const uint4*>(reinterpret_cast<const T*>(prm.u_pn) + off)), prev);
-      if (MODE == kModeDos)
+      if (MODE != kModeLdos)
         unpack16<T>(ld_gather(reinterpret_cast<const uint4*>(reinterpret_cast<const T*>(prm.u_cur) + off)), own);
       else {
         orig = static_cast<uint32_t>(prm.orig[p]);
@@ -418,7 +438,7 @@ __global__ void __launch_bounds__(kStepThreads) k_cheb_heavy(const StepParams pr
   if (threadIdx.x == 0) {
     const size_t i = static_cast<size_t>(tile) * gridDim.x + blockIdx.x;
     prm.partial[i] = dd0;
-    if (MODE == kModeDos) prm.partial[prm.part_width + i] = dd1;
+    if (MODE != kModeLdos) prm.partial[prm.part_width + i] = dd1;
   }
 }
 
@@ -451,7 +471,7 @@ __global__ void __launch_bounds__(kStepThreads) k_cheb_medium(const StepParams p
     uint32_t orig = 0;
     int32_t compact = 0;
     if (!prm.first) unpack16<T>(ld_stream(reinterpret_cast<const uint4*>(reinterpret_cast<const T*>(prm.u_pn) + off)), prev);
-    if (MODE == kModeDos)
+    if (MODE != kModeLdos)
       unpack16<T>(ld_gather(reinterpret_cast<const uint4*>(reinterpret_cast<const T*>(prm.u_cur) + off)), own);
     else {
       orig = static_cast<uint32_t>(prm.orig[p]);
@@ -482,7 +502,7 @@ __global__ void __launch_bounds__(kStepThreads) k_cheb_medium(const StepParams p
   if (threadIdx.x == 0) {
     const size_t i = static_cast<size_t>(prm.mid_part_off) + static_cast<size_t>(tile) * gridDim.x + blockIdx.x;
     prm.partial[i] = dd0;
-    if (MODE == kModeDos) prm.partial[prm.part_width + i] = dd1;
+    if (MODE != kModeLdos) prm.partial[prm.part_width + i] = dd1;
   }
 }
 
@@ -510,7 +530,7 @@ struct RoundLayout {
   static constexpr int off_col = off_rp + RP;
   static constexpr int off_prev = off_col + COL;
   static constexpr int off_aux = off_prev + BLK;
-  static constexpr int SLOT = off_aux + (MODE == kModeDos ? BLK : 2 * IDS);
+  static constexpr int SLOT = off_aux + (MODE != kModeLdos ? BLK : 2 * IDS);
   static constexpr int WARP = 2 * SLOT;  // two slots per warp
 };
 
@@ -571,13 +591,13 @@ __global__ void __launch_bounds__(kStepThreads, 3) k_cheb_light(const StepParams
     const uint32_t col_bytes = static_cast<uint32_t>((((e1 + 3) & ~int64_t(3)) - ea) * 4);
     const uint32_t blk_bytes = static_cast<uint32_t>((r1 - r0) * ROWB);
     const uint32_t id_bytes = static_cast<uint32_t>((((r1 + 3) & ~int64_t(3)) - r0i) * 4);
-    uint32_t tx = rp_bytes + col_bytes + (prm.first ? 0u : blk_bytes) + (MODE == kModeDos ? blk_bytes : 2 * id_bytes);
+    uint32_t tx = rp_bytes + col_bytes + (prm.first ? 0u : blk_bytes) + (MODE != kModeLdos ? blk_bytes : 2 * id_bytes);
     mbar_arrive_expect_tx(&bar[s], tx);
     const size_t row_off = (static_cast<size_t>(c.tile) * prm.n + r0) * TW;
     bulk_g2s(sl + L::off_rp, prm.row_ptr + r0a, rp_bytes, &bar[s]);
     bulk_g2s(sl + L::off_col, prm.col + ea, col_bytes, &bar[s]);
     if (!prm.first) bulk_g2s(sl + L::off_prev, reinterpret_cast<const T*>(prm.u_pn) + row_off, blk_bytes, &bar[s]);
-    if (MODE == kModeDos) {
+    if (MODE != kModeLdos) {
       bulk_g2s(sl + L::off_aux, reinterpret_cast<const T*>(prm.u_cur) + row_off, blk_bytes, &bar[s]);
     } else {
       bulk_g2s(sl + L::off_aux, prm.orig + r0i, id_bytes, &bar[s]);
@@ -653,7 +673,7 @@ __global__ void __launch_bounds__(kStepThreads, 3) k_cheb_light(const StepParams
       beg = rp[grp];
       end = rp[grp + 1];
       if (!prm.first) unpack16<T>(*reinterpret_cast<const uint4*>(sl + L::off_prev + grp * ROWB + ql * 16), prev);
-      if (MODE == kModeDos) {
+      if (MODE != kModeLdos) {
         unpack16<T>(*reinterpret_cast<const uint4*>(sl + L::off_aux + grp * ROWB + ql * 16), own);
       } else {
         orig = static_cast<uint32_t>(reinterpret_cast<const int32_t*>(sl + L::off_aux)[r0 + grp - r0i]);
@@ -680,7 +700,7 @@ __global__ void __launch_bounds__(kStepThreads, 3) k_cheb_light(const StepParams
   if (threadIdx.x == 0) {
     const size_t i = static_cast<size_t>(prm.light_part_off) + blockIdx.x;
     prm.partial[i] = dd0;
-    if (MODE == kModeDos) prm.partial[prm.part_width + i] = dd1;
+    if (MODE != kModeLdos) prm.partial[prm.part_width + i] = dd1;
   }
 }
 
@@ -698,6 +718,7 @@ struct InitParams {
   int nz, nz_pad;
   uint64_t seed;
   double* partial;  // [gridDim.x]: sum of squares of V_0
+  int unscaled;     // 1: U_0 = Z (operators A, D - A), else U_0 = S Z
 };
 
 __device__ __forceinline__ float probe_value(uint64_t word, int j, int nz) {
@@ -725,7 +746,7 @@ __global__ void __launch_bounds__(256) k_init_block(const InitParams prm) {
 #pragma unroll
       for (int v = 0; v < V; ++v) z[v] = probe_value(word, j0 + v, prm.nz);
     }
-    const float s = prm.s32[prm.compact[p]];
+    const float s = prm.unscaled ? 1.0f : prm.s32[prm.compact[p]];
     float u[V];
     float sq = 0.f;
 #pragma unroll
@@ -803,6 +824,11 @@ int launch_step_q(const Plan& plan, const StepParams& prm, cudaStream_t s, const
     if (fork) NDOS_CUDA(cudaEventRecord(side.join_b, ms));
   }
   if (prm.n > prm.n_mid && plan.light_ctas > 0) {
+    if (MODE == kModeDosOp) {  // the plan was made for kModeDos (same layout): raise this instance's limit
+      int smem = 0, ctas = 0;
+      const int st = light_config_q<T, Q, MODE>(&smem, &ctas);
+      if (st != DOS_OK) return st;
+    }
     k_cheb_light<T, Q, MODE><<<plan.light_ctas, kStepThreads, plan.smem, s>>>(prm);
     NDOS_LAUNCHED();
   }
@@ -832,9 +858,10 @@ int launch_step_q(const Plan& plan, const StepParams& prm, cudaStream_t s, const
 // Chebyshev step launch for storage type T (instantiated in kpm_<type>.cu)
 template <typename T>
 int launch_step(const Plan& plan, int mode, const StepParams& prm, cudaStream_t s, const SideStreams& side) {
-#define NDOS_LAUNCH_CALL(TT, QQ)                                     \
-  (mode == kModeDos ? launch_step_q<TT, QQ, kModeDos>(plan, prm, s, side) \
-                    : launch_step_q<TT, QQ, kModeLdos>(plan, prm, s, side))
+#define NDOS_LAUNCH_CALL(TT, QQ)                                                    \
+  (mode == kModeDos   ? launch_step_q<TT, QQ, kModeDos>(plan, prm, s, side)         \
+   : mode == kModeLdos ? launch_step_q<TT, QQ, kModeLdos>(plan, prm, s, side)       \
+                       : launch_step_q<TT, QQ, kModeDosOp>(plan, prm, s, side))
   NDOS_DISPATCH_Q(T, plan.q, NDOS_LAUNCH_CALL)
 #undef NDOS_LAUNCH_CALL
   return fail(DOS_EINVAL, "unsupported tile width");
