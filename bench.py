@@ -341,6 +341,8 @@ def run_ours(args):
         out["operators"] = ops
     if not args.no_time_to_l1:
         out["time_to_l1"] = time_to_l1(src_d, dst_d, n_nodes, seed, with_learned=not args.no_learned)
+    if args.scale_1b:
+        out["scale_1e9_edges"] = measure_scale(seed)
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(src_np, dst_np, n_nodes, budget_s=args.cpu_seconds)
     print(json.dumps(out), flush=True)
@@ -701,6 +703,9 @@ LEARN = {"train_graphs": 1600, "family": "Chung-Lu gamma U[2.1,3.0], mean degree
          "Nz_ref": 256, "hidden": [512, 512], "steps": 16000, "batch": 256, "lr": 2e-3, "seed": 11}
 
 
+_TRAINED = {}  # the network trained by learned_leg, reused by measure_scale
+
+
 def _family_member(k: int):
     import synthgraphs as sg
 
@@ -729,6 +734,7 @@ def learned_leg(g, h_ref, seed: int, timed_reps: int = 3) -> dict:
     t1 = time.perf_counter()
     rec = learned.train(x, t, LEARN["M_in"], LEARN["Nz_in"], hidden=LEARN["hidden"], steps=LEARN["steps"],
                         batch=LEARN["batch"], lr=LEARN["lr"], seed=LEARN["seed"])
+    _TRAINED["rec"] = rec
     torch.cuda.synchronize()
     t2 = time.perf_counter()
 
@@ -747,6 +753,82 @@ def learned_leg(g, h_ref, seed: int, timed_reps: int = 3) -> dict:
     l1 = float(np.abs(h.cpu().numpy() - h_ref).sum())
     return {"prec": "learned", "M": LEARN["M_in"], "Nz": LEARN["Nz_in"], "seconds": round(statistics.median(times), 5),
             "l1": round(l1, 5), "train": dict(LEARN, data_s=round(t1 - t0, 1), train_s=round(t2 - t1, 1))}
+
+
+# ---------------------------------------------------------------------------
+# scale: the 60M-node, 1e9-edge Chung-Lu graph (opt-in, --scale-1b)
+# ---------------------------------------------------------------------------
+SCALE = {"graph": "Chung-Lu gamma=2.5 mean_deg=33.33 N=60,000,000 (1.0e9 edges, ~2e9 stored nonzeros), drawn on "
+         "the device", "N": 60_000_000, "gamma": 2.5, "mean_degree": 2e9 / 60e6, "Nz": 10, "M_kpm": 200,
+         "M_learned": 50, "M_ref": 500, "Nz_ref": 32}
+
+
+def measure_scale(seed, reps: int = 2) -> dict:
+    """CSR build, twin filter and filtered KPM on the 60M-node graph: Jackson
+    KPM at M = 200 against the learned reconstruction from M = 50 (Nz = 10),
+    each timed (filter + moments + density) and compared in L1 with a filtered
+    M = 500, Nz = 32 reference of an independent seed."""
+    import torch
+
+    import paper_1905_09758_gb300 as nd
+    import synthgraphs as sg
+    from paper_1905_09758_gb300 import learned
+
+    t0 = time.perf_counter()
+    src, dst, n = sg.chung_lu_device(SCALE["N"], SCALE["gamma"], SCALE["mean_degree"], seed + 60)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    g = nd.dos_build_csr(src, dst, n)
+    torch.cuda.synchronize()
+    t_build = time.perf_counter() - t0
+    n_edges = int(src.numel())
+    del src, dst
+    torch.cuda.empty_cache()
+    info = g.info()
+    nz = SCALE["Nz"]
+    out = {"workload": "chung_lu_60M_1e9_edges", **SCALE, "n_edges": n_edges, "n_compact": info["n"],
+           "nnz": info["nnz"], "n_isolated": info["n_isolated"], "generate_s": round(t_gen, 2),
+           "csr_build_s": round(t_build, 2), "plan": nd.dos_get_plan(g, nz)}
+    f = nd.dos_motif_filter(g)
+    d_ref = nd.dos_moments(g, SCALE["M_ref"], SCALE["Nz_ref"], seed + 4242, filter=f)
+    h_ref = nd.density_with_spikes(d_ref, g, BINS, filter=f).cpu().numpy()
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        best, h = None, None
+        for _ in range(reps):
+            ta = time.perf_counter()
+            h = fn()
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - ta
+            best = dt if best is None or dt < best else best
+        return best, float(np.abs(h.cpu().numpy() - h_ref).sum())
+
+    def kpm():
+        ff = nd.dos_motif_filter(g)
+        return nd.density_with_spikes(nd.dos_moments(g, SCALE["M_kpm"], nz, seed, filter=ff), g, BINS, filter=ff)
+
+    nd.dos_profile_enable(True)
+    nd.dos_profile_read(reset=True)
+    t_kpm, l1_kpm = timed(kpm)
+    step_ms, launches = nd.dos_profile_read(reset=True)
+    nd.dos_profile_enable(False)
+    b_step = step_bytes(info["n"], info["nnz"], nz, False)
+    out["kpm"] = {"M": SCALE["M_kpm"], "seconds": round(t_kpm, 4), "l1": round(l1_kpm, 5),
+                  "avg_step_ms": round(step_ms / max(1, launches), 3),
+                  "step_gbs": round(b_step / (step_ms / max(1, launches) * 1e-3) / 1e9, 1)}
+    rec = _TRAINED.get("rec")
+    if rec is not None:
+        def lrn():
+            ff = nd.dos_motif_filter(g)
+            return learned.reconstruct(rec, g, ff, seed)
+
+        t_l, l1_l = timed(lrn)
+        out["learned"] = {"M": rec.m_in, "Nz": rec.nz_in, "seconds": round(t_l, 4), "l1": round(l1_l, 5),
+                          "note": "network of the time_to_l1 learned leg (trained on N <= 8e4)"}
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -841,6 +923,8 @@ def main():
     ap.add_argument("--no-motifs", action="store_true")
     ap.add_argument("--no-gql", action="store_true")
     ap.add_argument("--no-operators", action="store_true")
+    ap.add_argument("--scale-1b", action="store_true",
+                    help="also run the 60M-node, 1e9-edge graph (about 100 GB of device memory, a few minutes)")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--ref-steps-per-sample", type=int, default=3)
     args = ap.parse_args()

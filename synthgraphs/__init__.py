@@ -34,6 +34,7 @@ import numpy as np
 __all__ = [
     "erdos_renyi",
     "chung_lu",
+    "chung_lu_device",
     "barabasi_albert",
     "add_twin_leaves",
     "add_triangle_twins",
@@ -147,6 +148,35 @@ def chung_lu(n: int, gamma: float, mean_degree: float, seed: int, i0: float = 10
     dst = np.searchsorted(cdf, rng.random(m), side="right").astype(np.int64)
     np.minimum(src, n - 1, out=src)
     np.minimum(dst, n - 1, out=dst)
+    return src, dst, n
+
+
+def chung_lu_device(n: int, gamma: float, mean_degree: float, seed: int, device="cuda", i0: float = 10.0,
+                    chunk: int = 1 << 27):
+    """The Chung-Lu model of chung_lu, drawn with torch on a CUDA device for
+    graphs too large to generate on the host (1e9 edges): the same weights and
+    endpoint sampling (uniforms searched in the cumulative weights), from a
+    seeded torch generator on the device, so the draws differ from
+    chung_lu's.  Returns int64 device tensors src, dst and n."""
+    import torch
+
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    i = torch.arange(n, dtype=torch.float64, device=device)
+    w = (i + i0) ** (-1.0 / (gamma - 1.0))
+    w *= mean_degree * n / w.sum()
+    m = int(round(n * mean_degree / 2.0))
+    cdf = torch.cumsum(w, 0)
+    cdf /= cdf[-1].clone()
+    del i, w
+    src = torch.empty(m, dtype=torch.int64, device=device)
+    dst = torch.empty(m, dtype=torch.int64, device=device)
+    for out in (src, dst):
+        for off in range(0, m, chunk):
+            k = min(chunk, m - off)
+            u = torch.rand(k, generator=gen, dtype=torch.float64, device=device)
+            out[off:off + k] = torch.searchsorted(cdf, u, right=True).clamp_(max=n - 1)
+            del u
     return src, dst, n
 
 
