@@ -761,6 +761,10 @@ def learned_leg(g, h_ref, seed: int, timed_reps: int = 3) -> dict:
 SCALE = {"graph": "Chung-Lu gamma=2.5 mean_deg=33.33 N=60,000,000 (1.0e9 edges, ~2e9 stored nonzeros), drawn on "
          "the device", "N": 60_000_000, "gamma": 2.5, "mean_degree": 2e9 / 60e6, "Nz": 10, "M_kpm": 200,
          "M_learned": 50, "M_ref": 500, "Nz_ref": 32}
+# the scale network's training family: large Chung-Lu graphs drawn on the device
+SCALE_LEARN = {"train_graphs": 2000, "family": "Chung-Lu on the device, N log-uniform [1e4, 1e6], gamma U[2.1, 3.0], "
+               "mean degree U[5, 40]", "M_in": 50, "Nz_in": 10, "M_ref": 500, "Nz_ref": 64, "hidden": [512, 512],
+               "steps": 16000, "batch": 256, "lr": 2e-3, "seed": 23}
 
 
 def measure_scale(seed, reps: int = 2) -> dict:
@@ -826,8 +830,27 @@ def measure_scale(seed, reps: int = 2) -> dict:
             return learned.reconstruct(rec, g, ff, seed)
 
         t_l, l1_l = timed(lrn)
-        out["learned"] = {"M": rec.m_in, "Nz": rec.nz_in, "seconds": round(t_l, 4), "l1": round(l1_l, 5),
-                          "note": "network of the time_to_l1 learned leg (trained on N <= 8e4)"}
+        out["learned_small_family"] = {"M": rec.m_in, "Nz": rec.nz_in, "seconds": round(t_l, 4), "l1": round(l1_l, 5),
+                                       "note": "network of the time_to_l1 learned leg (trained on N <= 8e4)"}
+    # a network trained on a family that covers this graph's size and degree range
+    sl = SCALE_LEARN
+    t0 = time.perf_counter()
+    graphs = (sg.chung_lu_device_member(sl["seed"] * 1_000_003 + k) for k in range(sl["train_graphs"]))
+    x, t = learned.training_set(graphs, sl["M_in"], sl["Nz_in"], sl["M_ref"], sl["Nz_ref"], BINS, seed=sl["seed"] * 7919)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    rec2 = learned.train(x, t, sl["M_in"], sl["Nz_in"], hidden=sl["hidden"], steps=sl["steps"], batch=sl["batch"],
+                         lr=sl["lr"], seed=sl["seed"])
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+
+    def lrn2():
+        ff = nd.dos_motif_filter(g)
+        return learned.reconstruct(rec2, g, ff, seed)
+
+    t_l2, l1_l2 = timed(lrn2)
+    out["learned"] = {"M": rec2.m_in, "Nz": rec2.nz_in, "seconds": round(t_l2, 4), "l1": round(l1_l2, 5),
+                      "train": dict(sl, data_s=round(t1 - t0, 1), train_s=round(t2 - t1, 1))}
     return out
 
 

@@ -35,6 +35,7 @@ __all__ = [
     "erdos_renyi",
     "chung_lu",
     "chung_lu_device",
+    "chung_lu_device_member",
     "barabasi_albert",
     "add_twin_leaves",
     "add_triangle_twins",
@@ -178,6 +179,19 @@ def chung_lu_device(n: int, gamma: float, mean_degree: float, seed: int, device=
             out[off:off + k] = torch.searchsorted(cdf, u, right=True).clamp_(max=n - 1)
             del u
     return src, dst, n
+
+
+def chung_lu_device_member(seed: int, n_min: int = 10_000, n_max: int = 1_000_000, deg_min: float = 5.0,
+                           deg_max: float = 40.0, device="cuda"):
+    """One graph of the large Chung-Lu family, drawn on the device: N
+    log-uniform in [n_min, n_max], exponent uniform in [2.1, 3.0], mean
+    degree uniform in [deg_min, deg_max] (parameters from numpy PCG64(seed),
+    edges from chung_lu_device)."""
+    rng = _rng(seed)
+    n = int(round(math.exp(rng.uniform(math.log(n_min), math.log(n_max)))))
+    gam = float(rng.uniform(2.1, 3.0))
+    md = float(rng.uniform(deg_min, deg_max))
+    return chung_lu_device(n, gam, md, int(rng.integers(0, 2**62)), device=device)
 
 
 def barabasi_albert(n: int, m: int, seed: int):
