@@ -26,12 +26,14 @@ Parity status of each function (what pins it, see ``tests/test_oracle_*.py``):
 * ``twin_classes``, ``project_probes``
                                    -- pinned by stars, K_{a,b}, eigenvalue counts
                                       at 0 and the spectrum of P^T H P.
-* ``closed_twin_classes``, ``pendant_twin_classes``, ``motif_classes``
+* ``closed_twin_classes``, ``pendant_twin_classes``, ``parallel_path_classes``,
+  ``motif_classes``
                                    -- pinned by K_n (one class, -1/(n-1)), windmill
                                       graphs (-1/2), disjointness of the open and
                                       closed relations, P5's closed-form spectrum,
                                       spiders (+-1/sqrt 2), Fig. 3's degree-4 pendant
-                                      twins (+-1/2), invariance of the class-
+                                      twins (+-1/2), theta graphs (+-1/2), all motifs
+                                      together, invariance of the class-
                                       constant subspace and the spectrum of P^T H P.
 * ``jackson``, ``bin_integrals``,
   ``histogram``                    -- pinned by g_0 = 1, kernel positivity,

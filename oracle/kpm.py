@@ -34,6 +34,7 @@ __all__ = [
     "closed_twin_classes",
     "motif_classes",
     "pendant_twin_classes",
+    "parallel_path_classes",
     "project_probes",
     "jackson",
     "bin_edges",
@@ -361,7 +362,53 @@ def pendant_twin_classes(g: Csr):
     return class_id, 2 * sum(pairs.values()), pairs
 
 
-def motif_classes(g: Csr, open_twins: bool = True, closed_twins: bool = True, pendant_twins: bool = False):
+def parallel_path_classes(g: Csr):
+    """Classes of parallel 2-node paths between two hosts (the first +-1/2
+    drawing of §3.4, Fig. 3).
+
+    A path E - a - b - F with d(a) = d(b) = 2 and hosts E != F of degree >= 3
+    (E = F would make a, b closed twins; a degree-2 host is itself a path node
+    and would let instances overlap, as on a cycle, so such instances are
+    left unfiltered).  If c >= 2 such paths join the same hosts, the
+    nodes next to the smaller host form one class and those next to the
+    larger host another; the vectors summing to zero over each carry c - 1
+    eigenvalues at each of +-1/2 (H_ab = 1/2, the hosts see zero sums).
+    Returns class_id (smallest member), the removed count 2 sum (c - 1) and
+    the number of removed pairs.
+    """
+    class_id = np.arange(g.n, dtype=np.int32)
+    rp, col = g.row_ptr, g.col
+    deg = np.diff(rp)
+    groups: dict[tuple, list] = {}
+    for a in range(g.n):
+        if deg[a] != 2:
+            continue
+        for b in col[rp[a]:rp[a + 1]]:
+            b = int(b)
+            if b <= a or deg[b] != 2:
+                continue
+            na, nb = col[rp[a]:rp[a + 1]], col[rp[b]:rp[b + 1]]
+            e = int(na[0] if na[1] == b else na[1])
+            f = int(nb[0] if nb[1] == a else nb[1])
+            if e == f or deg[e] < 3 or deg[f] < 3:
+                continue
+            first, second = (a, b) if e < f else (b, a)
+            groups.setdefault((min(e, f), max(e, f)), []).append((first, second))
+    pairs = 0
+    for lst in groups.values():
+        if len(lst) < 2:
+            continue
+        f1 = min(x for x, _ in lst)
+        f2 = min(y for _, y in lst)
+        for x, y in lst:
+            class_id[x] = f1
+            class_id[y] = f2
+        pairs += len(lst) - 1
+    return class_id, 2 * pairs, pairs
+
+
+def motif_classes(g: Csr, open_twins: bool = True, closed_twins: bool = True, pendant_twins: bool = False,
+                  parallel_paths: bool = False):
     """Open-twin, closed-twin and (optionally) pendant-twin classes together (§3.4).
 
     The relations are disjoint: if N(i) = N(j) and N[i] = N[k] (k != i), then k
@@ -401,7 +448,20 @@ def motif_classes(g: Csr, open_twins: bool = True, closed_twins: bool = True, pe
         for d, c in pairs.items():
             r = 1.0 / np.sqrt(float(d))
             spikes.extend([(-r, c), (r, c)])
-    return cid, removed, sorted(spikes)
+        taken |= in_pt
+    if parallel_paths:
+        qc, r3, pairs = parallel_path_classes(g)
+        in_pp = np.bincount(qc, minlength=g.n)[qc] >= 2
+        assert not np.any(taken & in_pp)
+        cid = np.where(in_pp, qc, cid)
+        removed += r3
+        if pairs:
+            spikes.extend([(-0.5, pairs), (0.5, pairs)])
+    # equal eigenvalues from different motifs (e.g. -1/2) are one spike
+    merged: dict[float, int] = {}
+    for x, c in spikes:
+        merged[x] = merged.get(x, 0) + c
+    return cid, removed, sorted(merged.items())
 
 
 def project_probes(z: np.ndarray, class_id: np.ndarray) -> np.ndarray:

@@ -40,6 +40,7 @@ __all__ = [
     "add_twin_leaves",
     "add_triangle_twins",
     "add_pendant_twins",
+    "add_parallel_paths",
     "cycle",
     "complete",
     "star",
@@ -302,6 +303,31 @@ def add_pendant_twins(src, dst, n: int, n_groups: int, k_common: int, seed: int)
         s_new += [np.full(k_common, a), np.full(k_common, b), np.array([a, b], np.int64)]
         d_new += [common, common, np.array([la, lb], np.int64)]
     return np.concatenate(s_new), np.concatenate(d_new), n + 4 * int(n_groups)
+
+
+def add_parallel_paths(src, dst, n: int, n_groups: int, paths: int, seed: int):
+    """Join ``n_groups`` host pairs (drawn among the nodes with a non-loop
+    edge) by ``paths`` new paths of two degree-2 nodes each (the parallel-path
+    +-1/2 motif of §3.4, Fig. 3).  Returns the extended edge list and the new
+    node count."""
+    rng = _rng(seed)
+    src = np.asarray(src, np.int64)
+    dst = np.asarray(dst, np.int64)
+    live = np.zeros(n, bool)
+    nl = src != dst
+    live[src[nl]] = True
+    live[dst[nl]] = True
+    cand = np.nonzero(live)[0]
+    s_new, d_new = [src], [dst]
+    nxt = n
+    for _ in range(int(n_groups)):
+        e, f = rng.choice(cand, size=2, replace=False).astype(np.int64)
+        for _ in range(int(paths)):
+            a, b = nxt, nxt + 1
+            nxt += 2
+            s_new.append(np.array([e, a, b], np.int64))
+            d_new.append(np.array([a, b, f], np.int64))
+    return np.concatenate(s_new), np.concatenate(d_new), nxt
 
 
 def windmill(k: int):

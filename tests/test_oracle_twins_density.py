@@ -343,3 +343,46 @@ def test_random_graph_with_pendant_twins_of_mixed_degree():
     lam_r = np.linalg.eigvalsh(p.T @ h @ p)
     assert lam_r.size == g.n - removed
     assert np.allclose(np.sort(lam_r), np.sort(_remove_eigs(lam, spikes)), atol=1e-9)
+
+
+# ---- parallel paths between two hosts (lambda = +-1/2) -------------------------
+def test_theta_graph_parallel_paths():
+    # theta graph: hosts 0 and 1 joined by k paths 0 - a - b - 1 (k = 2 is the
+    # 6-cycle: no host of degree >= 3, nothing is filtered)
+    src, dst = [0, 2, 3, 0, 4, 5], [2, 3, 1, 4, 5, 1]
+    assert oracle.parallel_path_classes(oracle.build_csr(np.array(src), np.array(dst), 6))[1] == 0
+    for k in (3, 5):
+        src, dst = [], []
+        for t in range(k):
+            a, b = 2 + 2 * t, 3 + 2 * t
+            src += [0, a, b]
+            dst += [a, b, 1]
+        g = oracle.build_csr(np.array(src), np.array(dst), 2 + 2 * k)
+        cid, removed, pairs = oracle.parallel_path_classes(g)
+        assert removed == 2 * (k - 1) and pairs == k - 1
+        cid, removed, spikes = oracle.motif_classes(g, parallel_paths=True)
+        lam, _ = oracle.exact_eigs(g)
+        p = _p_matrix(cid)
+        h = oracle.dense_h(g)
+        assert np.allclose(p @ p.T @ h, h @ p @ p.T, atol=1e-12)
+        lam_r = np.linalg.eigvalsh(p.T @ h @ p)
+        assert np.allclose(np.sort(lam_r), np.sort(_remove_eigs(lam, spikes)), atol=1e-9)
+
+
+def test_all_motifs_together():
+    src, dst, n = sg.chung_lu(400, 2.4, 6.0, 91)
+    src, dst, n = sg.add_twin_leaves(src, dst, n, 8, 92)
+    src, dst, n = sg.add_triangle_twins(src, dst, n, 8, 93)
+    src, dst, n = sg.add_pendant_twins(src, dst, n, 4, 3, 94)
+    src, dst, n = sg.add_parallel_paths(src, dst, n, 4, 3, 95)
+    g = oracle.build_csr(src, dst, n)
+    _, _, pairs = oracle.parallel_path_classes(g)
+    assert pairs >= 8
+    cid, removed, spikes = oracle.motif_classes(g, pendant_twins=True, parallel_paths=True)
+    lam, _ = oracle.exact_eigs(g)
+    p = _p_matrix(cid)
+    h = oracle.dense_h(g)
+    assert np.allclose(p @ p.T @ h, h @ p @ p.T, atol=1e-12)
+    lam_r = np.linalg.eigvalsh(p.T @ h @ p)
+    assert lam_r.size == g.n - removed
+    assert np.allclose(np.sort(lam_r), np.sort(_remove_eigs(lam, spikes)), atol=1e-9)
