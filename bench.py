@@ -552,6 +552,10 @@ def measure_motifs(seed, reps: int = 3) -> dict:
                                                       ("open+closed", ("open", "closed"))), reps),
            "barabasi_albert_tree": None}
     out["chung_lu"]["graph"] = MOTIFS["graph"]
+    src, dst, n = sg.add_parallel_paths(src, dst, n, 20_000, 3, seed + 4)
+    out["chung_lu_parallel"] = motif_leg(src, dst, n, seed, (("open+closed", ("open", "closed")),
+                                                             ("all", ("open", "closed", "pendant", "parallel"))), reps)
+    out["chung_lu_parallel"]["graph"] = MOTIFS["graph"] + " + 20,000 host pairs joined by 3 parallel 2-node paths"
     src, dst, n = sg.barabasi_albert(N_BASE, 1, seed + 3)
     out["barabasi_albert_tree"] = motif_leg(src, dst, n, seed, (("none", None), ("open", ("open",)),
                                                                  ("open+pendant", ("open", "pendant")),

@@ -125,7 +125,8 @@ int dos_motif_filter(dos_graph_t g, void* stream, dos_filter_t* out);
 enum {
   DOS_MOTIF_OPEN_TWINS = 1,   /* N(i) = N(j): eigenvalue 0 (Fig. 3a) */
   DOS_MOTIF_CLOSED_TWINS = 2, /* N[i] = N[j] (adjacent, degree d): eigenvalue -1/d */
-  DOS_MOTIF_PENDANT_TWINS = 4 /* degree-d nodes equal but for one leaf each: +-1/sqrt(d) */
+  DOS_MOTIF_PENDANT_TWINS = 4, /* degree-d nodes equal but for one leaf each: +-1/sqrt(d) */
+  DOS_MOTIF_PARALLEL_PATHS = 8 /* >= 2 paths E - a - b - F of degree-2 nodes: +-1/2 */
 };
 
 /*
@@ -139,7 +140,10 @@ enum {
  * leaf neighbour each and equal neighbourhoods apart from it (d = 2: pendant
  * 2-paths u - a - a'; d = 4: the +-1/2 motif); a class of c carries c - 1
  * eigenvalues at each of +-1/sqrt(d) on vectors summing to zero over the
- * nodes and over their leaves, which become two classes.
+ * nodes and over their leaves, which become two classes.  Parallel paths
+ * are c >= 2 paths E - a - b - F through degree-2 nodes between the same
+ * hosts E != F of degree >= 3 (Fig. 3's first +-1/2 drawing): the nodes next
+ * to each host form a class, c - 1 eigenvalues at each of +-1/2.
  * The relations are disjoint, so all classes are filtered by one class-mean
  * projection; dos_filter_info's removed counts all of them, and
  * dos_filter_spikes lists the removed eigenvalues.  Hash collisions are
@@ -155,7 +159,8 @@ int dos_motif_filter_ex(dos_graph_t g, uint32_t motifs, void* stream,
 
 /* Removed eigenvalues [host]: up to `capacity` pairs (lambda, count) in
  * ascending lambda (0 for open twins, -1/d per degree d with closed twins,
- * +-1/sqrt(d) per degree d with pendant twins);
+ * +-1/sqrt(d) per degree d with pendant twins, +-1/2 for parallel paths;
+ * equal values of different motifs are one entry);
  * *n_spikes (may be NULL) receives the total number of pairs.
  * Errors: DOS_EINVAL. */
 int dos_filter_spikes(dos_filter_t f, double* spikes, int capacity,

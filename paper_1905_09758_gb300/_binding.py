@@ -20,7 +20,7 @@ DOS_OK, DOS_EINVAL, DOS_ENOMEM, DOS_ECUDA, DOS_ETIMEOUT, DOS_EOVERFLOW = range(6
 PREC = {"fp32": 0, "bf16": 1, "fp16": 2}
 KERNEL = {"none": 0, "jackson": 1}
 DOS_INPUT_HOST = 1
-MOTIF = {"open": 1, "closed": 2, "pendant": 4}
+MOTIF = {"open": 1, "closed": 2, "pendant": 4, "parallel": 8}
 OPERATOR = {"normalized_adjacency": 0, "adjacency": 1, "laplacian": 2, "normalized_laplacian": 3}
 
 _STATUS_NAMES = {
@@ -319,7 +319,8 @@ def dos_motif_filter(g: Graph, stream=None) -> Filter:
 
 def dos_motif_filter_ex(g: Graph, motifs=("open", "closed"), stream=None) -> Filter:
     """Motif classes for a set of motifs: "open" twins (lambda = 0), "closed"
-    twins (lambda = -1/d), "pendant" twins (lambda = +-1/sqrt d)."""
+    twins (lambda = -1/d), "pendant" twins (lambda = +-1/sqrt d), "parallel"
+    paths (lambda = +-1/2)."""
     mask = 0
     for m in motifs:
         mask |= MOTIF[m]

@@ -8,6 +8,10 @@
 //                 and their leaves another; the vectors summing to zero over
 //                 each carry c - 1 eigenvalues at each of +-1/sqrt(d) (d = 2:
 //                 pendant 2-paths, +-1/sqrt 2; d = 4: the +-1/2 motif).
+//   parallel paths  c >= 2 paths E - a - b - F through degree-2 nodes between
+//                 the same hosts E != F of degree >= 3: the nodes next to the
+//                 smaller host form one class and those next to the larger
+//                 another; c - 1 eigenvalues at each of +-1/2.
 // The relations are disjoint (no node is in two nontrivial classes), so one
 // class id per node and one class-mean projection of the probes filters all.
 //
@@ -246,6 +250,61 @@ __global__ void k_merge_pendant(int32_t* __restrict__ class_id, const int32_t* _
   }
 }
 
+// parallel-path candidates: an edge (a, b), a < b, between degree-2 nodes
+// whose other neighbours e (of a) and f (of b) differ and have degree >= 3;
+// key = (min(e, f) << 32) | max(e, f), first = the node next to min(e, f)
+__global__ void k_pp_candidates(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                                const int32_t* __restrict__ deg, int64_t n, uint64_t* __restrict__ key,
+                                int32_t* __restrict__ idx, int32_t* __restrict__ first, int32_t* __restrict__ second,
+                                unsigned long long* __restrict__ count) {
+  for (int64_t a = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; a < n;
+       a += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    if (deg[a] != 2) continue;
+    const int32_t x0 = col[row_ptr[a]], x1 = col[row_ptr[a] + 1];
+    for (int side = 0; side < 2; ++side) {
+      const int32_t b = side == 0 ? x0 : x1, e = side == 0 ? x1 : x0;
+      if (b <= a || deg[b] != 2) continue;
+      const int32_t y0 = col[row_ptr[b]], y1 = col[row_ptr[b] + 1];
+      const int32_t f = y0 == static_cast<int32_t>(a) ? y1 : y0;
+      if (e == f || deg[e] < 3 || deg[f] < 3) continue;
+      const unsigned long long k = atomicAdd(count, 1ull);
+      const uint32_t lo = static_cast<uint32_t>(e < f ? e : f), hi = static_cast<uint32_t>(e < f ? f : e);
+      key[k] = (static_cast<uint64_t>(lo) << 32) | hi;
+      idx[k] = static_cast<int32_t>(k);
+      first[k] = e < f ? static_cast<int32_t>(a) : b;
+      second[k] = e < f ? b : static_cast<int32_t>(a);
+    }
+  }
+}
+
+// a thread per run of equal keys (sorted): c >= 2 paths form two classes
+// (smallest members), c - 1 removed pairs
+__global__ void k_pp_assign(const uint64_t* __restrict__ key, const int32_t* __restrict__ order, int64_t m,
+                            const int32_t* __restrict__ first, const int32_t* __restrict__ second,
+                            const int32_t* __restrict__ size, int32_t* __restrict__ class_id,
+                            unsigned long long* __restrict__ pairs, int* __restrict__ conflict) {
+  for (int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; p < m;
+       p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    if (p > 0 && key[p - 1] == key[p]) continue;  // not a run start
+    int64_t q = p + 1;
+    int32_t f1 = first[order[p]], f2 = second[order[p]];
+    while (q < m && key[q] == key[p]) {
+      f1 = min(f1, first[order[q]]);
+      f2 = min(f2, second[order[q]]);
+      ++q;
+    }
+    if (q - p < 2) continue;
+    for (int64_t r = p; r < q; ++r) {
+      const int32_t a = first[order[r]], b = second[order[r]];
+      // cannot happen (disjoint relations): either node already in a nontrivial class
+      if (size[class_id[a]] >= 2 || size[class_id[b]] >= 2) atomicOr(conflict, 1);
+      class_id[a] = f1;
+      class_id[b] = f2;
+    }
+    atomicAdd(pairs, static_cast<unsigned long long>(q - p - 1));
+  }
+}
+
 __global__ void k_class_counts(const int32_t* __restrict__ class_id, int64_t n, int32_t* __restrict__ cnt,
                                unsigned long long* __restrict__ removed) {
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
@@ -446,6 +505,58 @@ static int motif_filter_impl(const Graph* G, uint32_t motifs, cudaStream_t s, Fi
         removed_paths += 2 * static_cast<int64_t>(h_deg[d]);
       }
   }
+  int64_t removed_pp = 0;
+  if (motifs & DOS_MOTIF_PARALLEL_PATHS) {
+    uint64_t *key = nullptr, *key_alt = nullptr;
+    int32_t *idx = nullptr, *idx_alt = nullptr, *first = nullptr, *second = nullptr, *size = nullptr;
+    unsigned long long *count = nullptr, *pairs_d = nullptr;
+    int* conflict = nullptr;
+    NDOS_CHECK(t.get(&key, n));
+    NDOS_CHECK(t.get(&key_alt, n));
+    NDOS_CHECK(t.get(&idx, n));
+    NDOS_CHECK(t.get(&idx_alt, n));
+    NDOS_CHECK(t.get(&first, n));
+    NDOS_CHECK(t.get(&second, n));
+    NDOS_CHECK(t.get(&size, n));
+    NDOS_CHECK(t.get(&count, 1));
+    NDOS_CHECK(t.get(&pairs_d, 1));
+    NDOS_CHECK(t.get(&conflict, 1));
+    NDOS_CUDA(cudaMemsetAsync(count, 0, sizeof(unsigned long long), s));
+    NDOS_CUDA(cudaMemsetAsync(pairs_d, 0, sizeof(unsigned long long), s));
+    NDOS_CUDA(cudaMemsetAsync(conflict, 0, sizeof(int), s));
+    NDOS_CUDA(cudaMemsetAsync(size, 0, sizeof(int32_t) * n, s));
+    k_pp_candidates<<<grid_for(n), 256, 0, s>>>(G->row_ptr, G->col, G->deg, n, key, idx, first, second, count);
+    NDOS_LAUNCHED();
+    k_sizes<<<grid_for(n), 256, 0, s>>>(F->class_id, n, size);
+    NDOS_LAUNCHED();
+    unsigned long long m = 0;
+    NDOS_CUDA(cudaMemcpyAsync(&m, count, sizeof(m), cudaMemcpyDeviceToHost, s));
+    NDOS_CUDA(cudaStreamSynchronize(s));
+    if (m > 0) {
+      cub::DoubleBuffer<uint64_t> kb(key, key_alt);
+      cub::DoubleBuffer<int32_t> vb(idx, idx_alt);
+      size_t bytes = 0;
+      NDOS_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, bytes, kb, vb, static_cast<int64_t>(m), 0, 64, s));
+      char* tmp = nullptr;
+      NDOS_CHECK(t.get(&tmp, bytes));
+      NDOS_CUDA(cub::DeviceRadixSort::SortPairs(tmp, bytes, kb, vb, static_cast<int64_t>(m), 0, 64, s));
+      count_launch();
+      k_pp_assign<<<grid_for(static_cast<int64_t>(m)), 256, 0, s>>>(kb.Current(), vb.Current(), static_cast<int64_t>(m),
+                                                                   first, second, size, F->class_id, pairs_d, conflict);
+      NDOS_LAUNCHED();
+    }
+    unsigned long long pairs = 0;
+    int h_conflict = 0;
+    NDOS_CUDA(cudaMemcpyAsync(&pairs, pairs_d, sizeof(pairs), cudaMemcpyDeviceToHost, s));
+    NDOS_CUDA(cudaMemcpyAsync(&h_conflict, conflict, sizeof(int), cudaMemcpyDeviceToHost, s));
+    NDOS_CUDA(cudaStreamSynchronize(s));
+    if (h_conflict) return fail(DOS_ECUDA, "dos_motif_filter: a parallel-path node already in another class");
+    if (pairs) {
+      F->spikes.push_back({-0.5, static_cast<int64_t>(pairs)});
+      F->spikes.push_back({0.5, static_cast<int64_t>(pairs)});
+    }
+    removed_pp = 2 * static_cast<int64_t>(pairs);
+  }
   k_class_counts<<<grid_for(n), 256, 0, s>>>(F->class_id, n, cnt, removed_d);
   NDOS_LAUNCHED();
   k_leader_flags<<<grid_for(n), 256, 0, s>>>(cnt, n, flag);
@@ -464,10 +575,19 @@ static int motif_filter_impl(const Graph* G, uint32_t motifs, cudaStream_t s, Fi
   NDOS_CUDA(cudaStreamSynchronize(s));
   F->n_classes = n_classes;
   F->removed = static_cast<int64_t>(removed);
-  const int64_t removed_open = F->removed - removed_closed - removed_paths;
+  const int64_t removed_open = F->removed - removed_closed - removed_paths - removed_pp;
   if (removed_open > 0) F->spikes.push_back({0.0, removed_open});
   std::sort(F->spikes.begin(), F->spikes.end(),
             [](const std::pair<double, int64_t>& x, const std::pair<double, int64_t>& y) { return x.first < y.first; });
+  // equal eigenvalues of different motifs (e.g. -1/2) are one spike
+  std::vector<std::pair<double, int64_t>> merged;
+  for (const auto& sp : F->spikes) {
+    if (!merged.empty() && merged.back().first == sp.first)
+      merged.back().second += sp.second;
+    else
+      merged.push_back(sp);
+  }
+  F->spikes.swap(merged);
   NDOS_CHECK(palloc(&F->slot_size, n_classes));
   k_slots<<<grid_for(n), 256, 0, s>>>(F->class_id, cnt, slot_of, G->p_compact, n, F->p_slot, F->slot_size);
   NDOS_LAUNCHED();
@@ -484,7 +604,8 @@ extern "C" int dos_motif_filter_ex(dos_graph_t g, uint32_t motifs, void* stream,
   if (!out) return fail(DOS_EINVAL, "dos_motif_filter: out is NULL");
   *out = nullptr;
   if (!g) return fail(DOS_EINVAL, "dos_motif_filter: null graph");
-  const uint32_t known = DOS_MOTIF_OPEN_TWINS | DOS_MOTIF_CLOSED_TWINS | DOS_MOTIF_PENDANT_TWINS;
+  const uint32_t known =
+      DOS_MOTIF_OPEN_TWINS | DOS_MOTIF_CLOSED_TWINS | DOS_MOTIF_PENDANT_TWINS | DOS_MOTIF_PARALLEL_PATHS;
   if (motifs == 0 || (motifs & ~known)) return fail(DOS_EINVAL, "dos_motif_filter_ex: unknown or empty motif set");
   Filter* F = new Filter();
   F->g = reinterpret_cast<const Graph*>(g);

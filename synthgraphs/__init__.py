@@ -306,10 +306,12 @@ def add_pendant_twins(src, dst, n: int, n_groups: int, k_common: int, seed: int)
 
 
 def add_parallel_paths(src, dst, n: int, n_groups: int, paths: int, seed: int):
-    """Join ``n_groups`` host pairs (drawn among the nodes with a non-loop
-    edge) by ``paths`` new paths of two degree-2 nodes each (the parallel-path
-    +-1/2 motif of §3.4, Fig. 3).  Returns the extended edge list and the new
-    node count."""
+    """Join ``n_groups`` host pairs by ``paths`` new paths of two degree-2
+    nodes each (the parallel-path +-1/2 motif of §3.4, Fig. 3).  The 2 n_groups
+    hosts are drawn without replacement among the nodes with a non-loop edge
+    (pair g = hosts 2g, 2g + 1); path j of pair g uses the new nodes
+    n + 2 (g paths + j) and the next one.  Returns the extended edge list and
+    the new node count."""
     rng = _rng(seed)
     src = np.asarray(src, np.int64)
     dst = np.asarray(dst, np.int64)
@@ -317,17 +319,14 @@ def add_parallel_paths(src, dst, n: int, n_groups: int, paths: int, seed: int):
     nl = src != dst
     live[src[nl]] = True
     live[dst[nl]] = True
-    cand = np.nonzero(live)[0]
-    s_new, d_new = [src], [dst]
-    nxt = n
-    for _ in range(int(n_groups)):
-        e, f = rng.choice(cand, size=2, replace=False).astype(np.int64)
-        for _ in range(int(paths)):
-            a, b = nxt, nxt + 1
-            nxt += 2
-            s_new.append(np.array([e, a, b], np.int64))
-            d_new.append(np.array([a, b, f], np.int64))
-    return np.concatenate(s_new), np.concatenate(d_new), nxt
+    hosts = rng.choice(np.nonzero(live)[0], size=2 * int(n_groups), replace=False).astype(np.int64)
+    e = np.repeat(hosts[0::2], paths)
+    f = np.repeat(hosts[1::2], paths)
+    a = n + 2 * np.arange(int(n_groups) * int(paths), dtype=np.int64)
+    b = a + 1
+    new_src = np.concatenate([src, e, a, b])
+    new_dst = np.concatenate([dst, a, b, f])
+    return new_src, new_dst, n + 2 * int(n_groups) * int(paths)
 
 
 def windmill(k: int):

@@ -317,7 +317,7 @@ def test_closed_twin_filter_bit_exact_and_moments(name):
 
 def test_motif_filter_ex_rejects_bad_sets():
     g = _gpu_graph(*sg.windmill(3))
-    for bad in (0, 8, 15):
+    for bad in (0, 16, 31, 1 << 20):
         with pytest.raises(nd.DosError) as e:
             out = nd._binding.C.c_void_p()
             nd._binding._check(nd.lib().dos_motif_filter_ex(g.handle, bad, None, nd._binding.C.byref(out)))
@@ -365,3 +365,41 @@ def test_pendant_twin_filter_bit_exact_and_moments(name):
     wts = [c / n_tot for _, c in spikes] + [ref.n_isolated / n_tot]
     want = (ref.n - removed) / n_tot * oracle.histogram(d, b) + oracle.point_mass_histogram(pts, wts, b)
     assert np.abs(h - want).max() <= 1e-12
+
+
+# ---- parallel paths between two hosts (lambda = +-1/2), all motifs together ----
+def _theta(k):
+    src, dst = [], []
+    for t in range(k):
+        a, b = 2 + 2 * t, 3 + 2 * t
+        src += [0, a, b]
+        dst += [a, b, 1]
+    return np.array(src, np.int64), np.array(dst, np.int64), 2 + 2 * k
+
+
+def _all_motifs():
+    s, d, n = sg.chung_lu(6000, 2.4, 6.0, 91)
+    s, d, n = sg.add_twin_leaves(s, d, n, 100, 92)
+    s, d, n = sg.add_triangle_twins(s, d, n, 100, 93)
+    s, d, n = sg.add_pendant_twins(s, d, n, 40, 3, 94)
+    return sg.add_parallel_paths(s, d, n, 40, 3, 95)
+
+
+ALL = {"theta5": _theta(5), "cycle6": sg.cycle(6), "all_motifs": _all_motifs()}
+
+
+@pytest.mark.parametrize("name", list(ALL))
+def test_all_motif_filters_bit_exact_and_moments(name):
+    src, dst, n = ALL[name]
+    ref = oracle.build_csr(src, dst, n)
+    g = _gpu_graph(src, dst, n)
+    f = nd.dos_motif_filter_ex(g, ("open", "closed", "pendant", "parallel"))
+    cid_ref, removed, spikes = oracle.motif_classes(ref, pendant_twins=True, parallel_paths=True)
+    assert np.array_equal(nd.dos_filter_export(f).cpu().numpy(), cid_ref)
+    assert f.info()["removed"] == removed
+    assert nd.dos_filter_spikes(f) == [(float(x), c) for x, c in spikes]
+    m, nz = 30, 16
+    d = nd.dos_moments(g, m, nz, 27, filter=f).cpu().numpy()
+    z = oracle.project_probes(oracle.probes(27, ref.old_id, nz), cid_ref)
+    d_ref = oracle.kpm_doubled(ref, z, m) / ((ref.n - removed) * nz)
+    assert np.abs(d - d_ref).max() <= TOL_D
