@@ -296,6 +296,29 @@ int dos_density(const double* d, int M, int n_bins, int kernel, double scale,
 int dos_moments_noalloc(dos_graph_t g, int M, int Nz, uint64_t seed,
                         double* d_out, void* stream);
 
+/*
+ * dos_pdos_nd -- exact PDOS moments by nested dissection.
+ * Paper: §3.3 (block recurrence for T_m(H) on a partition tree, Eq. (13)-(14))
+ * and Algorithm 1.  C_out[m * N + k] = T_m(H)_kk (compact ids), m < M,
+ * computed exactly up to FP32 rounding, without probes.  The partition tree
+ * is built on the host by recursive bisection with BFS level sets as vertex
+ * separators (partitions of at most leaf_size nodes are leaves); the cost and
+ * memory are the sum over tree nodes of |partition| x |separator| (three
+ * FP32 buffers of that many entries), small when the graph has small
+ * separators (meshes, road-like and geometric graphs) and prohibitive when it
+ * has not (expanders, power-law graphs).
+ *   leaf_size    >= 1 (e.g. 64)
+ *   max_entries  refuse (DOS_ENOMEM) when the block entries exceed this;
+ *                <= 0: no limit
+ *   C_out [device] float[M * N]
+ *   stats [host] int64[4] or NULL: tree nodes, depth levels, block entries,
+ *                largest separator.
+ * Stream-ordered after the partitioning (which synchronises `stream`).
+ * Errors: DOS_EINVAL, DOS_ENOMEM (too many block entries), DOS_ECUDA.
+ */
+int dos_pdos_nd(dos_graph_t g, int M, int leaf_size, double max_entries,
+                float* C_out, int64_t* stats, void* stream);
+
 /* ---------------------------------------------------------------------
  * Gauss quadrature and Lanczos (GQL), the second estimator of §3.2.
  * --------------------------------------------------------------------- */

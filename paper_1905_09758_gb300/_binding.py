@@ -85,6 +85,7 @@ _SIGNATURES = {
     "dos_hist_normalize": ([_vp, _i32, _i64, _vp, _vp], _i32),
     "dos_hist_assemble": ([_vp, _i32, _i64, _dbl, _vp, _i32, _vp, _vp], _i32),
     "dos_lanczos": ([_vp, _i32, _i32, _u64, _vp, _vp, _vp, _vp], _i32),
+    "dos_pdos_nd": ([_vp, _i32, _i32, _dbl, _vp, _P64, _vp], _i32),
     "dos_moments_op": ([_vp, _i32, _dbl, _dbl, _i32, _i32, _u64, _i32, _vp, _vp, _vp], _i32),
     "dos_gauss_rules": ([_vp, _vp, _vp, _i32, _i32, _vp, _vp, _vp], _i32),
     "dos_gql_moments": ([_vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp], _i32),
@@ -674,3 +675,19 @@ def dos_moments_op(g: Graph, op: str, M: int, Nz: int, seed: int, prec: str = "f
     _check(lib().dos_moments_op(g.handle, OPERATOR[op], lo, hi, int(M), int(Nz), int(seed) & (2**64 - 1), PREC[prec],
                                 _ptr(d_out), iv, _stream(stream)))
     return d_out, (iv[0], iv[1])
+
+
+# ---------------------------------------------------------------------------
+# nested dissection (§3.3, Algorithm 1)
+# ---------------------------------------------------------------------------
+def dos_pdos_nd(g: Graph, M: int, leaf_size: int = 64, max_entries: float = 1e9, C_out: torch.Tensor | None = None,
+                stream=None):
+    """Exact PDOS moments C (M, N) float32 CUDA, C[m, k] = T_m(H)_kk, and the
+    partition statistics."""
+    n = g.n
+    if C_out is None:
+        C_out = torch.empty((M, n), dtype=torch.float32, device=torch.device("cuda", torch.cuda.current_device()))
+    _need_cuda(C_out, torch.float32, "C_out", M * n)
+    st = (C.c_int64 * 4)()
+    _check(lib().dos_pdos_nd(g.handle, int(M), int(leaf_size), float(max_entries), _ptr(C_out), st, _stream(stream)))
+    return C_out, {"tree_nodes": st[0], "depth_levels": st[1], "block_entries": st[2], "max_separator": st[3]}

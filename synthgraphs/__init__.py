@@ -45,6 +45,8 @@ __all__ = [
     "complete",
     "star",
     "windmill",
+    "grid2d",
+    "random_geometric",
     "spider",
     "complete_bipartite",
     "path",
@@ -327,6 +329,49 @@ def add_parallel_paths(src, dst, n: int, n_groups: int, paths: int, seed: int):
     new_src = np.concatenate([src, e, a, b])
     new_dst = np.concatenate([dst, a, b, f])
     return new_src, new_dst, n + 2 * int(n_groups) * int(paths)
+
+
+def grid2d(nx: int, ny: int):
+    """nx x ny grid graph (4-neighbour lattice), node id = y * nx + x: a graph
+    with small vertex separators (O(sqrt N)), the case nested dissection (§3.3)
+    is made for."""
+    idx = np.arange(nx * ny, dtype=np.int64).reshape(ny, nx)
+    src = np.concatenate([idx[:, :-1].ravel(), idx[:-1, :].ravel()])
+    dst = np.concatenate([idx[:, 1:].ravel(), idx[1:, :].ravel()])
+    return src, dst, nx * ny
+
+
+def random_geometric(n: int, radius: float, seed: int):
+    """Random geometric graph: n points uniform in the unit square (PCG64
+    seed), joined when closer than ``radius`` (found with a cell grid of side
+    radius).  Small separators, like road and mesh networks."""
+    rng = _rng(seed)
+    pts = rng.random((n, 2))
+    cells = max(1, int(1.0 / radius))
+    cx = np.minimum((pts[:, 0] * cells).astype(np.int64), cells - 1)
+    cy = np.minimum((pts[:, 1] * cells).astype(np.int64), cells - 1)
+    cell = cy * cells + cx
+    order = np.argsort(cell, kind="stable")
+    start = np.searchsorted(cell[order], np.arange(cells * cells + 1))
+    srcs, dsts = [], []
+    r2 = radius * radius
+    for dy in (-1, 0, 1):
+        for dx in (-1, 0, 1):
+            ny_, nx_ = cy + dy, cx + dx
+            ok = (nx_ >= 0) & (nx_ < cells) & (ny_ >= 0) & (ny_ < cells)
+            for i in np.nonzero(ok)[0]:
+                c = ny_[i] * cells + nx_[i]
+                js = order[start[c]:start[c + 1]]
+                js = js[js > i]
+                if js.size == 0:
+                    continue
+                d2 = ((pts[js] - pts[i]) ** 2).sum(axis=1)
+                js = js[d2 < r2]
+                srcs.append(np.full(js.size, i, np.int64))
+                dsts.append(js.astype(np.int64))
+    if not srcs:
+        return np.zeros(0, np.int64), np.zeros(0, np.int64), n
+    return np.concatenate(srcs), np.concatenate(dsts), n
 
 
 def windmill(k: int):
