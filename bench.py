@@ -279,6 +279,7 @@ def run_ours(args):
     motifs = None if args.no_motifs else measure_motifs(seed)
     gql = None if args.no_gql else measure_gql(seed)
     ops = None if args.no_operators else measure_operators(seed)
+    ndr = None if args.no_nd else measure_nd(seed)
     ms, e2e_s = max_over_ranks(dist, [ms, e2e_s], dev)
     if rank != 0:
         if dist is not None:
@@ -339,6 +340,8 @@ def run_ours(args):
         out["gql"] = gql
     if ops is not None:
         out["operators"] = ops
+    if ndr is not None:
+        out["nested_dissection"] = ndr
     if not args.no_time_to_l1:
         out["time_to_l1"] = time_to_l1(src_d, dst_d, n_nodes, seed, with_learned=not args.no_learned)
     if args.scale_1b:
@@ -700,6 +703,59 @@ def measure_operators(seed, m: int = 200, nz: int = 16, reps: int = 3) -> dict:
 
 
 # ---------------------------------------------------------------------------
+# nested-dissection PDOS (§3.3, Algorithm 1) on graphs with small separators
+# ---------------------------------------------------------------------------
+ND = {"M": 100, "leaf": 64, "Nz_stochastic": 64, "sampled_nodes": 16}
+
+
+def measure_nd(seed, reps: int = 2) -> dict:
+    """Exact PDOS moments by nested dissection against the stochastic diagonal
+    estimator (ldos_moments, Nz = 64) on a 316 x 316 grid and a 100k-node
+    random geometric graph: time, partition statistics, and the largest error
+    on sampled nodes against the oracle's unit-probe recurrence (the exact
+    diagonal entries T_m(H)_kk)."""
+    import torch
+
+    import oracle
+    import paper_1905_09758_gb300 as nd
+    import synthgraphs as sg
+
+    out = {**ND, "graphs": {}}
+    for name, (src, dst, n) in (("grid_316x316", sg.grid2d(316, 316)),
+                                ("random_geometric_100k", sg.random_geometric(100_000, 0.006, seed + 9))):
+        g = nd.dos_build_csr(torch.from_numpy(src).cuda(), torch.from_numpy(dst).cuda(), n)
+        m = ND["M"]
+
+        def timed(fn):
+            fn()
+            torch.cuda.synchronize()
+            best, res = None, None
+            for _ in range(reps):
+                t0 = time.perf_counter()
+                res = fn()
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                best = dt if best is None or dt < best else best
+            return best, res
+
+        t_nd, (c_nd, stats) = timed(lambda: nd.dos_pdos_nd(g, m, leaf_size=ND["leaf"]))
+        t_st, (c_st, _) = timed(lambda: nd.ldos_moments(g, m, ND["Nz_stochastic"], seed))
+        ref = oracle.build_csr(src, dst, n)
+        rng = np.random.default_rng(seed)
+        sample = rng.choice(ref.n, ND["sampled_nodes"], replace=False)
+        z = np.zeros((ref.n, sample.size))
+        z[sample, np.arange(sample.size)] = 1.0
+        _, cz = oracle.kpm_direct(ref, z, m, ldos=True)
+        exact = cz[sample] * sample.size  # unit probes: C[k, m] = T_m(H)_kk / Nz
+        e_nd = float(np.abs(c_nd.cpu().numpy()[:, sample].T - exact).max())
+        e_st = float(np.abs(c_st.cpu().numpy()[:, sample].T - exact).max())
+        out["graphs"][name] = {"n": ref.n, "nnz": ref.nnz, "nd_s": round(t_nd, 4), "stochastic_s": round(t_st, 4),
+                               "nd_max_err": float(f"{e_nd:.3e}"), "stochastic_max_err": float(f"{e_st:.3e}"),
+                               **stats}
+    return out
+
+
+# ---------------------------------------------------------------------------
 # learned reconstruction: trained on a graph family, applied to the workload
 # ---------------------------------------------------------------------------
 LEARN = {"train_graphs": 1600, "family": "Chung-Lu gamma U[2.1,3.0], mean degree U[5,30], N U[1e4,8e4], "
@@ -950,6 +1006,7 @@ def main():
     ap.add_argument("--no-motifs", action="store_true")
     ap.add_argument("--no-gql", action="store_true")
     ap.add_argument("--no-operators", action="store_true")
+    ap.add_argument("--no-nd", action="store_true")
     ap.add_argument("--scale-1b", action="store_true",
                     help="also run the 60M-node, 1e9-edge graph (about 100 GB of device memory, a few minutes)")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
