@@ -47,6 +47,12 @@ Parity status of each function (what pins it, see ``tests/test_oracle_*.py``):
   ``kpm_operator``                 -- pinned by closed-form spectra of A and L (K_n,
                                       C_n, stars), Gershgorin containment, and identity
                                       probes giving the exact traces.
+* ``ritz_bounds``, ``spectral_interval``, ``lanczos`` on A and L
+                                   -- pinned by K_n and star closed forms (the Krylov
+                                      space is exhausted: the interval is the exact
+                                      spectrum), containment of the dense spectrum,
+                                      the Ritz bound's failure before convergence,
+                                      and tightness against Gershgorin on hub graphs.
 * ``mlp_*``                        -- pinned by central finite differences.
 """
 from .kpm import *  # noqa: F401,F403

@@ -26,13 +26,14 @@ from .kpm import Csr, h_sparse, point_mass_histogram
 __all__ = ["lanczos", "gauss_rules", "gql_moments", "gql_histogram"]
 
 
-def lanczos(g: Csr, z: np.ndarray, m_steps: int):
-    """Lanczos coefficients of each probe column (§3.2).
+def lanczos(g: Csr, z: np.ndarray, m_steps: int, x=None):
+    """Lanczos coefficients of each probe column (§3.2) on H, or on the
+    symmetric sparse operator x of the same graph (A or D - A, §2.1).
 
     Returns alpha (Nz, M), beta (Nz, M) (beta[:, k] couples steps k and k+1;
     the last column is the residual norm) and steps (Nz,) = the number of
     steps each probe ran (M, or fewer after a breakdown)."""
-    h = h_sparse(g)
+    h = h_sparse(g) if x is None else x
     z = np.asarray(z, np.float64)
     nz = z.shape[1]
     alpha = np.zeros((nz, m_steps))
