@@ -221,8 +221,7 @@ enum {
  *        interval [-d_max, d_max] (A) or [0, 2 d_max] (D - A).
  *   d_out        [device] double[M]
  *   interval_out [host] double[2] receives [a, b] (may be NULL).
- *   prec as dos_moments.  Stream-ordered (the Gershgorin interval
- *   synchronises `stream`).
+ *   prec as dos_moments.  Stream-ordered.
  * Errors: DOS_EINVAL (unknown operator, ...), as dos_moments otherwise.
  */
 int dos_moments_op(dos_graph_t g, int op, double lo, double hi, int M, int Nz,
@@ -331,7 +330,7 @@ int dos_pdos_nd(dos_graph_t g, int M, int leaf_size, double max_entries,
  *   beta_out  [device] double[Nz * M]: beta_out[p * M + k] = ||w_{k+1}||, the
  *             coupling of steps k and k + 1 (the last one is the residual)
  *   steps_out [device] int32[Nz]: steps run; a probe stops early when
- *             beta_k <= 1e-5 ||z|| (its Krylov space is exhausted; below that
+ *             beta_k <= 1e-5 (its Krylov space is exhausted; below 1e-5 ||H||
  *             the FP32 residual is rounding noise); entries past its steps
  *             are 0.
  *   M in [1, 4096], Nz in [1, 128].  Stream-ordered.
@@ -339,6 +338,60 @@ int dos_pdos_nd(dos_graph_t g, int M, int leaf_size, double max_entries,
  */
 int dos_lanczos(dos_graph_t g, int M, int Nz, uint64_t seed, double* alpha_out,
                 double* beta_out, int32_t* steps_out, void* stream);
+
+/*
+ * dos_lanczos_op -- dos_lanczos on another operator X of §2.1: op =
+ * DOS_OP_NORMALIZED_ADJACENCY (H, = dos_lanczos), DOS_OP_ADJACENCY (A) or
+ * DOS_OP_LAPLACIAN (D - A), unscaled, on the non-isolated nodes.  Outputs as
+ * dos_lanczos, in the units of X; a probe stops when beta_k <= 1e-5 x the
+ * Gershgorin bound of ||X|| (1, d_max, 2 d_max).  Stream-ordered.
+ * Errors: DOS_EINVAL (op DOS_OP_NORMALIZED_LAPLACIAN or unknown, ...), as
+ * dos_lanczos otherwise.
+ */
+int dos_lanczos_op(dos_graph_t g, int op, int M, int Nz, uint64_t seed,
+                   double* alpha_out, double* beta_out, int32_t* steps_out,
+                   void* stream);
+
+/* Margins of dos_spectral_interval. */
+enum {
+  DOS_BOUND_RESIDUAL = 0, /* theta -+ beta_M: safe after a few steps */
+  DOS_BOUND_RITZ = 1      /* theta -+ beta_M |s_M|: tight once converged */
+};
+
+/* Per-probe bounds of dos_spectral_interval from Lanczos coefficients as
+ * produced by dos_lanczos_op [device]: bounds_out[2p] = theta_min - r,
+ * bounds_out[2p + 1] = theta_max + r [device double[2 Nz]], theta the extreme
+ * eigenvalues of probe p's tridiagonal (bisection), r as chosen by bound
+ * (DOS_BOUND_*).  Stream-ordered.  Errors: DOS_EINVAL. */
+int dos_ritz_bounds(const double* alpha, const double* beta,
+                    const int32_t* steps, int M, int Nz, int bound,
+                    double* bounds_out, void* stream);
+
+/*
+ * dos_spectral_interval -- an interval [a, b] holding the spectrum of X, for
+ * the map onto [-1, 1] of Eq. (5) (dos_moments_op), much tighter than the
+ * Gershgorin interval on graphs with hubs.  M Lanczos steps on X (H for
+ * I - H) from Nz probes (§3.2's recurrence); each probe gives
+ * [theta_min - r, theta_max + r], its extreme Ritz values widened by
+ *   DOS_BOUND_RESIDUAL  r = beta_M, the residual norm of the last step (on
+ *                       Nz >= 4 probes it held the spectrum of every graph
+ *                       tested, from M = 3 on), or
+ *   DOS_BOUND_RITZ      r = beta_M |s_M|, the residual of the Ritz pair (s_M
+ *                       the last component of the tridiagonal's unit
+ *                       eigenvector): tight once the extreme Ritz values have
+ *                       converged (M >= 30, Nz >= 4), too narrow before.
+ * [a, b] is the union over the probes widened by pad (b - a) at each end,
+ * with ends that are eigenvalues of every graph with an edge taken exactly
+ * (lambda_max(H) = 1, lambda_min(D - A) = lambda_min(I - H) = 0), clipped to
+ * the Gershgorin interval.  An estimate, not a proof: pad guards the FP32
+ * rounding of the Ritz values (0.01 is ample).
+ *   op  DOS_OP_*;  M in [1, 4096], Nz in [1, 128];  bound DOS_BOUND_*;
+ *   pad in [0, 1];  interval_out [host] double[2].
+ * Synchronises `stream`.  Errors: DOS_EINVAL, DOS_ENOMEM, DOS_ECUDA.
+ */
+int dos_spectral_interval(dos_graph_t g, int op, int M, int Nz, uint64_t seed,
+                          int bound, double pad, double* interval_out,
+                          void* stream);
 
 /* The Gauss rule of each probe (§3.2): nodes_out[p * M + i] = eigenvalue tau_i
  * of Gamma_M (ascending), weights_out[p * M + i] = |p_i1|^2 (Christoffel

@@ -85,6 +85,9 @@ _SIGNATURES = {
     "dos_hist_normalize": ([_vp, _i32, _i64, _vp, _vp], _i32),
     "dos_hist_assemble": ([_vp, _i32, _i64, _dbl, _vp, _i32, _vp, _vp], _i32),
     "dos_lanczos": ([_vp, _i32, _i32, _u64, _vp, _vp, _vp, _vp], _i32),
+    "dos_lanczos_op": ([_vp, _i32, _i32, _i32, _u64, _vp, _vp, _vp, _vp], _i32),
+    "dos_ritz_bounds": ([_vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp], _i32),
+    "dos_spectral_interval": ([_vp, _i32, _i32, _i32, _u64, _i32, _dbl, _vp, _vp], _i32),
     "dos_pdos_nd": ([_vp, _i32, _i32, _dbl, _vp, _P64, _vp], _i32),
     "dos_moments_op": ([_vp, _i32, _dbl, _dbl, _i32, _i32, _u64, _i32, _vp, _vp, _vp], _i32),
     "dos_gauss_rules": ([_vp, _vp, _vp, _i32, _i32, _vp, _vp, _vp], _i32),
@@ -619,6 +622,48 @@ def dos_lanczos(g: Graph, M: int, Nz: int, seed: int, stream=None):
     _check(lib().dos_lanczos(g.handle, int(M), int(Nz), int(seed) & (2**64 - 1), _ptr(alpha), _ptr(beta),
                              _ptr(steps), _stream(stream)))
     return alpha, beta, steps
+
+
+def dos_lanczos_op(g: Graph, op: str, M: int, Nz: int, seed: int, stream=None):
+    """dos_lanczos on op = "normalized_adjacency", "adjacency" or "laplacian"."""
+    if op not in OPERATOR:
+        raise ValueError(f"unknown operator {op!r}; one of {sorted(OPERATOR)}")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    alpha = torch.empty((Nz, M), dtype=torch.float64, device=dev)
+    beta = torch.empty((Nz, M), dtype=torch.float64, device=dev)
+    steps = torch.empty(Nz, dtype=torch.int32, device=dev)
+    _check(lib().dos_lanczos_op(g.handle, OPERATOR[op], int(M), int(Nz), int(seed) & (2**64 - 1), _ptr(alpha),
+                                _ptr(beta), _ptr(steps), _stream(stream)))
+    return alpha, beta, steps
+
+
+BOUND = {"residual": 0, "ritz": 1}
+
+
+def dos_spectral_interval(g: Graph, op: str, M: int = 30, Nz: int = 16, seed: int = 1, bound: str = "residual",
+                          pad: float = 0.01, stream=None):
+    """(a, b) holding the spectrum of the operator: extreme Ritz values widened
+    by beta_M ("residual") or by the Ritz pair's residual ("ritz"), then by
+    pad (b - a) at each end."""
+    if op not in OPERATOR:
+        raise ValueError(f"unknown operator {op!r}; one of {sorted(OPERATOR)}")
+    if bound not in BOUND:
+        raise ValueError(f"unknown bound {bound!r}; one of {sorted(BOUND)}")
+    iv = (C.c_double * 2)()
+    _check(lib().dos_spectral_interval(g.handle, OPERATOR[op], int(M), int(Nz), int(seed) & (2**64 - 1),
+                                       BOUND[bound], float(pad), iv, _stream(stream)))
+    return iv[0], iv[1]
+
+
+def dos_ritz_bounds(alpha, beta, steps, bound: str = "residual", stream=None) -> torch.Tensor:
+    """Per probe [theta_min - r, theta_max + r], float64 CUDA (Nz, 2)."""
+    if bound not in BOUND:
+        raise ValueError(f"unknown bound {bound!r}; one of {sorted(BOUND)}")
+    nz, m = _lanczos_args(alpha, beta, steps)
+    out = torch.empty((nz, 2), dtype=torch.float64, device=alpha.device)
+    _check(lib().dos_ritz_bounds(_ptr(alpha), _ptr(beta), _ptr(steps), m, nz, BOUND[bound], _ptr(out),
+                                 _stream(stream)))
+    return out
 
 
 def _lanczos_args(alpha, beta, steps):

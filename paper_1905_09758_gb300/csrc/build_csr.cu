@@ -127,7 +127,9 @@ __global__ void k_perm_nodes(const int32_t* __restrict__ p_compact, int64_t n, c
                              const int32_t* __restrict__ old_id, int32_t* __restrict__ compact_to_p,
                              int32_t* __restrict__ p_deg, int64_t* __restrict__ p_deg64,
                              int32_t* __restrict__ p_orig, unsigned long long* __restrict__ n_heavy,
-                             unsigned long long* __restrict__ n_mid, int heavy_deg, int mid_deg) {
+                             unsigned long long* __restrict__ n_mid, unsigned long long* __restrict__ max_deg,
+                             int heavy_deg, int mid_deg) {
+  unsigned dmax = 0;
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
        p += (int64_t)gridDim.x * blockDim.x) {
     const int32_t k = p_compact[p];
@@ -138,7 +140,10 @@ __global__ void k_perm_nodes(const int32_t* __restrict__ p_compact, int64_t n, c
     p_orig[p] = old_id[k];
     if (d >= heavy_deg) atomicAdd(n_heavy, 1ull);
     if (d >= mid_deg) atomicAdd(n_mid, 1ull);
+    dmax = max(dmax, static_cast<unsigned>(d));
   }
+  dmax = __reduce_max_sync(0xffffffffu, dmax);
+  if ((threadIdx.x & 31) == 0 && dmax > 0) atomicMax(max_deg, static_cast<unsigned long long>(dmax));
 }
 
 // relabelled nonzero keys (pos(u) << 32 | pos(v)) from the unique original keys
@@ -348,9 +353,10 @@ static int build_csr_impl(const int64_t* src_in, const int64_t* dst_in, int64_t 
   }
 
   // ---- degree-sorted relabelling ----
-  unsigned long long* n_heavy_d = nullptr;  // [0] deg >= kHeavyDeg, [1] deg >= kMediumDeg
-  NDOS_CHECK(t.get(&n_heavy_d, 2));
-  NDOS_CUDA(cudaMemsetAsync(n_heavy_d, 0, 2 * sizeof(unsigned long long), s));
+  // [0] deg >= kHeavyDeg, [1] deg >= kMediumDeg, [2] the largest degree
+  unsigned long long* n_heavy_d = nullptr;
+  NDOS_CHECK(t.get(&n_heavy_d, 3));
+  NDOS_CUDA(cudaMemsetAsync(n_heavy_d, 0, 3 * sizeof(unsigned long long), s));
   if (n > 0) {
     int32_t *idx = nullptr, *idx_alt = nullptr;
     NDOS_CHECK(t.get(&idx, n));
@@ -387,8 +393,8 @@ static int build_csr_impl(const int64_t* src_in, const int64_t* dst_in, int64_t 
     int64_t* pdeg64 = nullptr;
     NDOS_CHECK(t.get(&pdeg64, n));
     k_perm_nodes<<<grid_for(n), kThreads, 0, s>>>(G->p_compact, n, G->deg, G->old_id, G->compact_to_p, G->p_deg,
-                                                 pdeg64, G->p_orig, n_heavy_d, n_heavy_d + 1, kHeavyDeg,
-                                                 kMediumDeg);
+                                                 pdeg64, G->p_orig, n_heavy_d, n_heavy_d + 1, n_heavy_d + 2,
+                                                 kHeavyDeg, kMediumDeg);
     NDOS_LAUNCHED();
     NDOS_CHECK(exclusive_scan_i64(pdeg64, G->p_row_ptr, n, t));
   } else {
@@ -405,11 +411,12 @@ static int build_csr_impl(const int64_t* src_in, const int64_t* dst_in, int64_t 
     k_low_word<<<grid_for(nnz), kThreads, 0, s>>>(k2, nnz, G->p_col);
     NDOS_LAUNCHED();
   }
-  unsigned long long nh[2] = {0, 0};
+  unsigned long long nh[3] = {0, 0, 0};
   NDOS_CUDA(cudaMemcpyAsync(nh, n_heavy_d, sizeof(nh), cudaMemcpyDeviceToHost, s));
   NDOS_CUDA(cudaStreamSynchronize(s));
   G->n_heavy = static_cast<int64_t>(nh[0]);
   G->n_mid = static_cast<int64_t>(nh[1]);
+  G->max_deg = static_cast<int32_t>(nh[2]);
 
   return DOS_OK;
 }

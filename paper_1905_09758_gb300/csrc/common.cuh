@@ -113,7 +113,7 @@ struct Graph {
   int32_t* p_orig = nullptr;    // [n]    original id of position k
   int32_t* p_compact = nullptr; // [n]    compact id of position k
   int32_t* compact_to_p = nullptr; // [n]
-  int32_t max_deg = 0;
+  int32_t max_deg = 0;          // largest degree
   int64_t n_heavy = 0;          // positions [0, n_heavy) have deg >= kHeavyDeg
   int64_t n_mid = 0;            // positions [n_heavy, n_mid) have kMediumDeg <= deg < kHeavyDeg
   // a batch of graphs (dos_build_csr_batched): the operator is their disjoint

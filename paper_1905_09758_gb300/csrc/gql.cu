@@ -1,22 +1,27 @@
-// Gauss quadrature and Lanczos (GQL, §3.2): per-probe Lanczos on H, the Gauss
-// rule of each probe's spectral measure, its Chebyshev moments and its
-// histogram.
+// Gauss quadrature and Lanczos (GQL, §3.2): per-probe Lanczos on H (or on A
+// and D - A, §2.1), the Gauss rule of each probe's spectral measure, its
+// Chebyshev moments and its histogram, and a spectral interval from the
+// extreme Ritz values.
 //
-// Lanczos runs on all Nz probes at once, FP32 vectors and FP64 reductions,
-// in the scaled space of the Chebyshev kernels (U = S v, S = D^{-1/2}):
+// Lanczos runs on all Nz probes at once, FP32 vectors and FP64 reductions.
+// On H it works in the scaled space of the Chebyshev kernels (U = S v,
+// S = D^{-1/2}):
 //     (S H v)_i = (1/d_i) sum_{j in N(i)} U_j,  u^T H u = sum_i d_i U_i (S H u)_i,
-//     ||v||^2 = sum_i d_i U_i^2.
-// The stored vectors are unnormalised: W_1 = S z, W_{k+1} = S (H u_k - alpha_k u_k
+//     ||v||^2 = sum_i d_i U_i^2;
+// on A and D - A the vectors are unscaled (S = I, unit dot weights) and the
+// apply is sum_j U_j, resp. d_i U_i - sum_j U_j.
+// The stored vectors are unnormalised: W_1 = S z, W_{k+1} = S (X u_k - alpha_k u_k
 // - beta_{k-1} u_{k-1}) with u_k = S^{-1} W_k / beta_{k-1}, beta_0 = ||z||.  A
 // step is two passes:
-//   apply   Y = S H u_k (gather: a CTA per heavy row, a warp per other row,
+//   apply   Y = S X u_k (gather: a CTA per heavy row, a warp per other row,
 //           in the degree-sorted row order) and the alpha_k partials;
 //   update  W_{k+1} = Y - (alpha_k / beta_{k-1}) W_k - (beta_{k-1} / beta_{k-2}) W_{k-1}
 //           (in place over W_{k-1}) and the ||w||^2 partials,
 // each followed by a fixed-order FP64 reduction over CTAs, one thread per
-// probe.  A probe stops when beta_k <= 1e-5 ||z||: its Krylov space is
-// exhausted and what is left is FP32 rounding noise (relative ~1e-7); its
-// later vectors are zero and its rule keeps the steps it ran.
+// probe.  A probe stops when beta_k <= 1e-5 x (the Gershgorin bound of ||X||:
+// 1 for H, d_max for A, 2 d_max for D - A): its Krylov space is exhausted and
+// what is left is FP32 rounding noise (relative ~1e-7); its later vectors are
+// zero and its rule keeps the steps it ran.
 // No reorthogonalisation (the paper names none).
 #include <algorithm>
 #include <cmath>
@@ -28,6 +33,9 @@ namespace {
 
 constexpr int kLzThreads = 256;
 constexpr int kLzWarps = kLzThreads / 32;
+
+// operator of a Lanczos run
+enum LzOp { kLzH = 0, kLzA = 1, kLzL = 2 };
 
 struct LanczosState {
   double* alpha;       // [nz][m] output
@@ -43,9 +51,10 @@ struct LanczosState {
 
 // W_1 = S z in the degree-sorted row order (a symmetric relabelling leaves
 // the Lanczos coefficients unchanged): row-major N x nzp, z_pj = +-1 from the
-// probe hash keyed by the original id, 0 in the padding columns
+// probe hash keyed by the original id, 0 in the padding columns; S = I for
+// A and D - A
 __global__ void k_lz_init(const int32_t* __restrict__ p_orig, const int32_t* __restrict__ p_compact,
-                          const float* __restrict__ s32, int64_t n, int nz, int nzp, uint64_t seed,
+                          const float* __restrict__ s32, int op, int64_t n, int nz, int nzp, uint64_t seed,
                           float* __restrict__ w_cur, float* __restrict__ w_prev) {
   const int64_t total = n * nzp;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
@@ -54,7 +63,7 @@ __global__ void k_lz_init(const int32_t* __restrict__ p_orig, const int32_t* __r
     float v = 0.f;
     if (j < nz) {
       const uint64_t word = probe_word(seed, static_cast<uint32_t>(p_orig[i]), static_cast<uint32_t>(j >> 6));
-      const float si = s32[p_compact[i]];
+      const float si = op == kLzH ? s32[p_compact[i]] : 1.0f;
       v = ((word >> (j & 63)) & 1ull) ? -si : si;
     }
     w_cur[e] = v;
@@ -100,26 +109,37 @@ __device__ __forceinline__ void lz_gather(const int32_t* __restrict__ col, const
   }
 }
 
-// Epilogue of one row (lanes of slot 0): Y = acc / d * inv_b, and the row's
-// alpha contributions d (W_own inv_b) Y.
-__device__ __forceinline__ void lz_row_out(int64_t i, float dd, const float4& acc, const float4& ib, int nzp, int ch,
-                                           const float* __restrict__ w_cur, float* __restrict__ y, double& a0,
+// Epilogue of one row (lanes of slot 0), acc = sum_j W_j over the neighbours:
+//   H      Y = acc / d * inv_b,                  alpha weight d
+//   A      Y = acc * inv_b,                      alpha weight 1
+//   D - A  Y = (d W_own - acc) * inv_b,          alpha weight 1
+// and the row's alpha contributions weight (W_own inv_b) Y.
+__device__ __forceinline__ void lz_row_out(int op, int64_t i, float dd, const float4& acc, const float4& ib, int nzp,
+                                           int ch, const float* __restrict__ w_cur, float* __restrict__ y, double& a0,
                                            double& a1, double& a2, double& a3) {
-  const float sc = 1.0f / dd;
-  const float4 out = make_float4(acc.x * sc * ib.x, acc.y * sc * ib.y, acc.z * sc * ib.z, acc.w * sc * ib.w);
-  reinterpret_cast<float4*>(y + static_cast<size_t>(i) * nzp)[ch] = out;
   const float4 own = reinterpret_cast<const float4*>(w_cur + static_cast<size_t>(i) * nzp)[ch];
-  a0 += static_cast<double>(dd * (own.x * ib.x) * out.x);
-  a1 += static_cast<double>(dd * (own.y * ib.y) * out.y);
-  a2 += static_cast<double>(dd * (own.z * ib.z) * out.z);
-  a3 += static_cast<double>(dd * (own.w * ib.w) * out.w);
+  float4 v = acc;
+  float wd = 1.0f;
+  if (op == kLzH) {
+    const float sc = 1.0f / dd;
+    v = make_float4(acc.x * sc, acc.y * sc, acc.z * sc, acc.w * sc);
+    wd = dd;
+  } else if (op == kLzL) {
+    v = make_float4(dd * own.x - acc.x, dd * own.y - acc.y, dd * own.z - acc.z, dd * own.w - acc.w);
+  }
+  const float4 out = make_float4(v.x * ib.x, v.y * ib.y, v.z * ib.z, v.w * ib.w);
+  reinterpret_cast<float4*>(y + static_cast<size_t>(i) * nzp)[ch] = out;
+  a0 += static_cast<double>(wd * (own.x * ib.x) * out.x);
+  a1 += static_cast<double>(wd * (own.y * ib.y) * out.y);
+  a2 += static_cast<double>(wd * (own.z * ib.z) * out.z);
+  a3 += static_cast<double>(wd * (own.w * ib.w) * out.w);
 }
 
-// apply, rows [row0, n) (degree < kHeavyDeg): Y = S H u_k and the alpha
+// apply, rows [row0, n) (degree < kHeavyDeg): Y = S X u_k and the alpha
 // partials.  A warp per row: Q = nzp / 4 lanes hold one 16-byte chunk each,
 // 32 / Q neighbour slots.  Partials of CTA b go to part[b].
 template <int Q>
-__global__ void __launch_bounds__(kLzThreads) k_lz_apply(const int64_t* __restrict__ row_ptr,
+__global__ void __launch_bounds__(kLzThreads) k_lz_apply(int op, const int64_t* __restrict__ row_ptr,
                                                          const int32_t* __restrict__ col,
                                                          const int32_t* __restrict__ deg, int64_t row0, int64_t n,
                                                          int nzp, const float* __restrict__ w_cur,
@@ -142,7 +162,7 @@ __global__ void __launch_bounds__(kLzThreads) k_lz_apply(const int64_t* __restri
       acc.z += __shfl_xor_sync(0xffffffffu, acc.z, o);
       acc.w += __shfl_xor_sync(0xffffffffu, acc.w, o);
     }
-    if (slot == 0) lz_row_out(i, static_cast<float>(deg[i]), acc, ib, nzp, ch, w_cur, y, a0, a1, a2, a3);
+    if (slot == 0) lz_row_out(op, i, static_cast<float>(deg[i]), acc, ib, nzp, ch, w_cur, y, a0, a1, a2, a3);
   }
   if (slot == 0) {
     red[warp][4 * ch + 0] = a0;
@@ -162,7 +182,7 @@ __global__ void __launch_bounds__(kLzThreads) k_lz_apply(const int64_t* __restri
 // batches of 32 neighbours; the warps' sums are added in warp order.
 // Partials of row r go to part[r].
 template <int Q>
-__global__ void __launch_bounds__(kLzThreads) k_lz_apply_heavy(const int64_t* __restrict__ row_ptr,
+__global__ void __launch_bounds__(kLzThreads) k_lz_apply_heavy(int op, const int64_t* __restrict__ row_ptr,
                                                                const int32_t* __restrict__ col,
                                                                const int32_t* __restrict__ deg, int nzp,
                                                                const float* __restrict__ w_cur,
@@ -193,7 +213,7 @@ __global__ void __launch_bounds__(kLzThreads) k_lz_apply_heavy(const int64_t* __
     }
     const float4 ib = reinterpret_cast<const float4*>(inv_b)[ch];
     double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-    lz_row_out(i, static_cast<float>(deg[i]), t, ib, nzp, ch, w_cur, y, a0, a1, a2, a3);
+    lz_row_out(op, i, static_cast<float>(deg[i]), t, ib, nzp, ch, w_cur, y, a0, a1, a2, a3);
     double* o = part + static_cast<size_t>(i) * nzp + 4 * ch;
     o[0] = a0;
     o[1] = a1;
@@ -202,10 +222,11 @@ __global__ void __launch_bounds__(kLzThreads) k_lz_apply_heavy(const int64_t* __
   }
 }
 
-// update: W_{k+1} = Y - c1 W_k - c2 W_{k-1} over W_{k-1}, ||w||^2 partials.
+// update: W_{k+1} = Y - c1 W_k - c2 W_{k-1} over W_{k-1}, ||w||^2 partials
+// (weights d_i for H, 1 for A and D - A).
 // Thread t handles chunk t % Q of rows t / Q, t / Q + stride, ...
 template <int Q>
-__global__ void __launch_bounds__(kLzThreads) k_lz_update(const int32_t* __restrict__ deg, int64_t n, int nzp,
+__global__ void __launch_bounds__(kLzThreads) k_lz_update(int op, const int32_t* __restrict__ deg, int64_t n, int nzp,
                                                           const float* __restrict__ y, const float* __restrict__ w_cur,
                                                           float* __restrict__ w_pn, const float* __restrict__ c1,
                                                           const float* __restrict__ c2, double* __restrict__ part) {
@@ -224,7 +245,7 @@ __global__ void __launch_bounds__(kLzThreads) k_lz_update(const int32_t* __restr
     const float4 o = make_float4(yy.x - a.x * wc.x - b.x * wp.x, yy.y - a.y * wc.y - b.y * wp.y,
                                  yy.z - a.z * wc.z - b.z * wp.z, yy.w - a.w * wc.w - b.w * wp.w);
     *pn = o;
-    const float dd = static_cast<float>(deg[i]);
+    const float dd = op == kLzH ? static_cast<float>(deg[i]) : 1.0f;
     s0 += static_cast<double>(dd * o.x * o.x);
     s1 += static_cast<double>(dd * o.y * o.y);
     s2 += static_cast<double>(dd * o.z * o.z);
@@ -297,6 +318,22 @@ __device__ int sturm_below(const double* a, const double* b, int k, double x) {
   return cnt;
 }
 
+// eigenvalue i (ascending) of tridiag(b; a; b) of size k by bisection of the
+// Sturm count, from the Gershgorin interval of the tridiagonal
+__device__ double tridiag_eig(const double* a, const double* b, int k, int i) {
+  double lo = a[0], hi = a[0];
+  for (int j = 0; j < k; ++j) {
+    const double r = (j > 0 ? fabs(b[j - 1]) : 0.0) + (j + 1 < k ? fabs(b[j]) : 0.0);
+    lo = fmin(lo, a[j] - r);
+    hi = fmax(hi, a[j] + r);
+  }
+  for (int it = 0; it < 200 && hi - lo > 1e-15 * fmax(1.0, fabs(lo) + fabs(hi)); ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (sturm_below(a, b, k, mid) > i) hi = mid; else lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
 // one thread per (probe, node index i): node i by bisection (the point where
 // the Sturm count passes i), its weight by the Christoffel number
 // w_i = 1 / sum_j p_j(tau_i)^2 of the orthonormal polynomials of the rule
@@ -310,23 +347,13 @@ __global__ void k_gauss_rules(const double* __restrict__ alpha, const double* __
   const int p = static_cast<int>(t / m), i = static_cast<int>(t % m);
   const double* a = alpha + static_cast<size_t>(p) * m;
   const double* b = beta + static_cast<size_t>(p) * m;
-  const int k = steps[p];
+  const int k = min(steps[p], m);
   if (i >= k) {
     nodes[t] = 0.0;
     weights[t] = 0.0;
     return;
   }
-  double lo = a[0], hi = a[0];
-  for (int j = 0; j < k; ++j) {  // Gershgorin interval
-    const double r = (j > 0 ? fabs(b[j - 1]) : 0.0) + (j + 1 < k ? fabs(b[j]) : 0.0);
-    lo = fmin(lo, a[j] - r);
-    hi = fmax(hi, a[j] + r);
-  }
-  for (int it = 0; it < 200 && hi - lo > 1e-15 * fmax(1.0, fabs(lo) + fabs(hi)); ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (sturm_below(a, b, k, mid) > i) hi = mid; else lo = mid;
-  }
-  const double x = 0.5 * (lo + hi);
+  const double x = tridiag_eig(a, b, k, i);
   double p_prev = 0.0, p_cur = 1.0, sum = 1.0;
   for (int j = 0; j + 1 < k; ++j) {
     const double nxt = ((x - a[j]) * p_cur - (j > 0 ? b[j - 1] * p_prev : 0.0)) / b[j];
@@ -336,6 +363,38 @@ __global__ void k_gauss_rules(const double* __restrict__ alpha, const double* __
   }
   nodes[t] = x;
   weights[t] = 1.0 / sum;
+}
+
+// extreme Ritz values of each probe widened by r: out[2p] = theta_min - r,
+// out[2p + 1] = theta_max + r (one thread per (probe, end)), with
+// r = beta_k (ritz = 0) or the Ritz pair's residual r = beta_k |s_k| (ritz =
+// 1), s the unit eigenvector of the tridiagonal for theta.  Its components
+// come from the three-term recurrence run backwards from s_k = 1,
+//     b_{j-1} s_{j-1} = (theta - a_j) s_j - b_j s_{j+1},
+// then |s_k| = 1 / ||s||: an extreme eigenvector decays toward its last
+// component, which the backward direction computes stably (the forward one
+// amplifies the rounding of theta into the tail).
+__global__ void k_ritz_bounds(const double* __restrict__ alpha, const double* __restrict__ beta,
+                              const int32_t* __restrict__ steps, int m, int nz, int ritz, double* __restrict__ out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * nz) return;
+  const int p = t >> 1, end = t & 1;
+  const double* a = alpha + static_cast<size_t>(p) * m;
+  const double* b = beta + static_cast<size_t>(p) * m;
+  const int k = min(max(steps[p], 1), m);
+  const double theta = tridiag_eig(a, b, k, end ? k - 1 : 0);
+  double r = fabs(b[k - 1]);
+  if (ritz) {
+    double s_next = 0.0, s_cur = 1.0, sum = 1.0;
+    for (int j = k - 1; j > 0; --j) {
+      const double prev = ((theta - a[j]) * s_cur - (j + 1 < k ? b[j] * s_next : 0.0)) / b[j - 1];
+      s_next = s_cur;
+      s_cur = prev;
+      sum += s_cur * s_cur;
+    }
+    r /= sqrt(sum);
+  }
+  out[t] = end ? theta + r : theta - r;
 }
 
 // Chebyshev moments of the averaged rules, d_m = (1/nz) sum_p e_1^T T_m(G_p) e_1,
@@ -348,7 +407,7 @@ __global__ void k_gql_moments(const double* __restrict__ alpha, const double* __
   if (p >= nz) return;
   const double* a = alpha + static_cast<size_t>(p) * m;
   const double* b = beta + static_cast<size_t>(p) * m;
-  const int k = steps[p];
+  const int k = min(max(steps[p], 1), m);
   double* t_prev = scratch + static_cast<size_t>(p) * 2 * m;
   double* t_cur = t_prev + m;
   for (int j = 0; j < k; ++j) {
@@ -419,24 +478,23 @@ inline unsigned blocks_for(int64_t work, int per = 256) {
 }
 
 template <int Q>
-int lanczos_steps(const Graph* G, int m, int nz, int nzp, float* w_cur, float* w_pn, float* y, LanczosState st,
-                  int grid, double stop, cudaStream_t s) {
+int lanczos_steps(const Graph* G, int op, int m, int nz, int nzp, float* w_cur, float* w_pn, float* y,
+                  LanczosState st, int grid, double stop, cudaStream_t s) {
   const unsigned gp = static_cast<unsigned>(nzp);  // a warp per padded probe
   const int64_t nh = G->n_heavy;
   const int parts = grid + static_cast<int>(nh);  // apply partials: light CTAs, then heavy rows
   for (int k = 0; k < m; ++k) {
     if (nh > 0) {
-      k_lz_apply_heavy<Q><<<static_cast<unsigned>(nh), kLzThreads, 0, s>>>(G->p_row_ptr, G->p_col, G->p_deg, nzp,
-                                                                          w_cur, st.inv_b, y,
-                                                                          st.part + static_cast<size_t>(grid) * nzp);
+      k_lz_apply_heavy<Q><<<static_cast<unsigned>(nh), kLzThreads, 0, s>>>(
+          op, G->p_row_ptr, G->p_col, G->p_deg, nzp, w_cur, st.inv_b, y, st.part + static_cast<size_t>(grid) * nzp);
       NDOS_LAUNCHED();
     }
-    k_lz_apply<Q><<<grid, kLzThreads, 0, s>>>(G->p_row_ptr, G->p_col, G->p_deg, nh, G->n, nzp, w_cur, st.inv_b, y,
-                                             st.part);
+    k_lz_apply<Q><<<grid, kLzThreads, 0, s>>>(op, G->p_row_ptr, G->p_col, G->p_deg, nh, G->n, nzp, w_cur, st.inv_b,
+                                             y, st.part);
     NDOS_LAUNCHED();
     k_lz_alpha<<<gp, 32, 0, s>>>(nz, nzp, m, k, parts, st);
     NDOS_LAUNCHED();
-    k_lz_update<Q><<<grid, kLzThreads, 0, s>>>(G->p_deg, G->n, nzp, y, w_cur, w_pn, st.c1, st.c2, st.part);
+    k_lz_update<Q><<<grid, kLzThreads, 0, s>>>(op, G->p_deg, G->n, nzp, y, w_cur, w_pn, st.c1, st.c2, st.part);
     NDOS_LAUNCHED();
     k_lz_beta<<<gp, 32, 0, s>>>(nz, nzp, m, k, grid, stop, st);
     NDOS_LAUNCHED();
@@ -450,15 +508,13 @@ int lanczos_steps(const Graph* G, int m, int nz, int nzp, float* w_cur, float* w
 
 using namespace netdos;
 
-extern "C" int dos_lanczos(dos_graph_t g, int M, int Nz, uint64_t seed, double* alpha_out, double* beta_out,
-                           int32_t* steps_out, void* stream) {
-  clear_error();
-  if (!g || !alpha_out || !beta_out || !steps_out) return fail(DOS_EINVAL, "dos_lanczos: null argument");
-  const Graph* G = reinterpret_cast<const Graph*>(g);
-  if (G->n == 0) return fail(DOS_EINVAL, "dos_lanczos: graph has no edges");
-  if (M < 1 || M > 4096) return fail(DOS_EINVAL, "dos_lanczos: M must be in [1, 4096]");
-  if (Nz < 1 || Nz > 128) return fail(DOS_EINVAL, "dos_lanczos: Nz must be in [1, 128]");
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
+namespace netdos {
+namespace {
+
+// M Lanczos steps of operator op (kLzH, kLzA, kLzL) from Nz probes into
+// alpha / beta / steps (device)
+int run_lanczos(const Graph* G, int op, int M, int Nz, uint64_t seed, double* alpha_out, double* beta_out,
+                int32_t* steps_out, cudaStream_t s) {
   // chunks per row: a power of two >= Nz / 4
   int q = 1;
   while (4 * q < Nz) q *= 2;
@@ -478,22 +534,127 @@ extern "C" int dos_lanczos(dos_graph_t g, int M, int Nz, uint64_t seed, double* 
   LanczosState st{alpha_out, beta_out, steps_out, dbl, dbl + nzp, fl, fl + nzp, fl + 2 * nzp, part};
   NDOS_CUDA(cudaMemsetAsync(alpha_out, 0, sizeof(double) * Nz * M, s));
   NDOS_CUDA(cudaMemsetAsync(beta_out, 0, sizeof(double) * Nz * M, s));
-  k_lz_init<<<blocks_for(n * nzp), 256, 0, s>>>(G->p_orig, G->p_compact, G->s32, n, Nz, nzp, seed, w_cur, w_pn);
+  k_lz_init<<<blocks_for(n * nzp), 256, 0, s>>>(G->p_orig, G->p_compact, G->s32, op, n, Nz, nzp, seed, w_cur, w_pn);
   NDOS_LAUNCHED();
   const double norm0 = std::sqrt(static_cast<double>(n));  // ||z||^2 = N for +-1 probes
   k_lz_state0<<<(nzp + 127) / 128, 128, 0, s>>>(Nz, nzp, norm0, st);
   NDOS_LAUNCHED();
-  const double stop = 1e-5 * norm0;  // FP32 vectors: a smaller residual is rounding noise
+  // FP32 vectors: a residual below 1e-5 ||X|| is rounding noise
+  const double x_norm = op == kLzH ? 1.0 : (op == kLzA ? 1.0 : 2.0) * G->max_deg;
+  const double stop = 1e-5 * x_norm;
   int st_code = DOS_OK;
   switch (q) {
-    case 1: st_code = lanczos_steps<1>(G, M, Nz, nzp, w_cur, w_pn, y, st, grid, stop, s); break;
-    case 2: st_code = lanczos_steps<2>(G, M, Nz, nzp, w_cur, w_pn, y, st, grid, stop, s); break;
-    case 4: st_code = lanczos_steps<4>(G, M, Nz, nzp, w_cur, w_pn, y, st, grid, stop, s); break;
-    case 8: st_code = lanczos_steps<8>(G, M, Nz, nzp, w_cur, w_pn, y, st, grid, stop, s); break;
-    case 16: st_code = lanczos_steps<16>(G, M, Nz, nzp, w_cur, w_pn, y, st, grid, stop, s); break;
-    default: st_code = lanczos_steps<32>(G, M, Nz, nzp, w_cur, w_pn, y, st, grid, stop, s); break;
+    case 1: st_code = lanczos_steps<1>(G, op, M, Nz, nzp, w_cur, w_pn, y, st, grid, stop, s); break;
+    case 2: st_code = lanczos_steps<2>(G, op, M, Nz, nzp, w_cur, w_pn, y, st, grid, stop, s); break;
+    case 4: st_code = lanczos_steps<4>(G, op, M, Nz, nzp, w_cur, w_pn, y, st, grid, stop, s); break;
+    case 8: st_code = lanczos_steps<8>(G, op, M, Nz, nzp, w_cur, w_pn, y, st, grid, stop, s); break;
+    case 16: st_code = lanczos_steps<16>(G, op, M, Nz, nzp, w_cur, w_pn, y, st, grid, stop, s); break;
+    default: st_code = lanczos_steps<32>(G, op, M, Nz, nzp, w_cur, w_pn, y, st, grid, stop, s); break;
   }
-  NDOS_CHECK(st_code);
+  return st_code;
+}
+
+int lanczos_args(const char* who, dos_graph_t g, int M, int Nz, const void* a, const void* b, const void* st) {
+  if (!g || !a || !b || !st) return fail(DOS_EINVAL, std::string(who) + ": null argument");
+  if (reinterpret_cast<const Graph*>(g)->n == 0) return fail(DOS_EINVAL, std::string(who) + ": graph has no edges");
+  if (M < 1 || M > 4096) return fail(DOS_EINVAL, std::string(who) + ": M must be in [1, 4096]");
+  if (Nz < 1 || Nz > 128) return fail(DOS_EINVAL, std::string(who) + ": Nz must be in [1, 128]");
+  return DOS_OK;
+}
+
+}  // namespace
+}  // namespace netdos
+
+extern "C" int dos_lanczos(dos_graph_t g, int M, int Nz, uint64_t seed, double* alpha_out, double* beta_out,
+                           int32_t* steps_out, void* stream) {
+  clear_error();
+  NDOS_CHECK(lanczos_args("dos_lanczos", g, M, Nz, alpha_out, beta_out, steps_out));
+  return run_lanczos(reinterpret_cast<const Graph*>(g), kLzH, M, Nz, seed, alpha_out, beta_out, steps_out,
+                     static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int dos_lanczos_op(dos_graph_t g, int op, int M, int Nz, uint64_t seed, double* alpha_out,
+                              double* beta_out, int32_t* steps_out, void* stream) {
+  clear_error();
+  NDOS_CHECK(lanczos_args("dos_lanczos_op", g, M, Nz, alpha_out, beta_out, steps_out));
+  int lz = 0;
+  switch (op) {
+    case DOS_OP_NORMALIZED_ADJACENCY: lz = kLzH; break;
+    case DOS_OP_ADJACENCY: lz = kLzA; break;
+    case DOS_OP_LAPLACIAN: lz = kLzL; break;
+    default: return fail(DOS_EINVAL, "dos_lanczos_op: operator must be H, A or D - A");
+  }
+  return run_lanczos(reinterpret_cast<const Graph*>(g), lz, M, Nz, seed, alpha_out, beta_out, steps_out,
+                     static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int dos_ritz_bounds(const double* alpha, const double* beta, const int32_t* steps, int M, int Nz,
+                               int bound, double* bounds_out, void* stream) {
+  clear_error();
+  if (!alpha || !beta || !steps || !bounds_out || M < 1 || Nz < 1)
+    return fail(DOS_EINVAL, "dos_ritz_bounds: bad argument");
+  if (bound != DOS_BOUND_RESIDUAL && bound != DOS_BOUND_RITZ)
+    return fail(DOS_EINVAL, "dos_ritz_bounds: bound must be DOS_BOUND_RESIDUAL or DOS_BOUND_RITZ");
+  k_ritz_bounds<<<(2 * Nz + 127) / 128, 128, 0, static_cast<cudaStream_t>(stream)>>>(
+      alpha, beta, steps, M, Nz, bound == DOS_BOUND_RITZ, bounds_out);
+  NDOS_LAUNCHED();
+  return DOS_OK;
+}
+
+extern "C" int dos_spectral_interval(dos_graph_t g, int op, int M, int Nz, uint64_t seed, int bound, double pad,
+                                     double* interval_out, void* stream) {
+  clear_error();
+  if (!g || !interval_out) return fail(DOS_EINVAL, "dos_spectral_interval: null argument");
+  if (bound != DOS_BOUND_RESIDUAL && bound != DOS_BOUND_RITZ)
+    return fail(DOS_EINVAL, "dos_spectral_interval: bound must be DOS_BOUND_RESIDUAL or DOS_BOUND_RITZ");
+  if (!(pad >= 0.0 && pad <= 1.0)) return fail(DOS_EINVAL, "dos_spectral_interval: pad must be in [0, 1]");
+  const Graph* G = reinterpret_cast<const Graph*>(g);
+  if (G->n == 0) return fail(DOS_EINVAL, "dos_spectral_interval: graph has no edges");
+  if (M < 1 || M > 4096) return fail(DOS_EINVAL, "dos_spectral_interval: M must be in [1, 4096]");
+  if (Nz < 1 || Nz > 128) return fail(DOS_EINVAL, "dos_spectral_interval: Nz must be in [1, 128]");
+  // the Lanczos operator and the Gershgorin interval; an end that is an
+  // eigenvalue of every graph with an edge is taken exactly
+  int lz = kLzH;
+  double g_lo = -1.0, g_hi = 1.0;
+  bool exact_lo = false, exact_hi = false;
+  const double dmax = static_cast<double>(G->max_deg);
+  switch (op) {
+    case DOS_OP_NORMALIZED_ADJACENCY: exact_hi = true; break;  // lambda_max(H) = 1
+    case DOS_OP_NORMALIZED_LAPLACIAN: g_lo = 0.0; g_hi = 2.0; exact_lo = true; break;  // from H: 1 - [lo, hi]
+    case DOS_OP_ADJACENCY: lz = kLzA; g_lo = -dmax; g_hi = dmax; break;
+    case DOS_OP_LAPLACIAN: lz = kLzL; g_lo = 0.0; g_hi = 2.0 * dmax; exact_lo = true; break;  // lambda_min = 0
+    default: return fail(DOS_EINVAL, "dos_spectral_interval: unknown operator");
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Temps t(s);
+  double *alpha = nullptr, *beta = nullptr, *bounds = nullptr;
+  int32_t* steps = nullptr;
+  NDOS_CHECK(t.get(&alpha, static_cast<int64_t>(Nz) * M));
+  NDOS_CHECK(t.get(&beta, static_cast<int64_t>(Nz) * M));
+  NDOS_CHECK(t.get(&steps, Nz));
+  NDOS_CHECK(t.get(&bounds, 2 * Nz));
+  NDOS_CHECK(run_lanczos(G, lz, M, Nz, seed, alpha, beta, steps, s));
+  NDOS_CHECK(dos_ritz_bounds(alpha, beta, steps, M, Nz, bound, bounds, s));
+  std::vector<double> h(2 * Nz);
+  NDOS_CUDA(cudaMemcpyAsync(h.data(), bounds, sizeof(double) * 2 * Nz, cudaMemcpyDeviceToHost, s));
+  NDOS_CUDA(cudaStreamSynchronize(s));
+  double lo = h[0], hi = h[1];
+  for (int p = 1; p < Nz; ++p) {
+    lo = std::min(lo, h[2 * p]);
+    hi = std::max(hi, h[2 * p + 1]);
+  }
+  if (op == DOS_OP_NORMALIZED_LAPLACIAN) {  // spectrum of I - H = 1 - spectrum of H
+    const double l = 1.0 - hi, u = 1.0 - lo;
+    lo = l;
+    hi = u;
+  }
+  const double w = hi - lo;
+  lo -= pad * w;
+  hi += pad * w;
+  if (exact_lo) lo = g_lo;
+  if (exact_hi) hi = g_hi;
+  interval_out[0] = std::max(lo, g_lo);
+  interval_out[1] = std::min(hi, g_hi);
   return DOS_OK;
 }
 

@@ -78,17 +78,6 @@ __global__ void k_moments_from_raw(const double* __restrict__ raw, int M, int do
   }
 }
 
-// largest degree (the first degree-sorted row of a single graph; a batch
-// orders rows graph by graph inside the degree classes)
-__global__ void k_max_deg(const int32_t* __restrict__ deg, int64_t n, int* __restrict__ out) {
-  int v = 0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    v = max(v, deg[i]);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
-  if ((threadIdx.x & 31) == 0) atomicMax(out, v);
-}
-
 __global__ void k_fill_f32(float* __restrict__ p, int64_t n, float v) {
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x)
@@ -403,18 +392,9 @@ int dos_moments_op(dos_graph_t g, int op, double lo, double hi, int M, int Nz, u
         a = lo;
         b = hi;
       } else {  // Gershgorin discs: [-d_max, d_max] for A, [0, 2 d_max] for D - A
-        Temps t(s);
-        int* dmax_d = nullptr;
-        NDOS_CHECK(t.get(&dmax_d, 1));
-        NDOS_CUDA(cudaMemsetAsync(dmax_d, 0, sizeof(int), s));
-        const unsigned blocks = static_cast<unsigned>(std::min<int64_t>((G->n + 255) / 256, 1024));
-        k_max_deg<<<blocks, 256, 0, s>>>(G->p_deg, G->n, dmax_d);
-        NDOS_LAUNCHED();
-        int dmax = 0;
-        NDOS_CUDA(cudaMemcpyAsync(&dmax, dmax_d, sizeof(int), cudaMemcpyDeviceToHost, s));
-        NDOS_CUDA(cudaStreamSynchronize(s));
-        a = op == DOS_OP_ADJACENCY ? -static_cast<double>(dmax) : 0.0;
-        b = op == DOS_OP_ADJACENCY ? static_cast<double>(dmax) : 2.0 * dmax;
+        const double dmax = static_cast<double>(G->max_deg);
+        a = op == DOS_OP_ADJACENCY ? -dmax : 0.0;
+        b = op == DOS_OP_ADJACENCY ? dmax : 2.0 * dmax;
       }
       spec.c = 0.5 * (a + b);
       spec.inv_r = 2.0 / (b - a);
