@@ -53,6 +53,14 @@ Parity status of each function (what pins it, see ``tests/test_oracle_*.py``):
                                       spectrum), containment of the dense spectrum,
                                       the Ritz bound's failure before convergence,
                                       and tightness against Gershgorin on hub graphs.
+* ``cheb_coeffs``, ``trace_fn``, ``diag_fn``, ``ldos_operator``, ``exact_fn_trace``,
+  ``exact_fn_diag``, ``fn_values``
+                                   -- pinned by the Bessel (exp) and geometric
+                                      (resolvent) closed forms of the coefficients, the
+                                      Estrada index of K_n and stars, subgraph and
+                                      resolvent centralities of stars, the heat kernel
+                                      trace of a star's Laplacian, scipy's expm, and
+                                      identity probes giving the exact diagonal.
 * ``mlp_*``                        -- pinned by central finite differences.
 """
 from .kpm import *  # noqa: F401,F403
@@ -63,5 +71,7 @@ from .mlp import *  # noqa: F401,F403
 from .mlp import __all__ as _mlp_all
 from .operators import *  # noqa: F401,F403
 from .operators import __all__ as _op_all
+from .functions import *  # noqa: F401,F403
+from .functions import __all__ as _fn_all
 
-__all__ = list(_kpm_all) + list(_gql_all) + list(_op_all) + list(_mlp_all)
+__all__ = list(_kpm_all) + list(_gql_all) + list(_op_all) + list(_fn_all) + list(_mlp_all)
