@@ -246,6 +246,18 @@ int ldos_moments(dos_graph_t g, int M, int Nz, uint64_t seed, int prec,
                  float* C_out, double* d_out, void* stream);
 
 /*
+ * ldos_moments_op -- ldos_moments on another operator X (§2.1), mapped by
+ * Eq. (5) as in dos_moments_op: C[m][k] = (1/Nz) sum_j z_kj (T_m(X~) z_j)_k,
+ * the diagonal estimator of Eq. (12) on X~ (C[m][k] estimates T_m(X~)_kk).
+ *   op, lo, hi, interval_out as dos_moments_op (I - H: odd rows negated).
+ *   C_out, d_out as ldos_moments.  FP32 storage.  Stream-ordered.
+ * Errors: DOS_EINVAL (unknown operator, ...), as ldos_moments otherwise.
+ */
+int ldos_moments_op(dos_graph_t g, int op, double lo, double hi, int M, int Nz,
+                    uint64_t seed, float* C_out, double* d_out,
+                    double* interval_out, void* stream);
+
+/*
  * dos_density -- damped spectral histogram from moments.
  * Paper: §2.2 (spectral histogram on equal bins), Eq. (7)-(8) (dual Chebyshev
  * basis, expansion of the DOS), §4.1 (Jackson damping; the factors are the
@@ -415,6 +427,45 @@ int dos_gql_moments(const double* alpha, const double* beta,
  * Errors: DOS_EINVAL. */
 int dos_gql_histogram(const double* nodes, const double* weights, int M,
                       int Nz, int n_bins, double* hist_out, void* stream);
+
+/* ---------------------------------------------------------------------
+ * Traces and diagonals of matrix functions (§6: centralities and
+ * connectivity indices such as the Estrada index are traces and diagonals
+ * of f(X)).  With X~ = (X - c) / r on [a, b] -> [-1, 1] (Eq. (5)) and
+ * f(c + r x) = sum_m g_m T_m(x):
+ *   tr f(X) = N sum_m g_m d_m (+ f(0) per node without edges),
+ *   f(X)_kk = sum_m g_m T_m(X~)_kk, estimated from LDOS moments (Eq. (10),
+ *   (12)).  Estrada index: tr exp(A); subgraph centrality: exp(A)_kk;
+ *   resolvent centrality: ((I - p A)^{-1})_kk; heat kernel: exp(-t L).
+ * --------------------------------------------------------------------- */
+
+/* Functions of dos_fn_coeffs. */
+enum {
+  DOS_FN_EXP = 0,       /* f(x) = exp(p x) */
+  DOS_FN_RESOLVENT = 1  /* f(x) = 1 / (1 - p x); 1 - p x must not vanish on [lo, hi] */
+};
+
+/* Chebyshev coefficients of f on [lo, hi]: coef_out [device double[M]] with
+ * f(c + r x) ~ sum_m coef_out[m] T_m(x), by interpolation at max(4M, 256)
+ * Chebyshev-Gauss points.  Stream-ordered.  Errors: DOS_EINVAL (unknown fn,
+ * lo >= hi, M outside [1, 2^20], a resolvent pole inside [lo, hi]). */
+int dos_fn_coeffs(int fn, double p, double lo, double hi, int M,
+                  double* coef_out, void* stream);
+
+/* tr f(X): out [device double[1]] = N sum_m coef[m] d[m] + (nodes without
+ * edges) x f(0), f(0) = 1 for both functions; d [device double[M]] DOS
+ * moments of X~ on the same interval as coef (dos_moments_op), N the graph's
+ * nodes with edges.  Stream-ordered.  Errors: DOS_EINVAL. */
+int dos_fn_trace(dos_graph_t g, const double* coef, const double* d, int M,
+                 double* out, void* stream);
+
+/* f(X)_kk for every node: out[k] [device double[N]] = sum_m coef[m] C[m][k]
+ * over the moment-major LDOS matrix C [device float[M * N]] of ldos_moments_op
+ * (compact node ids).  FP32 products and sums of coef / max|coef|, the scale
+ * applied in FP64 (no overflow for large f).  HBM-bound: reads M N 4 bytes.
+ * Stream-ordered.  Errors: DOS_EINVAL. */
+int dos_fn_diag(const float* C, int64_t N, int M, const double* coef,
+                double* out, void* stream);
 
 /* ---------------------------------------------------------------------
  * Batches of graphs (one operator for many small graphs).

@@ -86,6 +86,10 @@ _SIGNATURES = {
     "dos_hist_assemble": ([_vp, _i32, _i64, _dbl, _vp, _i32, _vp, _vp], _i32),
     "dos_lanczos": ([_vp, _i32, _i32, _u64, _vp, _vp, _vp, _vp], _i32),
     "dos_lanczos_op": ([_vp, _i32, _i32, _i32, _u64, _vp, _vp, _vp, _vp], _i32),
+    "ldos_moments_op": ([_vp, _i32, _dbl, _dbl, _i32, _i32, _u64, _vp, _vp, _vp, _vp], _i32),
+    "dos_fn_coeffs": ([_i32, _dbl, _dbl, _dbl, _i32, _vp, _vp], _i32),
+    "dos_fn_trace": ([_vp, _vp, _vp, _i32, _vp, _vp], _i32),
+    "dos_fn_diag": ([_vp, _i64, _i32, _vp, _vp, _vp], _i32),
     "dos_ritz_bounds": ([_vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp], _i32),
     "dos_spectral_interval": ([_vp, _i32, _i32, _i32, _u64, _i32, _dbl, _vp, _vp], _i32),
     "dos_pdos_nd": ([_vp, _i32, _i32, _dbl, _vp, _P64, _vp], _i32),
@@ -720,6 +724,89 @@ def dos_moments_op(g: Graph, op: str, M: int, Nz: int, seed: int, prec: str = "f
     _check(lib().dos_moments_op(g.handle, OPERATOR[op], lo, hi, int(M), int(Nz), int(seed) & (2**64 - 1), PREC[prec],
                                 _ptr(d_out), iv, _stream(stream)))
     return d_out, (iv[0], iv[1])
+
+
+def ldos_moments_op(g: Graph, op: str, M: int, Nz: int, seed: int, interval=None,
+                    C_out: torch.Tensor | None = None, d_out: torch.Tensor | None = None, stream=None):
+    """LDOS moments C (float32 (M, N)) of (X - c) / r and the DOS moments
+    (float64 (M,)); returns (C, d, (a, b))."""
+    if op not in OPERATOR:
+        raise ValueError(f"unknown operator {op!r}; one of {sorted(OPERATOR)}")
+    n = g.n
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if C_out is None:
+        C_out = torch.empty((M, n), dtype=torch.float32, device=dev)
+    _need_cuda(C_out, torch.float32, "C_out", M * n)
+    if d_out is None:
+        d_out = torch.empty(M, dtype=torch.float64, device=dev)
+    _need_cuda(d_out, torch.float64, "d_out", M)
+    lo, hi = (0.0, 0.0) if interval is None else (float(interval[0]), float(interval[1]))
+    iv = (C.c_double * 2)()
+    _check(lib().ldos_moments_op(g.handle, OPERATOR[op], lo, hi, int(M), int(Nz), int(seed) & (2**64 - 1),
+                                 _ptr(C_out), _ptr(d_out), iv, _stream(stream)))
+    return C_out, d_out, (iv[0], iv[1])
+
+
+# ---------------------------------------------------------------------------
+# traces and diagonals of matrix functions (§6)
+# ---------------------------------------------------------------------------
+FUNCTION = {"exp": 0, "resolvent": 1}
+
+
+def dos_fn_coeffs(fn: str, p: float, interval, M: int, stream=None) -> torch.Tensor:
+    """Chebyshev coefficients (float64 CUDA (M,)) of exp(p x) or 1 / (1 - p x) on the interval."""
+    if fn not in FUNCTION:
+        raise ValueError(f"unknown function {fn!r}; one of {sorted(FUNCTION)}")
+    coef = torch.empty(M, dtype=torch.float64, device=torch.device("cuda", torch.cuda.current_device()))
+    _check(lib().dos_fn_coeffs(FUNCTION[fn], float(p), float(interval[0]), float(interval[1]), int(M), _ptr(coef),
+                               _stream(stream)))
+    return coef
+
+
+def dos_fn_trace(g: Graph, coef: torch.Tensor, d: torch.Tensor, stream=None) -> torch.Tensor:
+    """tr f(X) (float64 CUDA (1,)) from DOS moments d and coefficients coef on the same interval."""
+    _need_cuda(coef, torch.float64, "coef")
+    _need_cuda(d, torch.float64, "d", coef.numel())
+    out = torch.empty(1, dtype=torch.float64, device=coef.device)
+    _check(lib().dos_fn_trace(g.handle, _ptr(coef), _ptr(d), coef.numel(), _ptr(out), _stream(stream)))
+    return out
+
+
+def dos_fn_diag(C_moments: torch.Tensor, coef: torch.Tensor, out: torch.Tensor | None = None,
+                stream=None) -> torch.Tensor:
+    """f(X)_kk (float64 CUDA (N,)) from LDOS moments (float32 (M, N)) and coefficients."""
+    _need_cuda(C_moments, torch.float32, "C_moments")
+    m, n = C_moments.shape
+    _need_cuda(coef, torch.float64, "coef", m)
+    if out is None:
+        out = torch.empty(n, dtype=torch.float64, device=C_moments.device)
+    _need_cuda(out, torch.float64, "out", n)
+    _check(lib().dos_fn_diag(_ptr(C_moments), int(n), int(m), _ptr(coef), _ptr(out), _stream(stream)))
+    return out
+
+
+def matrix_function_trace(g: Graph, op: str, fn: str, p: float, M: int = 100, Nz: int = 32, seed: int = 1,
+                          interval=None, stream=None):
+    """tr f(X) of op ("adjacency", "laplacian", ...) by KPM: the interval
+    (Lanczos Ritz bounds unless given), DOS moments, coefficients, trace.
+    Returns (trace, (a, b)).  exp with p = 1 on A: the Estrada index."""
+    if interval is None:
+        interval = dos_spectral_interval(g, op, 30, 8, seed + 1, bound="ritz", stream=stream)
+    d, iv = dos_moments_op(g, op, M, Nz, seed, interval=interval, stream=stream)
+    coef = dos_fn_coeffs(fn, p, iv, M, stream=stream)
+    return float(dos_fn_trace(g, coef, d, stream=stream).item()), iv
+
+
+def matrix_function_diag(g: Graph, op: str, fn: str, p: float, M: int = 100, Nz: int = 32, seed: int = 1,
+                         interval=None, stream=None):
+    """f(X)_kk of every node with edges (float64 CUDA (N,), compact ids) from
+    LDOS moments: exp with p = 1 on A gives subgraph centrality, resolvent
+    with p < 1 / lambda_max resolvent centrality.  Returns (diag, (a, b))."""
+    if interval is None:
+        interval = dos_spectral_interval(g, op, 30, 8, seed + 1, bound="ritz", stream=stream)
+    cm, _, iv = ldos_moments_op(g, op, M, Nz, seed, interval=interval, stream=stream)
+    coef = dos_fn_coeffs(fn, p, iv, M, stream=stream)
+    return dos_fn_diag(cm, coef, stream=stream), iv
 
 
 # ---------------------------------------------------------------------------

@@ -215,8 +215,9 @@ static int run_steps(const Graph* G, const Filter* F, const Plan& plan, int M, i
                      double* d_out, float* C_out, cudaStream_t s, const OpSpec& op = OpSpec()) {
   constexpr int V = VecT<T>::N;
   const int64_t n = G->n;
-  const int steps = mode == kModeDos ? M / 2 : M - 1;
-  const int n_dots = mode == kModeDos ? 2 : 1;
+  const bool ldos = mode == kModeLdos || mode == kModeLdosOp;
+  const int steps = ldos ? M - 1 : M / 2;
+  const int n_dots = ldos ? 1 : 2;
   const int64_t width = plan.part_width;
   const int64_t n_raw = 1 + static_cast<int64_t>(steps) * n_dots;
   const size_t elems = static_cast<size_t>(n) * plan.nz_pad;
@@ -271,7 +272,7 @@ static int run_steps(const Graph* G, const Filter* F, const Plan& plan, int M, i
   const int init_grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((chunks + 255) / 256, width)));
   if (st == DOS_OK) st = launch_init<T>(ip, init_grid, s);
 
-  if (mode == kModeLdos && st == DOS_OK) {
+  if (ldos && st == DOS_OK) {
     if (plan.tiles > 1) cu(cudaMemsetAsync(C_out, 0, sizeof(float) * static_cast<size_t>(M) * n, s), "memset C");
     k_fill_f32<<<std::min<unsigned>(4096, std::max<unsigned>(1, ceil_div(n, 256))), 256, 0, s>>>(C_out, n, 1.0f);
     count_launch();
@@ -306,9 +307,10 @@ static int run_steps(const Graph* G, const Filter* F, const Plan& plan, int M, i
     prm.u_pn = (k & 1) ? ua : ub;
     prm.first = k == 0 ? 1 : 0;
     prm.partial = partial + static_cast<size_t>(1 + static_cast<int64_t>(k) * n_dots) * width;
-    prm.ldos = mode == kModeLdos ? C_out + static_cast<size_t>(k + 1) * n : nullptr;
+    prm.ldos = ldos ? C_out + static_cast<size_t>(k + 1) * n : nullptr;
     if (prof) profile_begin(s);
-    st = launch_step<T>(plan, mode == kModeDos && op.kind != 0 ? kModeDosOp : mode, prm, s, side);
+    st = launch_step<T>(plan, op.kind == 0 ? (ldos ? kModeLdos : kModeDos) : (ldos ? kModeLdosOp : kModeDosOp), prm,
+                        s, side);
     if (prof) profile_end(s);
   }
   if (st == DOS_OK) {
@@ -318,7 +320,7 @@ static int run_steps(const Graph* G, const Filter* F, const Plan& plan, int M, i
   }
   if (st == DOS_OK && d_out) {
     const double r = F ? static_cast<double>(n - F->removed) : static_cast<double>(n);
-    k_moments_from_raw<<<1, 256, 0, s>>>(raw, M, mode == kModeDos ? 1 : 0, r * Nz, prm.err, op.negate_odd, d_out);
+    k_moments_from_raw<<<1, 256, 0, s>>>(raw, M, ldos ? 0 : 1, r * Nz, prm.err, op.negate_odd, d_out);
     count_launch();
     cu(cudaGetLastError(), "k_moments_from_raw");
   }
@@ -334,6 +336,10 @@ static int run_kpm(const Graph* G, const Filter* F, int M, int Nz, uint64_t seed
   if (Nz < 1 || Nz > 65536) return fail(DOS_EINVAL, "Nz must be in [1, 65536]");
   if (prec != DOS_FP32 && prec != DOS_BF16 && prec != DOS_FP16) return fail(DOS_EINVAL, "unknown precision");
   if (F && F->g != G) return fail(DOS_EINVAL, "filter belongs to another graph");
+  if (mode == kModeLdos && op.kind != 0) {
+    if (prec != DOS_FP32) return fail(DOS_EINVAL, "LDOS of A and D - A is computed in FP32 only");
+    mode = kModeLdosOp;  // the light kernel's round layout carries both the own rows and the ids
+  }
   Plan plan;
   NDOS_CHECK(make_plan(G, Nz, prec, mode, &plan));
   switch (prec) {
@@ -343,6 +349,55 @@ static int run_kpm(const Graph* G, const Filter* F, int M, int Nz, uint64_t seed
       return run_steps<__half>(G, F, plan, M, Nz, seed, mode, d_out, C_out, s, op);
     default:
       return run_steps<float>(G, F, plan, M, Nz, seed, mode, d_out, C_out, s, op);
+  }
+}
+
+// operator and interval of a KPM run on op (DOS_OP_*): H and I - H on
+// their fixed intervals, A and D - A on [lo, hi] when lo < hi, else on the
+// Gershgorin interval ([-d_max, d_max], [0, 2 d_max])
+static int op_spec(const Graph* G, int op, double lo, double hi, OpSpec* spec, double* interval_out) {
+  double a = -1.0, b = 1.0;
+  switch (op) {
+    case DOS_OP_NORMALIZED_ADJACENCY:
+      break;
+    case DOS_OP_NORMALIZED_LAPLACIAN:  // I - H on [0, 2]: (I - H) - 1 = -H
+      a = 0.0;
+      b = 2.0;
+      spec->negate_odd = 1;
+      break;
+    case DOS_OP_ADJACENCY:
+    case DOS_OP_LAPLACIAN: {
+      spec->kind = op == DOS_OP_ADJACENCY ? 1 : 2;
+      if (lo < hi) {
+        a = lo;
+        b = hi;
+      } else {
+        const double dmax = static_cast<double>(G->max_deg);
+        a = op == DOS_OP_ADJACENCY ? -dmax : 0.0;
+        b = op == DOS_OP_ADJACENCY ? dmax : 2.0 * dmax;
+      }
+      spec->c = 0.5 * (a + b);
+      spec->inv_r = 2.0 / (b - a);
+      break;
+    }
+    default:
+      return fail(DOS_EINVAL, "unknown operator");
+  }
+  if (interval_out) {
+    interval_out[0] = a;
+    interval_out[1] = b;
+  }
+  return DOS_OK;
+}
+
+// rows m = 1, 3, 5, ... of a moment-major [M][n] matrix change sign
+__global__ void k_negate_odd_rows(float* __restrict__ c, int M, int64_t n) {
+  const int64_t total = static_cast<int64_t>(M / 2) * n;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t r = e / n;
+    float* p = c + static_cast<size_t>(2 * r + 1) * n + (e - r * n);
+    *p = -*p;
   }
 }
 
@@ -374,40 +429,28 @@ int dos_moments_op(dos_graph_t g, int op, double lo, double hi, int M, int Nz, u
   if (!g || !d_out) return fail(DOS_EINVAL, "dos_moments_op: null argument");
   const Graph* G = reinterpret_cast<const Graph*>(g);
   if (G->n < 1) return fail(DOS_EINVAL, "dos_moments_op: graph has no edges");
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   OpSpec spec;
-  double a = -1.0, b = 1.0;
-  switch (op) {
-    case DOS_OP_NORMALIZED_ADJACENCY:
-      break;
-    case DOS_OP_NORMALIZED_LAPLACIAN:  // I - H on [0, 2]: (I - H) - 1 = -H
-      a = 0.0;
-      b = 2.0;
-      spec.negate_odd = 1;
-      break;
-    case DOS_OP_ADJACENCY:
-    case DOS_OP_LAPLACIAN: {
-      spec.kind = op == DOS_OP_ADJACENCY ? 1 : 2;
-      if (lo < hi) {
-        a = lo;
-        b = hi;
-      } else {  // Gershgorin discs: [-d_max, d_max] for A, [0, 2 d_max] for D - A
-        const double dmax = static_cast<double>(G->max_deg);
-        a = op == DOS_OP_ADJACENCY ? -dmax : 0.0;
-        b = op == DOS_OP_ADJACENCY ? dmax : 2.0 * dmax;
-      }
-      spec.c = 0.5 * (a + b);
-      spec.inv_r = 2.0 / (b - a);
-      break;
-    }
-    default:
-      return fail(DOS_EINVAL, "dos_moments_op: unknown operator");
+  NDOS_CHECK(op_spec(G, op, lo, hi, &spec, interval_out));
+  return run_kpm(G, nullptr, M, Nz, seed, prec, kModeDos, d_out, nullptr, static_cast<cudaStream_t>(stream), spec);
+}
+
+int ldos_moments_op(dos_graph_t g, int op, double lo, double hi, int M, int Nz, uint64_t seed, float* C_out,
+                    double* d_out, double* interval_out, void* stream) {
+  clear_error();
+  if (!g || !C_out) return fail(DOS_EINVAL, "ldos_moments_op: null argument");
+  const Graph* G = reinterpret_cast<const Graph*>(g);
+  if (G->n < 1) return fail(DOS_EINVAL, "ldos_moments_op: graph has no edges");
+  OpSpec spec;
+  NDOS_CHECK(op_spec(G, op, lo, hi, &spec, interval_out));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  NDOS_CHECK(run_kpm(G, nullptr, M, Nz, seed, DOS_FP32, kModeLdos, d_out, C_out, s, spec));
+  if (spec.negate_odd && M > 1) {  // I - H: T_m(-H) = (-1)^m T_m(H), row by row
+    const int64_t work = static_cast<int64_t>(M / 2) * G->n;
+    k_negate_odd_rows<<<static_cast<unsigned>(std::min<int64_t>((work + 255) / 256, 8LL * num_sms())), 256, 0, s>>>(
+        C_out, M, G->n);
+    NDOS_LAUNCHED();
   }
-  if (interval_out) {
-    interval_out[0] = a;
-    interval_out[1] = b;
-  }
-  return run_kpm(G, nullptr, M, Nz, seed, prec, kModeDos, d_out, nullptr, s, spec);
+  return DOS_OK;
 }
 
 int dos_set_plan(int tile_width, int ctas_per_sm) {

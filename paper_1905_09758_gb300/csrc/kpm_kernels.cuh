@@ -26,6 +26,7 @@
 // round's contiguous data in shared memory with bulk copies (k_cheb_light).
 #pragma once
 
+#include <type_traits>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -36,10 +37,17 @@ namespace netdos {
 constexpr int kStepThreads = 256;
 constexpr int kStepWarps = kStepThreads / 32;
 
-// DOS: fused moment dots on H; LDOS: per-node products on H; DOS_OP: fused
-// moment dots on another operator (A or D - A, shifted and scaled), a
-// separate instance so that the H kernels carry no operator code
-enum StepMode { kModeDos = 0, kModeLdos = 1, kModeDosOp = 2 };
+// DOS: fused moment dots on H; LDOS: per-node products on H; DOS_OP /
+// LDOS_OP: the same on another operator (A or D - A, shifted and scaled),
+// separate instances so that the H kernels carry no operator code
+enum StepMode { kModeDos = 0, kModeLdos = 1, kModeDosOp = 2, kModeLdosOp = 3 };
+
+template <int MODE>
+struct ModeOf {
+  static constexpr bool op = MODE == kModeDosOp || MODE == kModeLdosOp;  // X~ on unscaled vectors
+  static constexpr bool ldos = MODE == kModeLdos || MODE == kModeLdosOp;  // per-node outputs, no dots
+  static constexpr bool own = MODE != kModeLdos;  // the row's own U_k (dots or the X~ diagonal term)
+};
 
 template <typename T>
 struct VecT;
@@ -218,12 +226,13 @@ __device__ __forceinline__ void step_epilogue(const StepParams& prm, bool active
                                               double& dd1) {
   constexpr int V = VecT<T>::N;
   constexpr int TW = Q * V;
+  using MD = ModeOf<MODE>;
   float prod0 = 0.f, prod1 = 0.f;
   if (active) {
     const size_t off = (static_cast<size_t>(tile) * prm.n + p) * TW + ql * V;
     uint4* pn = reinterpret_cast<uint4*>(reinterpret_cast<T*>(prm.u_pn) + off);
     float u[V];
-    if (MODE != kModeDosOp) {
+    if (!MD::op) {
       const float sc = (prm.first ? 1.0f : 2.0f) / fd;
 #pragma unroll
       for (int v = 0; v < V; ++v) u[v] = fmaf(acc[v], sc, -prev[v]);
@@ -238,7 +247,7 @@ __device__ __forceinline__ void step_epilogue(const StepParams& prm, bool active
     const uint4 packed = pack16<T>(u);
     st_stream(pn, packed);
     unpack16<T>(packed, u);  // the dots use the stored (rounded) values
-    if (MODE != kModeLdos) {
+    if (!MD::ldos) {
 #pragma unroll
       for (int v = 0; v < V; ++v) {
         prod0 = fmaf(u[v], u[v], prod0);
@@ -258,9 +267,9 @@ __device__ __forceinline__ void step_epilogue(const StepParams& prm, bool active
 #pragma unroll
   for (int s = 1; s < Q; s <<= 1) {
     prod0 += __shfl_xor_sync(0xffffffffu, prod0, s);
-    if (MODE != kModeLdos) prod1 += __shfl_xor_sync(0xffffffffu, prod1, s);
+    if (!MD::ldos) prod1 += __shfl_xor_sync(0xffffffffu, prod1, s);
   }
-  if (MODE != kModeLdos && prm.gid) {
+  if (!MD::ldos && prm.gid) {
     // batch: per-graph sums.  Rows are grouped by graph, so a warp's rows
     // nearly always share one graph: reduce in the warp and issue one atomic
     // per dot instead of one per row (the rows of a graph all hit the same
@@ -268,7 +277,7 @@ __device__ __forceinline__ void step_epilogue(const StepParams& prm, bool active
     const int32_t g = active ? prm.gid[p] : -1;
     const int32_t g0 = __shfl_sync(0xffffffffu, g, 0);
     const bool uniform = __all_sync(0xffffffffu, !active || g == g0);
-    const float wd = MODE == kModeDosOp ? 1.0f : fd;  // <V_a, V_b> = sum_i w_i <U_a, U_b>_i
+    const float wd = MD::op ? 1.0f : fd;  // <V_a, V_b> = sum_i w_i <U_a, U_b>_i
     double a0 = active && owner ? static_cast<double>(wd * prod0) : 0.0;
     double a1 = active && owner ? static_cast<double>(wd * prod1) : 0.0;
     if (uniform) {
@@ -288,12 +297,13 @@ __device__ __forceinline__ void step_epilogue(const StepParams& prm, bool active
     return;
   }
   if (active && owner) {
-    if (MODE != kModeLdos) {
-      const float wd = MODE == kModeDosOp ? 1.0f : fd;  // <V_a, V_b> = sum_i w_i <U_a, U_b>_i
+    if (!MD::ldos) {
+      const float wd = MD::op ? 1.0f : fd;  // <V_a, V_b> = sum_i w_i <U_a, U_b>_i
       dd0 += static_cast<double>(wd * prod0);
       dd1 += static_cast<double>(wd * prod1);
     } else {
-      const float vsum = prod0 * sqrtf(fd);  // sum_j z_j (V_{k+1})_j of this tile
+      // sum_j z_j (V_{k+1})_j of this tile (V = S^{-1} U on H, U on X~)
+      const float vsum = MD::op ? prod0 : prod0 * sqrtf(fd);
       dd0 += static_cast<double>(vsum);
       float* dst = prm.ldos + compact;
       if (prm.ldos_atomic)
@@ -392,9 +402,9 @@ __global__ void __launch_bounds__(kStepThreads) k_cheb_heavy(const StepParams pr
     if (warp == 0) {
       if (!prm.first)
         unpack16<T>(ld_stream(reinterpret_cast<const uint4*>(reinterpret_cast<const T*>(prm.u_pn) + off)), prev);
-      if (MODE != kModeLdos)
+      if (ModeOf<MODE>::own)
         unpack16<T>(ld_gather(reinterpret_cast<const uint4*>(reinterpret_cast<const T*>(prm.u_cur) + off)), own);
-      else {
+      if (ModeOf<MODE>::ldos) {
         orig = static_cast<uint32_t>(prm.orig[p]);
         compact = prm.compact[p];
       }
@@ -438,7 +448,7 @@ __global__ void __launch_bounds__(kStepThreads) k_cheb_heavy(const StepParams pr
   if (threadIdx.x == 0) {
     const size_t i = static_cast<size_t>(tile) * gridDim.x + blockIdx.x;
     prm.partial[i] = dd0;
-    if (MODE != kModeLdos) prm.partial[prm.part_width + i] = dd1;
+    if (!ModeOf<MODE>::ldos) prm.partial[prm.part_width + i] = dd1;
   }
 }
 
@@ -471,9 +481,9 @@ __global__ void __launch_bounds__(kStepThreads) k_cheb_medium(const StepParams p
     uint32_t orig = 0;
     int32_t compact = 0;
     if (!prm.first) unpack16<T>(ld_stream(reinterpret_cast<const uint4*>(reinterpret_cast<const T*>(prm.u_pn) + off)), prev);
-    if (MODE != kModeLdos)
+    if (ModeOf<MODE>::own)
       unpack16<T>(ld_gather(reinterpret_cast<const uint4*>(reinterpret_cast<const T*>(prm.u_cur) + off)), own);
-    else {
+    if (ModeOf<MODE>::ldos) {
       orig = static_cast<uint32_t>(prm.orig[p]);
       compact = prm.compact[p];
     }
@@ -502,7 +512,7 @@ __global__ void __launch_bounds__(kStepThreads) k_cheb_medium(const StepParams p
   if (threadIdx.x == 0) {
     const size_t i = static_cast<size_t>(prm.mid_part_off) + static_cast<size_t>(tile) * gridDim.x + blockIdx.x;
     prm.partial[i] = dd0;
-    if (MODE != kModeLdos) prm.partial[prm.part_width + i] = dd1;
+    if (!ModeOf<MODE>::ldos) prm.partial[prm.part_width + i] = dd1;
   }
 }
 
@@ -529,8 +539,9 @@ struct RoundLayout {
   static constexpr int off_rp = 0;
   static constexpr int off_col = off_rp + RP;
   static constexpr int off_prev = off_col + COL;
-  static constexpr int off_aux = off_prev + BLK;
-  static constexpr int SLOT = off_aux + (MODE != kModeLdos ? BLK : 2 * IDS);
+  static constexpr int off_aux = off_prev + BLK;                              // own U_k rows
+  static constexpr int off_ids = off_aux + (ModeOf<MODE>::own ? BLK : 0);     // original / compact ids
+  static constexpr int SLOT = off_ids + (ModeOf<MODE>::ldos ? 2 * IDS : 0);
   static constexpr int WARP = 2 * SLOT;  // two slots per warp
 };
 
@@ -591,17 +602,18 @@ __global__ void __launch_bounds__(kStepThreads, 3) k_cheb_light(const StepParams
     const uint32_t col_bytes = static_cast<uint32_t>((((e1 + 3) & ~int64_t(3)) - ea) * 4);
     const uint32_t blk_bytes = static_cast<uint32_t>((r1 - r0) * ROWB);
     const uint32_t id_bytes = static_cast<uint32_t>((((r1 + 3) & ~int64_t(3)) - r0i) * 4);
-    uint32_t tx = rp_bytes + col_bytes + (prm.first ? 0u : blk_bytes) + (MODE != kModeLdos ? blk_bytes : 2 * id_bytes);
+    uint32_t tx = rp_bytes + col_bytes + (prm.first ? 0u : blk_bytes) + (ModeOf<MODE>::own ? blk_bytes : 0u) +
+                  (ModeOf<MODE>::ldos ? 2 * id_bytes : 0u);
     mbar_arrive_expect_tx(&bar[s], tx);
     const size_t row_off = (static_cast<size_t>(c.tile) * prm.n + r0) * TW;
     bulk_g2s(sl + L::off_rp, prm.row_ptr + r0a, rp_bytes, &bar[s]);
     bulk_g2s(sl + L::off_col, prm.col + ea, col_bytes, &bar[s]);
     if (!prm.first) bulk_g2s(sl + L::off_prev, reinterpret_cast<const T*>(prm.u_pn) + row_off, blk_bytes, &bar[s]);
-    if (MODE != kModeLdos) {
+    if (ModeOf<MODE>::own)
       bulk_g2s(sl + L::off_aux, reinterpret_cast<const T*>(prm.u_cur) + row_off, blk_bytes, &bar[s]);
-    } else {
-      bulk_g2s(sl + L::off_aux, prm.orig + r0i, id_bytes, &bar[s]);
-      bulk_g2s(sl + L::off_aux + L::IDS, prm.compact + r0i, id_bytes, &bar[s]);
+    if (ModeOf<MODE>::ldos) {
+      bulk_g2s(sl + L::off_ids, prm.orig + r0i, id_bytes, &bar[s]);
+      bulk_g2s(sl + L::off_ids + L::IDS, prm.compact + r0i, id_bytes, &bar[s]);
     }
   };
 
@@ -673,11 +685,11 @@ __global__ void __launch_bounds__(kStepThreads, 3) k_cheb_light(const StepParams
       beg = rp[grp];
       end = rp[grp + 1];
       if (!prm.first) unpack16<T>(*reinterpret_cast<const uint4*>(sl + L::off_prev + grp * ROWB + ql * 16), prev);
-      if (MODE != kModeLdos) {
+      if (ModeOf<MODE>::own)
         unpack16<T>(*reinterpret_cast<const uint4*>(sl + L::off_aux + grp * ROWB + ql * 16), own);
-      } else {
-        orig = static_cast<uint32_t>(reinterpret_cast<const int32_t*>(sl + L::off_aux)[r0 + grp - r0i]);
-        compact = reinterpret_cast<const int32_t*>(sl + L::off_aux + L::IDS)[r0 + grp - r0i];
+      if (ModeOf<MODE>::ldos) {
+        orig = static_cast<uint32_t>(reinterpret_cast<const int32_t*>(sl + L::off_ids)[r0 + grp - r0i]);
+        compact = reinterpret_cast<const int32_t*>(sl + L::off_ids + L::IDS)[r0 + grp - r0i];
       }
     }
     float acc[V];
@@ -700,7 +712,7 @@ __global__ void __launch_bounds__(kStepThreads, 3) k_cheb_light(const StepParams
   if (threadIdx.x == 0) {
     const size_t i = static_cast<size_t>(prm.light_part_off) + blockIdx.x;
     prm.partial[i] = dd0;
-    if (MODE != kModeLdos) prm.partial[prm.part_width + i] = dd1;
+    if (!ModeOf<MODE>::ldos) prm.partial[prm.part_width + i] = dd1;
   }
 }
 
@@ -855,13 +867,39 @@ int launch_step_q(const Plan& plan, const StepParams& prm, cudaStream_t s, const
       break;                                          \
   }
 
+// one tile width, dispatch on the mode (LDOS on A / D - A: FP32 storage only)
+template <typename T, int Q>
+int launch_step_mode(const Plan& plan, int mode, const StepParams& prm, cudaStream_t s, const SideStreams& side) {
+  switch (mode) {
+    case kModeDos:
+      return launch_step_q<T, Q, kModeDos>(plan, prm, s, side);
+    case kModeLdos:
+      return launch_step_q<T, Q, kModeLdos>(plan, prm, s, side);
+    case kModeDosOp:
+      return launch_step_q<T, Q, kModeDosOp>(plan, prm, s, side);
+    default:
+      if constexpr (std::is_same<T, float>::value) return launch_step_q<T, Q, kModeLdosOp>(plan, prm, s, side);
+      return fail(DOS_EINVAL, "LDOS of A and D - A is computed in FP32 only");
+  }
+}
+
+template <typename T, int Q>
+int config_mode(int mode, int* smem, int* ctas) {
+  switch (mode) {
+    case kModeLdos:
+      return light_config_q<T, Q, kModeLdos>(smem, ctas);
+    case kModeLdosOp:
+      if constexpr (std::is_same<T, float>::value) return light_config_q<T, Q, kModeLdosOp>(smem, ctas);
+      return fail(DOS_EINVAL, "LDOS of A and D - A is computed in FP32 only");
+    default:  // kModeDos; kModeDosOp has the same layout
+      return light_config_q<T, Q, kModeDos>(smem, ctas);
+  }
+}
+
 // Chebyshev step launch for storage type T (instantiated in kpm_<type>.cu)
 template <typename T>
 int launch_step(const Plan& plan, int mode, const StepParams& prm, cudaStream_t s, const SideStreams& side) {
-#define NDOS_LAUNCH_CALL(TT, QQ)                                                    \
-  (mode == kModeDos   ? launch_step_q<TT, QQ, kModeDos>(plan, prm, s, side)         \
-   : mode == kModeLdos ? launch_step_q<TT, QQ, kModeLdos>(plan, prm, s, side)       \
-                       : launch_step_q<TT, QQ, kModeDosOp>(plan, prm, s, side))
+#define NDOS_LAUNCH_CALL(TT, QQ) launch_step_mode<TT, QQ>(plan, mode, prm, s, side)
   NDOS_DISPATCH_Q(T, plan.q, NDOS_LAUNCH_CALL)
 #undef NDOS_LAUNCH_CALL
   return fail(DOS_EINVAL, "unsupported tile width");
@@ -870,8 +908,7 @@ int launch_step(const Plan& plan, int mode, const StepParams& prm, cudaStream_t 
 // dynamic shared memory and resident CTAs per SM of the light kernel
 template <typename T>
 int step_config(int q, int mode, int* smem, int* ctas) {
-#define NDOS_CONFIG_CALL(TT, QQ) \
-  (mode == kModeDos ? light_config_q<TT, QQ, kModeDos>(smem, ctas) : light_config_q<TT, QQ, kModeLdos>(smem, ctas))
+#define NDOS_CONFIG_CALL(TT, QQ) config_mode<TT, QQ>(mode, smem, ctas)
   NDOS_DISPATCH_Q(T, q, NDOS_CONFIG_CALL)
 #undef NDOS_CONFIG_CALL
   return fail(DOS_EINVAL, "unsupported tile width");
