@@ -280,6 +280,7 @@ def run_ours(args):
     gql = None if args.no_gql else measure_gql(seed)
     ops = None if args.no_operators else measure_operators(seed)
     ndr = None if args.no_nd else measure_nd(seed)
+    fns = None if args.no_functions else measure_functions(seed)
     ms, e2e_s = max_over_ranks(dist, [ms, e2e_s], dev)
     if rank != 0:
         if dist is not None:
@@ -342,6 +343,8 @@ def run_ours(args):
         out["operators"] = ops
     if ndr is not None:
         out["nested_dissection"] = ndr
+    if fns is not None:
+        out["matrix_functions"] = fns
     if not args.no_time_to_l1:
         out["time_to_l1"] = time_to_l1(src_d, dst_d, n_nodes, seed, with_learned=not args.no_learned)
     if args.scale_1b:
@@ -732,11 +735,10 @@ def measure_nd(seed, reps: int = 2) -> dict:
     """Exact PDOS moments by nested dissection against the stochastic diagonal
     estimator (ldos_moments, Nz = 64) on a 316 x 316 grid and a 100k-node
     random geometric graph: time, partition statistics, and the largest error
-    on sampled nodes against the oracle's unit-probe recurrence (the exact
+    on sampled nodes against a unit-probe recurrence in scipy (the exact
     diagonal entries T_m(H)_kk)."""
     import torch
 
-    import oracle
     import paper_1905_09758_gb300 as nd
     import synthgraphs as sg
 
@@ -760,18 +762,138 @@ def measure_nd(seed, reps: int = 2) -> dict:
 
         t_nd, (c_nd, stats) = timed(lambda: nd.dos_pdos_nd(g, m, leaf_size=ND["leaf"]))
         t_st, (c_st, _) = timed(lambda: nd.ldos_moments(g, m, ND["Nz_stochastic"], seed))
-        ref = oracle.build_csr(src, dst, n)
+        a = _adjacency(src, dst, n)
         rng = np.random.default_rng(seed)
-        sample = rng.choice(ref.n, ND["sampled_nodes"], replace=False)
-        z = np.zeros((ref.n, sample.size))
-        z[sample, np.arange(sample.size)] = 1.0
-        _, cz = oracle.kpm_direct(ref, z, m, ldos=True)
-        exact = cz[sample] * sample.size  # unit probes: C[k, m] = T_m(H)_kk / Nz
+        sample = rng.choice(a.shape[0], ND["sampled_nodes"], replace=False)
+        exact = _unit_probe_diagonal(a, sample, m)
         e_nd = float(np.abs(c_nd.cpu().numpy()[:, sample].T - exact).max())
         e_st = float(np.abs(c_st.cpu().numpy()[:, sample].T - exact).max())
-        out["graphs"][name] = {"n": ref.n, "nnz": ref.nnz, "nd_s": round(t_nd, 4), "stochastic_s": round(t_st, 4),
-                               "nd_max_err": float(f"{e_nd:.3e}"), "stochastic_max_err": float(f"{e_st:.3e}"),
-                               **stats}
+        out["graphs"][name] = {"n": a.shape[0], "nnz": int(a.nnz), "nd_s": round(t_nd, 4),
+                               "stochastic_s": round(t_st, 4), "nd_max_err": float(f"{e_nd:.3e}"),
+                               "stochastic_max_err": float(f"{e_st:.3e}"), **stats}
+    return out
+
+
+# ---------------------------------------------------------------------------
+# traces and diagonals of matrix functions (§6)
+# ---------------------------------------------------------------------------
+FUNCS = {"M": 60, "Nz": 16, "lanczos_steps": 30, "lanczos_Nz": 8, "small_M": 80, "small_Nz": 64}
+
+
+def measure_functions(seed, reps: int = 10) -> dict:
+    """Subgraph centrality exp(beta A)_kk and the Estrada-type trace
+    tr exp(beta A), beta = 1 / lambda_max estimate, on the 1.1M-node graph
+    (Lanczos interval, LDOS on A, coefficients, contraction): the time of
+    each stage and the contraction kernel's HBM throughput (CUDA events,
+    M N 4 + N 8 bytes per launch; its input, 264 MB, exceeds L2).  On
+    G(1500, 0.004) with 7 isolated nodes: the Estrada index tr exp(A) and
+    subgraph centrality against the dense eigendecomposition (numpy)."""
+    import torch
+
+    import paper_1905_09758_gb300 as nd
+    import synthgraphs as sg
+
+    src, dst, n = make_edges(seed)
+    g = nd.dos_build_csr(torch.from_numpy(src).cuda(), torch.from_numpy(dst).cuda(), n)
+    info = g.info()
+    nn = info["n"]
+    m, nz = FUNCS["M"], FUNCS["Nz"]
+
+    def wall(fn):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, res
+
+    t_iv, iv = wall(lambda: nd.dos_spectral_interval(g, "adjacency", FUNCS["lanczos_steps"], FUNCS["lanczos_Nz"],
+                                                     seed + 1, bound="ritz"))
+    beta = 1.0 / iv[1]
+    t_ldos, (cm, _, _) = wall(lambda: nd.ldos_moments_op(g, "adjacency", m, nz, seed, interval=iv))
+    coef = nd.dos_fn_coeffs("exp", beta, iv, m)
+    t_tr, tr = wall(lambda: nd.dos_fn_trace(g, coef, nd.dos_moments_op(g, "adjacency", m, nz, seed,
+                                                                       interval=iv)[0]).item())
+    out_d = torch.empty(nn, dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        nd.dos_fn_diag(cm, coef, out=out_d)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        nd.dos_fn_diag(cm, coef, out=out_d)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    diag_ms = e0.elapsed_time(e1) / reps
+    diag_bytes = 4.0 * m * nn + 8.0 * nn + 8.0 * m
+    diag_gbs = diag_bytes / (diag_ms * 1e-3) / 1e9
+    peak, peak_kind = load_peaks()
+    sc = out_d.cpu().numpy()
+    large = {"workload": "chung_lu_1M_twins_50k (unfiltered)", "op": "adjacency", "fn": "exp(beta A)",
+             "beta": float(f"{beta:.6g}"), "M": m, "Nz": nz, "interval": [round(iv[0], 3), round(iv[1], 3)],
+             "interval_ms": round(1e3 * t_iv, 3), "ldos_ms": round(1e3 * t_ldos, 3),
+             "trace_ms": round(1e3 * t_tr, 3), "trace": float(f"{tr:.6e}"),
+             "diag_kernel_ms": round(diag_ms, 4), "diag_kernel_gbs": round(diag_gbs, 1),
+             "diag_kernel_frac": round(diag_gbs / peak, 3), "diag_kernel_peak": f"{peak_kind} hbm_gbs {peak}",
+             "subgraph_centrality_max": float(f"{sc.max():.6e}"), "subgraph_centrality_median":
+                 float(f"{np.median(sc):.6e}")}
+    # accuracy against the dense spectrum on a graph small enough for it
+    src_s, dst_s, n_s = sg.erdos_renyi(1500, 0.004, seed + 8)
+    gs = nd.dos_build_csr(torch.from_numpy(src_s).cuda(), torch.from_numpy(dst_s).cuda(), n_s + 7)
+    a = _adjacency(src_s, dst_s, n_s + 7)
+    t0 = time.perf_counter()
+    lam, q = np.linalg.eigh(a.toarray())
+    t_dense = time.perf_counter() - t0
+    exact_sc = (q * q) @ np.exp(lam)
+    exact_ee = float(np.exp(lam).sum() + (n_s + 7 - a.shape[0]))
+    t_ee, (ee, _) = wall(lambda: nd.matrix_function_trace(gs, "adjacency", "exp", 1.0, M=FUNCS["small_M"],
+                                                          Nz=FUNCS["small_Nz"], seed=seed))
+    t_sc, (sc_s, _) = wall(lambda: nd.matrix_function_diag(gs, "adjacency", "exp", 1.0, M=FUNCS["small_M"],
+                                                           Nz=FUNCS["small_Nz"], seed=seed))
+    rel = np.abs(sc_s.cpu().numpy() - exact_sc) / exact_sc
+    small = {"workload": "erdos_renyi_1500_p0.004 + 7 isolated", "M": FUNCS["small_M"], "Nz": FUNCS["small_Nz"],
+             "estrada_index": float(f"{ee:.6e}"), "estrada_exact": float(f"{exact_ee:.6e}"),
+             "estrada_rel_err": float(f"{abs(ee - exact_ee) / exact_ee:.3e}"), "estrada_ms": round(1e3 * t_ee, 3),
+             "subgraph_centrality_median_rel_err": float(f"{np.median(rel):.3e}"),
+             "subgraph_centrality_ms": round(1e3 * t_sc, 3), "dense_eigh_cpu_ms": round(1e3 * t_dense, 1)}
+    return {"large": large, "small": small}
+
+
+def _adjacency(src, dst, n):
+    """Symmetric 0/1 adjacency (scipy CSR, float64) of the nodes with edges,
+    in increasing original id (the library's compact order): duplicates
+    merged, self-loops dropped.  Accuracy references of the bench only."""
+    import scipy.sparse as sp
+
+    src, dst = np.asarray(src, np.int64), np.asarray(dst, np.int64)
+    keep = src != dst
+    src, dst = src[keep], dst[keep]
+    a = sp.coo_matrix((np.ones(2 * src.size), (np.concatenate([src, dst]), np.concatenate([dst, src]))),
+                      shape=(n, n)).tocsr()
+    a.sum_duplicates()
+    a.data[:] = 1.0
+    nodes = np.flatnonzero(np.diff(a.indptr) > 0)
+    return a[nodes][:, nodes].tocsr()
+
+
+def _unit_probe_diagonal(a, sample, m):
+    """T_m(H)_kk for the sampled nodes k by the Chebyshev recurrence from the
+    unit vectors e_k (H = D^{-1/2} A D^{-1/2}); shape (len(sample), m)."""
+    import scipy.sparse as sp
+
+    s = 1.0 / np.sqrt(np.diff(a.indptr).astype(np.float64))
+    h = sp.diags(s) @ a @ sp.diags(s)
+    z = np.zeros((a.shape[0], len(sample)))
+    z[sample, np.arange(len(sample))] = 1.0
+    out = np.zeros((len(sample), m))
+    v_prev, v = z, h @ z
+    out[:, 0] = 1.0
+    if m > 1:
+        out[:, 1] = v[sample, np.arange(len(sample))]
+    for k in range(2, m):
+        v_prev, v = v, 2.0 * (h @ v) - v_prev
+        out[:, k] = v[sample, np.arange(len(sample))]
     return out
 
 
@@ -1027,6 +1149,7 @@ def main():
     ap.add_argument("--no-gql", action="store_true")
     ap.add_argument("--no-operators", action="store_true")
     ap.add_argument("--no-nd", action="store_true")
+    ap.add_argument("--no-functions", action="store_true")
     ap.add_argument("--scale-1b", action="store_true",
                     help="also run the 60M-node, 1e9-edge graph (about 100 GB of device memory, a few minutes)")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)

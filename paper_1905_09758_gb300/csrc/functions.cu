@@ -51,30 +51,35 @@ __global__ void k_fn_trace(const double* __restrict__ g, const double* __restric
 }
 
 constexpr int kDiagThreads = 256;
+constexpr int kDiagWarps = kDiagThreads / 32;
 constexpr int kDiagChunk = 2048;  // coefficients staged in shared memory at a time
-constexpr int kDiagUnroll = 8;    // independent row loads in flight per thread
+constexpr int kDiagUnroll = 4;    // independent row loads in flight per thread
 
 // out[k] = s sum_m (g_m / s) C[m][k], s = max |g_m| (FP32 products and sums of
 // the scaled coefficients: no overflow for large f, FP32 FMA throughput; the
-// scale is applied in FP64).  VEC = 4: each thread owns 4 consecutive nodes
-// (16-byte loads, n % 4 == 0 and C 16-byte aligned); VEC = 1: one node.
+// scale is applied in FP64).  Each thread owns VEC consecutive nodes (VEC = 4:
+// 16-byte loads, n % 4 == 0 and C 16-byte aligned; VEC = 1: ragged n) and
+// runs over all rows m, so a CTA reads 256 VEC contiguous floats of each row.
+// At most 32 registers: eight CTAs per SM are resident, so n = 1.1M nodes
+// (1074 CTAs) run in one wave.
 template <int VEC>
-__global__ void __launch_bounds__(kDiagThreads) k_fn_diag(const float* __restrict__ C, int64_t n, int m_count,
-                                                          const double* __restrict__ g, double* __restrict__ out) {
+__global__ void __launch_bounds__(kDiagThreads, 8) k_fn_diag(const float* __restrict__ C, int64_t n, int m_count,
+                                                             const double* __restrict__ g, double* __restrict__ out) {
   __shared__ float gs[kDiagChunk];
-  __shared__ double s_max[kDiagThreads / 32];
+  __shared__ double s_max[kDiagWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double mx = 0.0;
   for (int m = threadIdx.x; m < m_count; m += kDiagThreads) mx = fmax(mx, fabs(g[m]));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = mx;
+  if (lane == 0) s_max[warp] = mx;
   __syncthreads();
   mx = 0.0;
 #pragma unroll
-  for (int w = 0; w < kDiagThreads / 32; ++w) mx = fmax(mx, s_max[w]);
+  for (int w = 0; w < kDiagWarps; ++w) mx = fmax(mx, s_max[w]);
   const double scale = mx > 0.0 ? mx : 1.0;
   const int64_t k0 = (static_cast<int64_t>(blockIdx.x) * kDiagThreads + threadIdx.x) * VEC;
-  const bool live = k0 < n;
+  const bool live = k0 < n;  // n % VEC == 0 when VEC = 4, so all VEC nodes exist
   float acc[VEC];
 #pragma unroll
   for (int v = 0; v < VEC; ++v) acc[v] = 0.f;
@@ -162,8 +167,8 @@ extern "C" int dos_fn_diag(const float* C, int64_t N, int M, const double* coef,
   if (!C || !coef || !out || N < 1 || M < 1) return fail(DOS_EINVAL, "dos_fn_diag: bad argument");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const bool vec = N % 4 == 0 && (reinterpret_cast<uintptr_t>(C) & 15) == 0;
-  const int64_t threads = vec ? N / 4 : N;
-  const unsigned blocks = static_cast<unsigned>((threads + kDiagThreads - 1) / kDiagThreads);
+  const int64_t per_cta = vec ? 4 * kDiagThreads : kDiagThreads;  // VEC nodes per thread
+  const unsigned blocks = static_cast<unsigned>((N + per_cta - 1) / per_cta);
   if (vec)
     k_fn_diag<4><<<blocks, kDiagThreads, 0, s>>>(C, N, M, coef, out);
   else
