@@ -188,9 +188,12 @@ int dos_filter_export(dos_filter_t f, int32_t* class_id, void* stream) {
 void dos_filter_destroy(dos_filter_t f) {
   if (!f) return;
   Filter* F = reinterpret_cast<Filter*>(f);
+  // the buffers are pool allocations: wait for any work still using them,
+  // then return them to the pool
+  cudaDeviceSynchronize();
   void* ptrs[] = {F->class_id, F->p_slot, F->slot_size};
   for (void* p : ptrs)
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, 0);
   delete F;
 }
 

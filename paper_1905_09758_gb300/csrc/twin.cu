@@ -43,18 +43,35 @@ __device__ __forceinline__ bool pendant_eligible(const int32_t* deg, const int32
   return deg[i] >= 2 && nleaf[i] == 1;
 }
 
-// warp per row: order-free hash of the open (mode 0), closed (1) or
-// leaf-reduced (2, pendant twins) neighbourhood; a node that cannot be a
-// pendant twin gets a hash of its own (mode 2)
-__global__ void k_row_hash(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-                           const int32_t* __restrict__ deg, int64_t n, int mode, const int32_t* __restrict__ nleaf,
-                           const int32_t* __restrict__ leaf_of, uint64_t* __restrict__ hash,
-                           int32_t* __restrict__ idx) {
+// Order-free hash of the open (mode 0), closed (1) or leaf-reduced (2,
+// pendant twins) neighbourhood of every row; a node that cannot be a pendant
+// twin gets a hash of its own (mode 2).  Modes 0 and 1 fold the hash to 32
+// bits (half the radix-sort passes; runs of equal keys are resolved by exact
+// comparison, so a collision only costs a comparison); mode 2 keeps 64 bits,
+// whose top bit marks the nodes that are not eligible.
+__device__ __forceinline__ void row_hash_store(int mode, int64_t i, uint64_t h, const int32_t* __restrict__ deg,
+                                               uint64_t* __restrict__ hash, int32_t* __restrict__ idx) {
+  if (mode == 1) h += mix_id(static_cast<uint64_t>(i)) + 0x9e3779b97f4a7c15ull;
+  if (mode == 2) h += 0x3c6ef372fe94f82bull;
+  h += mix_id(0x8000000000000000ull | static_cast<uint64_t>(deg[i]));
+  if (mode != 2) h = (h ^ (h >> 32)) & 0xffffffffull;
+  hash[i] = h;
+  idx[i] = static_cast<int32_t>(i);
+}
+
+// rows of degree >= 64 (degree-sorted positions [0, n_mid)): a warp per row,
+// four independent column loads per lane in flight
+__global__ void k_row_hash_wide(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                                const int32_t* __restrict__ deg, const int32_t* __restrict__ p_compact,
+                                int64_t n_mid, int mode, const int32_t* __restrict__ nleaf,
+                                const int32_t* __restrict__ leaf_of, uint64_t* __restrict__ hash,
+                                int32_t* __restrict__ idx) {
   const int lane = threadIdx.x & 31;
   const int64_t w0 = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
   const int64_t nw = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
-  for (int64_t i = w0; i < n; i += nw) {
-    if (mode == 2 && !pendant_eligible(deg, nleaf, i)) {
+  for (int64_t k = w0; k < n_mid; k += nw) {
+    const int64_t i = p_compact[k];
+    if (mode == 2 && !pendant_eligible(deg, nleaf, i)) {  // warp-uniform
       if (lane == 0) {
         hash[i] = 0x8000000000000000ull | static_cast<uint64_t>(i);
         idx[i] = static_cast<int32_t>(i);
@@ -62,16 +79,59 @@ __global__ void k_row_hash(const int64_t* __restrict__ row_ptr, const int32_t* _
       continue;
     }
     const int32_t skip = mode == 2 ? leaf_of[i] : -1;
+    const int64_t e1 = row_ptr[i + 1];
     uint64_t h = 0;
-    for (int64_t e = row_ptr[i] + lane; e < row_ptr[i + 1]; e += 32)
-      if (col[e] != skip) h += mix_id(static_cast<uint64_t>(col[e]));
+    for (int64_t e0 = row_ptr[i] + lane; e0 < e1; e0 += 128) {
+      int32_t c[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) c[u] = e0 + 32 * u < e1 ? col[e0 + 32 * u] : -1;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (c[u] >= 0 && c[u] != skip) h += mix_id(static_cast<uint64_t>(c[u]));
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xffffffffu, h, o);
-    if (lane == 0) {
-      if (mode == 1) h += mix_id(static_cast<uint64_t>(i)) + 0x9e3779b97f4a7c15ull;
-      if (mode == 2) h += 0x3c6ef372fe94f82bull;
-      hash[i] = h + mix_id(0x8000000000000000ull | static_cast<uint64_t>(deg[i]));
-      idx[i] = static_cast<int32_t>(i);
+    if (lane == 0) row_hash_store(mode, i, h, deg, hash, idx);
+  }
+}
+
+// rows of degree < kMediumDeg = 64 (positions [n_mid, n)): eight lanes per
+// row, four rows per warp, each lane loading its (at most eight) columns at once
+__global__ void k_row_hash_narrow(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                                  const int32_t* __restrict__ deg, const int32_t* __restrict__ p_compact,
+                                  int64_t n_mid, int64_t n, int mode, const int32_t* __restrict__ nleaf,
+                                  const int32_t* __restrict__ leaf_of, uint64_t* __restrict__ hash,
+                                  int32_t* __restrict__ idx) {
+  const int lane = threadIdx.x & 31, sub = lane >> 3, sl = lane & 7;
+  const int64_t w0 = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
+  const int64_t nw = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t k0 = n_mid + 4 * w0; k0 < n; k0 += 4 * nw) {  // warp-uniform bound
+    const int64_t k = k0 + sub;
+    const bool act = k < n;
+    const int64_t i = act ? p_compact[k] : 0;
+    const bool elig = act && (mode != 2 || pendant_eligible(deg, nleaf, i));
+    uint64_t h = 0;
+    if (elig) {
+      const int32_t skip = mode == 2 ? leaf_of[i] : -1;
+      const int64_t e0 = row_ptr[i] + sl, e1 = row_ptr[i + 1];
+      static_assert(kMediumDeg <= 64, "eight lanes x eight loads cover a light row");
+      int32_t c[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) c[u] = e0 + 8 * u < e1 ? col[e0 + 8 * u] : -1;
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (c[u] >= 0 && c[u] != skip) h += mix_id(static_cast<uint64_t>(c[u]));
+    }
+    h += __shfl_xor_sync(0xffffffffu, h, 4);
+    h += __shfl_xor_sync(0xffffffffu, h, 2);
+    h += __shfl_xor_sync(0xffffffffu, h, 1);
+    if (act && sl == 0) {
+      if (elig) {
+        row_hash_store(mode, i, h, deg, hash, idx);
+      } else {
+        hash[i] = 0x8000000000000000ull | static_cast<uint64_t>(i);
+        idx[i] = static_cast<int32_t>(i);
+      }
     }
   }
 }
@@ -367,15 +427,24 @@ static int find_classes(const Graph* G, int mode, int32_t* cid, Temps& t, const 
   NDOS_CHECK(t.get(&run_start, n));
   NDOS_CHECK(t.get(&n_runs_d, 1));
   NDOS_CUDA(cudaMemsetAsync(n_runs_d, 0, sizeof(unsigned long long), s));
-  k_row_hash<<<grid_for(n * 32), 256, 0, s>>>(G->row_ptr, G->col, G->deg, n, mode, nleaf, leaf_of, h, idx);
-  NDOS_LAUNCHED();
+  if (G->n_mid > 0) {
+    k_row_hash_wide<<<grid_for(G->n_mid * 32), 256, 0, s>>>(G->row_ptr, G->col, G->deg, G->p_compact, G->n_mid,
+                                                            mode, nleaf, leaf_of, h, idx);
+    NDOS_LAUNCHED();
+  }
+  if (n > G->n_mid) {
+    k_row_hash_narrow<<<grid_for((n - G->n_mid) * 8), 256, 0, s>>>(G->row_ptr, G->col, G->deg, G->p_compact,
+                                                                   G->n_mid, n, mode, nleaf, leaf_of, h, idx);
+    NDOS_LAUNCHED();
+  }
   cub::DoubleBuffer<uint64_t> kb(h, h_alt);
   cub::DoubleBuffer<int32_t> vb(idx, idx_alt);
+  const int key_bits = mode == 2 ? 64 : 32;
   size_t bytes = 0;
-  NDOS_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, bytes, kb, vb, n, 0, 64, s));
+  NDOS_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, bytes, kb, vb, n, 0, key_bits, s));
   char* tmp = nullptr;
   NDOS_CHECK(t.get(&tmp, bytes));
-  NDOS_CUDA(cub::DeviceRadixSort::SortPairs(tmp, bytes, kb, vb, n, 0, 64, s));
+  NDOS_CUDA(cub::DeviceRadixSort::SortPairs(tmp, bytes, kb, vb, n, 0, key_bits, s));
   count_launch();
   k_mark_runs<<<grid_for(n), 256, 0, s>>>(kb.Current(), vb.Current(), n, cid, run_start, n_runs_d);
   NDOS_LAUNCHED();
@@ -394,11 +463,14 @@ static int find_classes(const Graph* G, int mode, int32_t* cid, Temps& t, const 
 static int motif_filter_impl(const Graph* G, uint32_t motifs, cudaStream_t s, Filter* F) {
   const int64_t n = G->n;
   Temps t(s);
-  auto palloc = [](int32_t** p, int64_t count) -> int {
-    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), sizeof(int32_t) * (count > 0 ? count : 1));
+  // the filter's own buffers come from the stream-ordered pool (a filter per
+  // query would otherwise pay a cudaMalloc each time); dos_filter_destroy
+  // synchronises the device before it returns them
+  auto palloc = [s](int32_t** p, int64_t count) -> int {
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(p), sizeof(int32_t) * (count > 0 ? count : 1), s);
     if (e != cudaSuccess) {
       cudaGetLastError();
-      return cuda_fail(e, "cudaMalloc", __FILE__, __LINE__);
+      return cuda_fail(e, "cudaMallocAsync", __FILE__, __LINE__);
     }
     return DOS_OK;
   };
