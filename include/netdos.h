@@ -64,10 +64,12 @@ enum dos_build_flags {
   DOS_INPUT_HOST = 1 /* src/dst are host pointers; the library copies them */
 };
 
-/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+/* Instrumentation, not in the paper. Library version as MAJOR*10000 +
+ * MINOR*100 + PATCH. */
 int dos_version(void);
 
-/* Thread-local text describing the last failed call on this thread ("" if none). */
+/* Error reporting, not in the paper. Thread-local text describing the last
+ * failed call on this thread ("" if none). */
 const char* dos_last_error(void);
 
 /*
@@ -89,13 +91,15 @@ int dos_build_csr(const int64_t* src, const int64_t* dst, int64_t n_edges,
                   int64_t n_nodes, uint32_t flags, void* stream,
                   dos_graph_t* out);
 
-/* Sizes of a built graph [host outputs; any may be NULL]: N = non-isolated
- * nodes, nnz = stored nonzeros (2 x undirected edges), n_isolated = nodes
- * dropped for having no edge, n_original = n_nodes given to dos_build_csr. */
+/* §2.1 (the graph and its compacted node set). Sizes of a built graph [host
+ * outputs; any may be NULL]: N = non-isolated nodes, nnz = stored nonzeros (2
+ * x undirected edges), n_isolated = nodes dropped for having no edge,
+ * n_original = n_nodes given to dos_build_csr. */
 int dos_graph_info(dos_graph_t g, int64_t* n, int64_t* nnz,
                    int64_t* n_isolated, int64_t* n_original);
 
 /*
+ * §2.1 (A in CSR, degrees, D^{-1/2}).
  * dos_graph_export -- copy the CSR (compact ids) to caller buffers [device].
  *   row_ptr int64[N+1], col int32[nnz] (ascending within each row),
  *   deg int32[N], inv_sqrt_deg double[N] = 1/sqrt(deg) (IEEE, correctly
@@ -157,23 +161,23 @@ enum {
 int dos_motif_filter_ex(dos_graph_t g, uint32_t motifs, void* stream,
                         dos_filter_t* out);
 
-/* Removed eigenvalues [host]: up to `capacity` pairs (lambda, count) in
- * ascending lambda (0 for open twins, -1/d per degree d with closed twins,
- * +-1/sqrt(d) per degree d with pendant twins, +-1/2 for parallel paths;
- * equal values of different motifs are one entry);
- * *n_spikes (may be NULL) receives the total number of pairs.
- * Errors: DOS_EINVAL. */
+/* §3.4, Fig. 3 (motif eigenvalues). Removed eigenvalues [host]: up to
+ * `capacity` pairs (lambda, count) in ascending lambda (0 for open twins, -1/d
+ * per degree d with closed twins, +-1/sqrt(d) per degree d with pendant twins,
+ * +-1/2 for parallel paths; equal values of different motifs are one entry);
+ * *n_spikes (may be NULL) receives the total number of pairs. Errors:
+ * DOS_EINVAL. */
 int dos_filter_spikes(dos_filter_t f, double* spikes, int capacity,
                       int* n_spikes);
 
-/* Filter summary [host outputs; any may be NULL]: removed = sum over classes
- * of (size - 1) = number of eigenvalues at 0 the filter takes out,
- * n_classes = classes of size >= 2, r = N - removed. */
+/* §3.4 (filtered eigenvalue counts). Filter summary [host outputs; any may be
+ * NULL]: removed = sum over classes of (size - 1) = number of eigenvalues at 0
+ * the filter takes out, n_classes = classes of size >= 2, r = N - removed. */
 int dos_filter_info(dos_filter_t f, int64_t* removed, int64_t* n_classes,
                     int64_t* r);
 
-/* class_id [device] int32[N]: the smallest compact id in each node's class
- * (a node's own id if it has no twin).  Stream-ordered. */
+/* §3.4 (motif classes). class_id [device] int32[N]: the smallest compact id in
+ * each node's class (a node's own id if it has no twin).  Stream-ordered. */
 int dos_filter_export(dos_filter_t f, int32_t* class_id, void* stream);
 
 void dos_filter_destroy(dos_filter_t f);
@@ -282,6 +286,7 @@ int dos_density(const double* d, int M, int n_bins, int kernel, double scale,
                 void* stream);
 
 /*
+ * §3.1, Eq. (6), (9), (11); the allocation-free form is a project addition.
  * dos_moments_noalloc -- dos_moments (FP32 storage, no filter) for callers
  * that cannot allocate device memory.  The paper has no counterpart; this is
  * a deployment variant of the same computation.
@@ -338,7 +343,8 @@ int dos_pdos_nd(dos_graph_t g, int M, int leaf_size, double max_entries,
  * dos_lanczos -- M Lanczos steps on H from each of Nz Rademacher probes (the
  * probes of dos_moments for the same seed), FP32 vectors, FP64 reductions,
  * no reorthogonalisation.  Paper: §3.2 (H Z_M = Z_M Gamma_M + r_M e_M^T).
- *   alpha_out [device] double[Nz * M]: alpha_out[p * M + k] = alpha_k of probe p
+ *   alpha_out [device] double[Nz * M]: alpha_out[p * M + k] = alpha_k of probe
+ * p
  *   beta_out  [device] double[Nz * M]: beta_out[p * M + k] = ||w_{k+1}||, the
  *             coupling of steps k and k + 1 (the last one is the residual)
  *   steps_out [device] int32[Nz]: steps run; a probe stops early when
@@ -370,11 +376,11 @@ enum {
   DOS_BOUND_RITZ = 1      /* theta -+ beta_M |s_M|: tight once converged */
 };
 
-/* Per-probe bounds of dos_spectral_interval from Lanczos coefficients as
- * produced by dos_lanczos_op [device]: bounds_out[2p] = theta_min - r,
- * bounds_out[2p + 1] = theta_max + r [device double[2 Nz]], theta the extreme
- * eigenvalues of probe p's tridiagonal (bisection), r as chosen by bound
- * (DOS_BOUND_*).  Stream-ordered.  Errors: DOS_EINVAL. */
+/* §3.2 (Lanczos on X), Eq. (5). Per-probe bounds of dos_spectral_interval from
+ * Lanczos coefficients as produced by dos_lanczos_op [device]: bounds_out[2p]
+ * = theta_min - r, bounds_out[2p + 1] = theta_max + r [device double[2 Nz]],
+ * theta the extreme eigenvalues of probe p's tridiagonal (bisection), r as
+ * chosen by bound (DOS_BOUND_*).  Stream-ordered.  Errors: DOS_EINVAL. */
 int dos_ritz_bounds(const double* alpha, const double* beta,
                     const int32_t* steps, int M, int Nz, int bound,
                     double* bounds_out, void* stream);
@@ -413,18 +419,19 @@ int dos_gauss_rules(const double* alpha, const double* beta,
                     const int32_t* steps, int M, int Nz, double* nodes_out,
                     double* weights_out, void* stream);
 
-/* Chebyshev moments of the probe-averaged Gauss rules, d_out[m] =
- * (1/Nz) sum_p e_1^T T_m(Gamma_p) e_1, m < m_count [device double[m_count]];
- * equal to the KPM moments of the same probes for m <= 2 steps - 1 (Gauss
- * exactness).  Stream-ordered.  Errors: DOS_EINVAL, DOS_ENOMEM. */
+/* §3.2 (Gauss rule), Eq. (9). Chebyshev moments of the probe-averaged Gauss
+ * rules, d_out[m] = (1/Nz) sum_p e_1^T T_m(Gamma_p) e_1, m < m_count [device
+ * double[m_count]]; equal to the KPM moments of the same probes for m <= 2
+ * steps - 1 (Gauss exactness).  Stream-ordered.  Errors: DOS_EINVAL,
+ * DOS_ENOMEM. */
 int dos_gql_moments(const double* alpha, const double* beta,
                     const int32_t* steps, int M, int Nz, int m_count,
                     double* d_out, void* stream);
 
-/* GQL density: bin masses of the rules' point masses averaged over probes,
- * hist_out [device] double[n_bins] over n_bins equal bins of [-1, 1] (a node
- * within 1e-9 of an interior edge splits evenly).  Stream-ordered.
- * Errors: DOS_EINVAL. */
+/* §3.2, §4.1 (histogram). GQL density: bin masses of the rules' point masses
+ * averaged over probes, hist_out [device] double[n_bins] over n_bins equal
+ * bins of [-1, 1] (a node within 1e-9 of an interior edge splits evenly).
+ * Stream-ordered. Errors: DOS_EINVAL. */
 int dos_gql_histogram(const double* nodes, const double* weights, int M,
                       int Nz, int n_bins, double* hist_out, void* stream);
 
@@ -445,25 +452,28 @@ enum {
   DOS_FN_RESOLVENT = 1  /* f(x) = 1 / (1 - p x); 1 - p x must not vanish on [lo, hi] */
 };
 
-/* Chebyshev coefficients of f on [lo, hi]: coef_out [device double[M]] with
- * f(c + r x) ~ sum_m coef_out[m] T_m(x), by interpolation at max(4M, 256)
- * Chebyshev-Gauss points.  Stream-ordered.  Errors: DOS_EINVAL (unknown fn,
- * lo >= hi, M outside [1, 2^20], a resolvent pole inside [lo, hi]). */
+/* §6, Eq. (5) (Chebyshev expansion of f on [a, b]). Chebyshev coefficients of
+ * f on [lo, hi]: coef_out [device double[M]] with f(c + r x) ~ sum_m
+ * coef_out[m] T_m(x), by interpolation at max(4M, 256) Chebyshev-Gauss points.
+ * Stream-ordered.  Errors: DOS_EINVAL (unknown fn, lo >= hi, M outside [1,
+ * 2^20], a resolvent pole inside [lo, hi]). */
 int dos_fn_coeffs(int fn, double p, double lo, double hi, int M,
                   double* coef_out, void* stream);
 
-/* tr f(X): out [device double[1]] = N sum_m coef[m] d[m] + (nodes without
- * edges) x f(0), f(0) = 1 for both functions; d [device double[M]] DOS
- * moments of X~ on the same interval as coef (dos_moments_op), N the graph's
- * nodes with edges.  Stream-ordered.  Errors: DOS_EINVAL. */
+/* §6, Eq. (9), (11) (trace from moments). tr f(X): out [device double[1]] = N
+ * sum_m coef[m] d[m] + (nodes without edges) x f(0), f(0) = 1 for both
+ * functions; d [device double[M]] DOS moments of X~ on the same interval as
+ * coef (dos_moments_op), N the graph's nodes with edges.  Stream-ordered.
+ * Errors: DOS_EINVAL. */
 int dos_fn_trace(dos_graph_t g, const double* coef, const double* d, int M,
                  double* out, void* stream);
 
-/* f(X)_kk for every node: out[k] [device double[N]] = sum_m coef[m] C[m][k]
- * over the moment-major LDOS matrix C [device float[M * N]] of ldos_moments_op
- * (compact node ids).  FP32 products and sums of coef / max|coef|, the scale
- * applied in FP64 (no overflow for large f).  HBM-bound: reads M N 4 bytes.
- * Stream-ordered.  Errors: DOS_EINVAL. */
+/* §6, Eq. (10), (12) (diagonal from LDOS moments). f(X)_kk for every node:
+ * out[k] [device double[N]] = sum_m coef[m] C[m][k] over the moment-major LDOS
+ * matrix C [device float[M * N]] of ldos_moments_op (compact node ids).  FP32
+ * products and sums of coef / max|coef|, the scale applied in FP64 (no
+ * overflow for large f).  HBM-bound: reads M N 4 bytes. Stream-ordered.
+ * Errors: DOS_EINVAL. */
 int dos_fn_diag(const float* C, int64_t N, int M, const double* coef,
                 double* out, void* stream);
 
@@ -489,9 +499,10 @@ int dos_build_csr_batched(const int64_t* src, const int64_t* dst,
                           int64_t n_graphs, uint32_t flags, void* stream,
                           dos_graph_t* out);
 
-/* Batch sizes [host outputs; any may be NULL]: n_graphs (0 for a graph from
- * dos_build_csr), and per graph its non-isolated node count graph_n[n_graphs]
- * and isolated node count graph_isolated[n_graphs]. */
+/* Batches: a project addition (§2.1 per graph). Batch sizes [host outputs; any
+ * may be NULL]: n_graphs (0 for a graph from dos_build_csr), and per graph its
+ * non-isolated node count graph_n[n_graphs] and isolated node count
+ * graph_isolated[n_graphs]. */
 int dos_batch_info(dos_graph_t g, int64_t* n_graphs, int64_t* graph_n,
                    int64_t* graph_isolated);
 
@@ -514,6 +525,7 @@ int dos_moments_batched(dos_graph_t g, int M, int Nz, uint64_t seed, int prec,
                         double* d_out, void* stream);
 
 /*
+ * A project addition (tuning of the §3.1 step).
  * dos_autotune -- time the step kernel's candidate plans (probe tile widths
  * with at most 16 tiles, 1 to 3 light-row CTAs per SM) on this graph for
  * (Nz, prec) and keep the fastest on the handle; later dos_moments /
@@ -553,39 +565,46 @@ int dos_density_batched(const double* d, int M, int64_t n_graphs, int n_bins,
  * order, so results are bit-reproducible.
  * --------------------------------------------------------------------- */
 
-/* Network with n_layers weight layers of sizes[0] -> sizes[1] -> ... ->
- * sizes[n_layers] (each in [1, 8192], n_layers in [1, 16]); weights
- * He-uniform from SplitMix64(seed), biases 0.  Synchronises the device.
- * Errors: DOS_EINVAL, DOS_ENOMEM. */
+/* Learned reconstruction: a project addition, not in the paper. Network with
+ * n_layers weight layers of sizes[0] -> sizes[1] -> ... -> sizes[n_layers]
+ * (each in [1, 8192], n_layers in [1, 16]); weights He-uniform from
+ * SplitMix64(seed), biases 0.  Synchronises the device. Errors: DOS_EINVAL,
+ * DOS_ENOMEM. */
 int dos_mlp_create(int n_layers, const int* sizes, uint64_t seed,
                    dos_mlp_t* out);
 void dos_mlp_destroy(dos_mlp_t net);
-/* Number of float32 parameters [host output]. */
+/* Project addition (learned reconstruction). Number of float32 parameters
+ * [host output]. */
 int dos_mlp_param_count(dos_mlp_t net, int64_t* count);
-/* Copy the parameters to / from a device buffer of dos_mlp_param_count
- * floats.  set_params also resets Adam's moments and step count. */
+/* Project addition (learned reconstruction). Copy the parameters to / from a
+ * device buffer of dos_mlp_param_count floats.  set_params also resets Adam's
+ * moments and step count. */
 int dos_mlp_get_params(dos_mlp_t net, float* out, void* stream);
 int dos_mlp_set_params(dos_mlp_t net, const float* in, void* stream);
 
-/* probs[rows][sizes[n_layers]] = softmax(network(x)), x[rows][sizes[0]].
- * Errors: DOS_EINVAL (rows < 1, null pointer), DOS_ENOMEM. */
+/* Project addition (learned reconstruction). probs[rows][sizes[n_layers]] =
+ * softmax(network(x)), x[rows][sizes[0]]. Errors: DOS_EINVAL (rows < 1, null
+ * pointer), DOS_ENOMEM. */
 int dos_mlp_forward(dos_mlp_t net, const float* x, int rows, float* probs,
                     void* stream);
 
-/* Cross-entropy -(1/rows) sum t log p of targets t[rows][out] (rows of t
- * sum to 1) and its gradient.  loss [device] float[1] or NULL; grad [device]
- * float[param_count] or NULL (the gradient is kept on the handle). */
+/* Project addition (learned reconstruction). Cross-entropy -(1/rows) sum t log
+ * p of targets t[rows][out] (rows of t sum to 1) and its gradient.  loss
+ * [device] float[1] or NULL; grad [device] float[param_count] or NULL (the
+ * gradient is kept on the handle). */
 int dos_mlp_loss_grad(dos_mlp_t net, const float* x, const float* t, int rows,
                       float* loss, float* grad, void* stream);
 
-/* One Adam step on the minibatch rows idx[0..rows) of (x, t) (idx [device]
- * int32, NULL = the first `rows` rows) with learning rate lr > 0; loss
- * [device] float[1] or NULL receives the minibatch loss before the step. */
+/* Project addition (learned reconstruction). One Adam step on the minibatch
+ * rows idx[0..rows) of (x, t) (idx [device] int32, NULL = the first `rows`
+ * rows) with learning rate lr > 0; loss [device] float[1] or NULL receives the
+ * minibatch loss before the step. */
 int dos_mlp_train_step(dos_mlp_t net, const float* x, const float* t,
                        const int32_t* idx, int rows, float lr, float* loss,
                        void* stream);
 
-/* Feature rows for the network, one per graph g < n_graphs:
+/* Project addition (learned reconstruction; inputs from §3.1, §4.1).
+ * Feature rows for the network, one per graph g < n_graphs:
  *   x_out[g] = [ n_bins * hist[g * n_bins + b] for b < n_bins,
  *                d[g * ld_d + m] for 1 <= m < K ]      (n_bins + K - 1 floats)
  * hist [device] double (a Jackson histogram, e.g. dos_density_batched),
@@ -605,7 +624,8 @@ int dos_hist_assemble(const float* probs, int n_bins, int64_t rows,
                       double scale, const double* spikes, int n_spikes,
                       double* hist_out, void* stream);
 
-/* Training targets: t_out[g][b] = max(hist[g][b], 0) / sum_b max(hist[g][b], 0)
+/* Project addition (learned reconstruction; §4.1 histograms). Training
+ * targets: t_out[g][b] = max(hist[g][b], 0) / sum_b max(hist[g][b], 0)
  * (uniform if that sum is 0).  Errors: DOS_EINVAL. */
 int dos_hist_normalize(const double* hist, int n_bins, int64_t n_graphs,
                        float* t_out, void* stream);
@@ -614,35 +634,40 @@ int dos_hist_normalize(const double* hist, int n_bins, int64_t n_graphs,
  * Tuning and instrumentation (not part of the method).
  * --------------------------------------------------------------------- */
 
-/* Planner override (tuning): force the probe tile width t (a power of two in
- * [4, 64] that is a multiple of 16 bytes of the storage type; 0 = automatic)
- * and the resident CTAs per SM of the light-row step kernel (0 = as many as
- * fit) of later dos_moments / ldos_moments calls.  Process-wide.
- * Errors: DOS_EINVAL. */
+/* Tuning of the §3.1 step, not in the paper. Planner override (tuning): force
+ * the probe tile width t (a power of two in [4, 64] that is a multiple of 16
+ * bytes of the storage type; 0 = automatic) and the resident CTAs per SM of
+ * the light-row step kernel (0 = as many as fit) of later dos_moments /
+ * ldos_moments calls.  Process-wide. Errors: DOS_EINVAL. */
 int dos_set_plan(int tile_width, int ctas_per_sm);
 
-/* The plan dos_moments would use for (g, Nz, prec): tile width t, light-row
- * CTAs per SM, number of tiles T = ceil(Nz / t) and the number of CTAs of the
- * light-row kernel [host outputs; any may be NULL]. */
+/* Tuning of the §3.1 step, not in the paper. The plan dos_moments would use
+ * for (g, Nz, prec): tile width t, light-row CTAs per SM, number of tiles T =
+ * ceil(Nz / t) and the number of CTAs of the light-row kernel [host outputs;
+ * any may be NULL]. */
 int dos_get_plan(dos_graph_t g, int Nz, int prec, int* tile_width,
                  int* ctas_per_sm, int* tiles, int* grid_x);
 
-/* Status of the device-side error word of the current device: the step
- * kernels' waits on their shared-memory pipeline are bounded (2 s); if one
- * gives up, the kernel records it, leaves, and the affected call's moments are
- * NaN.  Synchronises `stream`, returns the word in *status (0 = none; may be
- * NULL) and clears it.  Returns DOS_ETIMEOUT if a wait gave up, else DOS_OK. */
+/* Failure detection, not in the paper. Status of the device-side error word of
+ * the current device: the step kernels' waits on their shared-memory pipeline
+ * are bounded (2 s); if one gives up, the kernel records it, leaves, and the
+ * affected call's moments are NaN.  Synchronises `stream`, returns the word in
+ * *status (0 = none; may be NULL) and clears it.  Returns DOS_ETIMEOUT if a
+ * wait gave up, else DOS_OK. */
 int dos_device_status(void* stream, int* status);
 
-/* Number of kernels this library has launched since load (all threads). */
+/* Instrumentation, not in the paper. Number of kernels this library has
+ * launched since load (all threads). */
 int64_t dos_launch_count(void);
 
-/* Enable (1) / disable (0) CUDA-event timing of the Chebyshev step kernels.
- * While enabled, every step launch is bracketed by events on its own stream. */
+/* Instrumentation, not in the paper. Enable (1) / disable (0) CUDA-event
+ * timing of the Chebyshev step kernels. While enabled, every step launch is
+ * bracketed by events on its own stream. */
 int dos_profile_enable(int on);
 
-/* Total device time (ms) and launch count of the step kernels recorded since
- * the last reset; synchronises on the recorded events.  reset != 0 clears. */
+/* Instrumentation, not in the paper. Total device time (ms) and launch count
+ * of the step kernels recorded since the last reset; synchronises on the
+ * recorded events.  reset != 0 clears. */
 int dos_profile_read(double* total_ms, int64_t* launches, int reset);
 
 #ifdef __cplusplus

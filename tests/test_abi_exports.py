@@ -24,6 +24,20 @@ def test_header_declares_the_boundary():
         assert must in names
 
 
+def test_every_declaration_cites_its_passage():
+    """Each declaration's comment (or the comment of the section it opens a
+    group in) names the passage that defines the operation, or says that it
+    is not in the paper (instrumentation, tuning, project additions)."""
+    import os
+    import re
+
+    text = open(os.path.join(os.path.dirname(__file__), "..", "include", "netdos.h")).read()
+    marks = ("§", "Eq.", "Algorithm", "Fig.", "not in the paper", "project addition", "Project addition")
+    decl = re.compile(r"/\*((?:(?!\*/).)*)\*/\s*\n(?:int|void|const char\*|int64_t|uint64_t)\s+(\w+)\(", re.S)
+    missing = [name for com, name in decl.findall(text) if not any(m in com for m in marks)]
+    assert not missing, missing
+
+
 def test_library_exports_every_declared_symbol(libpath):
     assert libpath == LIB
     handle = ctypes.CDLL(libpath)
