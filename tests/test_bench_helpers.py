@@ -1,0 +1,35 @@
+"""The bench's own accuracy references (scipy/numpy, no oracle on the bench
+path) checked here against the oracle on small graphs (CPU only)."""
+import os
+import sys
+
+import numpy as np
+
+import oracle
+import synthgraphs as sg
+
+sys.path.insert(0, os.path.join(os.path.dirname(__file__), ".."))
+import bench  # noqa: E402
+
+
+def test_adjacency_matches_the_oracle_csr():
+    src, dst, n = sg.random_geometric(800, 0.05, 3)
+    # duplicates, a self-loop and isolated nodes on top
+    src = np.concatenate([src, src[:50], [7]])
+    dst = np.concatenate([dst, dst[:50], [7]])
+    a = bench._adjacency(src, dst, n + 5)
+    ref = oracle.build_csr(src, dst, n + 5)
+    assert a.shape == (ref.n, ref.n)
+    assert np.array_equal(a.indptr, ref.row_ptr)
+    assert np.array_equal(a.indices, ref.col)
+    assert np.all(a.data == 1.0)
+
+
+def test_unit_probe_diagonal_is_the_exact_ldos():
+    src, dst, n = sg.erdos_renyi(300, 0.03, 5)
+    a = bench._adjacency(src, dst, n)
+    ref = oracle.build_csr(src, dst, n)
+    lam, q = oracle.exact_eigs(ref)
+    sample = np.array([0, 3, 77, ref.n - 1])
+    got = bench._unit_probe_diagonal(a, sample, 25)
+    assert np.abs(got - oracle.exact_ldos(lam, q, 25)[sample]).max() <= 1e-12
