@@ -1136,12 +1136,35 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def side_kernels(seed: int = 1):
+    """A short sequence for profiling the widening rows' kernels under ncu:
+    four Lanczos steps (Nz = 16) and LDOS of A (M = 60, Nz = 16) with three
+    contractions on the 1.1M-node workload.  Prints one line; no timing."""
+    import torch
+
+    import paper_1905_09758_gb300 as nd
+
+    src, dst, n = make_edges(WORKLOAD["seed"])
+    g = nd.dos_build_csr(torch.from_numpy(src).cuda(), torch.from_numpy(dst).cuda(), n)
+    nd.dos_lanczos(g, 4, 16, seed)
+    iv = (-122.352, 255.371)  # the Lanczos Ritz interval of A on this graph
+    cm, _, _ = nd.ldos_moments_op(g, "adjacency", 60, 16, seed, interval=iv)
+    coef = nd.dos_fn_coeffs("exp", 1.0 / iv[1], iv, 60)
+    out = None
+    for _ in range(3):
+        out = nd.dos_fn_diag(cm, coef)
+    torch.cuda.synchronize()
+    print("ok", float(out.max()))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--side-kernels", action="store_true",
+                    help="run only a short Lanczos / LDOS-of-A / contraction sequence (for ncu) and exit")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-time-to-l1", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
@@ -1159,7 +1182,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         ap.error("--warmup must be >= 3")
-    if args.impl == "reference":
+    if args.side_kernels:
+        side_kernels()
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
