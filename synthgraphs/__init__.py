@@ -220,6 +220,37 @@ def barabasi_albert(n: int, m: int, seed: int):
     return src, dst, n
 
 
+def watts_strogatz(n: int, k: int, p: float, seed: int):
+    """Watts-Strogatz small world: the ring lattice joining each node to its k
+    nearest neighbours on each side, then each lattice edge (i, i + j) has its
+    far end moved, with probability p, to a uniformly drawn node that is
+    neither i nor already a neighbour of i (numpy PCG64).  Returns unique pairs."""
+    n, k = int(n), int(k)
+    if not 1 <= k < n // 2:
+        raise ValueError("need 1 <= k < n / 2")
+    rng = _rng(seed)
+    nbr = [set() for _ in range(n)]
+    for i in range(n):
+        for j in range(1, k + 1):
+            nbr[i].add((i + j) % n)
+            nbr[(i + j) % n].add(i)
+    for j in range(1, k + 1):
+        for i in range(n):
+            v = (i + j) % n
+            if v not in nbr[i] or rng.random() >= p:
+                continue
+            w = int(rng.integers(n))
+            if w == i or w in nbr[i]:
+                continue  # no move when the draw hits i or a neighbour
+            nbr[i].discard(v)
+            nbr[v].discard(i)
+            nbr[i].add(w)
+            nbr[w].add(i)
+    src = np.array([i for i in range(n) for v in nbr[i] if i < v], np.int64)
+    dst = np.array([v for i in range(n) for v in nbr[i] if i < v], np.int64)
+    return src, dst, n
+
+
 def add_twin_leaves(src, dst, n: int, n_hosts: int, seed: int):
     """Hang two new degree-1 leaves on each of ``n_hosts`` hosts.
 

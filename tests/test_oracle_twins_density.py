@@ -386,3 +386,33 @@ def test_all_motifs_together():
     lam_r = np.linalg.eigvalsh(p.T @ h @ p)
     assert lam_r.size == g.n - removed
     assert np.allclose(np.sort(lam_r), np.sort(_remove_eigs(lam, spikes)), atol=1e-9)
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_motif_filters_on_watts_strogatz_and_ba_tree(seed):
+    """The synthetic models of the paper's small-world and BA examples (§5.3):
+    Watts-Strogatz with twin leaves and triangle twins, and the BA tree (m = 1),
+    where pendant twins abound.  All relations together keep the projection
+    exact: P P^T commutes with H, spec(P^T H P) is spec(H) without the spikes."""
+    for src, dst, n in (sg.add_triangle_twins(*sg.add_twin_leaves(*sg.watts_strogatz(300, 2, 0.3, seed), 10, seed),
+                                              10, seed + 1),
+                        sg.barabasi_albert(300, 1, seed)):
+        g = oracle.build_csr(src, dst, n)
+        cid, removed, spikes = oracle.motif_classes(g, pendant_twins=True, parallel_paths=True)
+        assert removed > 0
+        lam, _ = oracle.exact_eigs(g)
+        p = _p_matrix(cid)
+        h = oracle.dense_h(g)
+        assert np.allclose(p @ p.T @ h, h @ p @ p.T, atol=1e-12)
+        lam_r = np.linalg.eigvalsh(p.T @ h @ p)
+        assert lam_r.size == g.n - removed
+        assert np.allclose(np.sort(lam_r), np.sort(_remove_eigs(lam, spikes)), atol=1e-9)
+
+
+def test_watts_strogatz_generator():
+    src, dst, n = sg.watts_strogatz(200, 3, 0.0, 5)  # the lattice itself
+    deg = np.bincount(np.concatenate([src, dst]), minlength=n)
+    assert np.all(deg == 6) and src.size == 600
+    src, dst, n = sg.watts_strogatz(200, 3, 0.5, 5)  # rewiring keeps the edge count, no loops
+    assert src.size == 600 and np.all(src != dst) and np.all(src < dst)
+    assert len(set(zip(src.tolist(), dst.tolist()))) == 600
