@@ -47,6 +47,9 @@ Parity status of each function (what pins it, see ``tests/test_oracle_*.py``):
   ``kpm_operator``                 -- pinned by closed-form spectra of A and L (K_n,
                                       C_n, stars), Gershgorin containment, and identity
                                       probes giving the exact traces.
+* ``motif_spikes``                 -- pinned by K_n, star and P5 closed forms for A and L, and by
+                                      spec(X) = spec(P^T X P) plus the spikes for all four
+                                      operators on a graph with every motif.
 * ``ritz_bounds``, ``spectral_interval``, ``lanczos`` on A and L
                                    -- pinned by K_n and star closed forms (the Krylov
                                       space is exhausted: the interval is the exact

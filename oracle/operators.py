@@ -32,10 +32,11 @@ import scipy.sparse as sp
 from scipy.linalg import eigh_tridiagonal
 
 from .gql import lanczos
-from .kpm import Csr, cheb_values, h_sparse
+from .kpm import (Csr, cheb_values, closed_twin_classes, h_sparse, motif_classes, parallel_path_classes,
+                  pendant_twin_classes, twin_classes)
 
 __all__ = ["operator_matrix", "gershgorin_interval", "exact_operator_moments", "kpm_operator",
-           "ritz_bounds", "spectral_interval"]
+           "ritz_bounds", "spectral_interval", "motif_spikes"]
 
 
 def operator_matrix(g: Csr, op: str) -> sp.csr_matrix:
@@ -126,3 +127,60 @@ def spectral_interval(g: Csr, op: str, z: np.ndarray, m_steps: int, pad: float =
     if op == "normalized_adjacency":
         hi = 1.0
     return max(lo, g_lo), min(hi, g_hi)
+
+
+def motif_spikes(g: Csr, op: str, open_twins: bool = True, closed_twins: bool = True, pendant_twins: bool = False,
+                 parallel_paths: bool = False):
+    """Eigenvalues of X that the motif classes of ``motif_classes`` take out
+    (§3.4's motifs on §2.1's operators), as sorted (lambda, count) pairs.
+
+    Members of a class share their degree, so the within-class difference
+    vectors span the same invariant subspace of H, A and D - A; only the
+    eigenvalue differs.  For a class of c members of degree d (c - 1
+    eigenvalues each, two per pair for the two-class motifs):
+      open twins        H 0             A 0     D - A  d
+      closed twins      H -1/d          A -1    D - A  d + 1
+      pendant twins     H +-1/sqrt(d)   A +-1   D - A  ((d + 1) +- sqrt((d - 1)^2 + 4)) / 2
+      parallel paths    H +-1/2         A +-1   D - A  1, 3
+    (on a node / leaf pair the operators act as [[0, 1], [1, 0]] (A) and
+    [[d, -1], [-1, 1]] (D - A); on a path pair a - b as [[0, 1], [1, 0]] and
+    [[2, -1], [-1, 2]]).  op "normalized_adjacency" gives motif_classes' own
+    spikes, "normalized_laplacian" 1 - those."""
+    if op in ("normalized_adjacency", "normalized_laplacian"):
+        _, _, sp = motif_classes(g, open_twins, closed_twins, pendant_twins, parallel_paths)
+        if op == "normalized_laplacian":
+            sp = sorted((1.0 - x, c) for x, c in sp)
+        return sp
+    if op not in ("adjacency", "laplacian"):
+        raise ValueError(op)
+    lap = op == "laplacian"
+    deg = np.diff(g.row_ptr)
+    out: dict[float, int] = {}
+
+    def add(x, c):
+        out[float(x)] = out.get(float(x), 0) + int(c)
+
+    if open_twins:
+        oc, _ = twin_classes(g)
+        for i in np.nonzero(oc != np.arange(g.n))[0]:
+            add(float(deg[i]) if lap else 0.0, 1)
+    if closed_twins:
+        _, _, per_d = closed_twin_classes(g)
+        for d, c in per_d.items():
+            add(d + 1.0 if lap else -1.0, c)
+    if pendant_twins:
+        _, _, pairs = pendant_twin_classes(g)
+        for d, c in pairs.items():
+            if lap:
+                r = np.sqrt((d - 1.0) ** 2 + 4.0)
+                add((d + 1.0 - r) / 2.0, c)
+                add((d + 1.0 + r) / 2.0, c)
+            else:
+                add(-1.0, c)
+                add(1.0, c)
+    if parallel_paths:
+        _, _, pairs = parallel_path_classes(g)
+        if pairs:
+            add(1.0 if lap else -1.0, pairs)
+            add(3.0 if lap else 1.0, pairs)
+    return sorted(out.items())

@@ -175,3 +175,67 @@ def test_spectral_interval_is_tight_on_hub_graphs():
     ga, gb = oracle.gershgorin_interval(g, "laplacian")
     a, b = oracle.spectral_interval(g, "laplacian", z, 30, bound="ritz")
     assert b - a <= 1.03 * (lam.max() - lam.min()) and b - a <= 0.55 * (gb - ga)
+
+
+def _p_matrix(class_id):
+    ids = np.unique(class_id)
+    p = np.zeros((class_id.size, ids.size))
+    for k, c in enumerate(ids):
+        mem = class_id == c
+        p[mem, k] = 1.0 / np.sqrt(mem.sum())
+    return p
+
+
+def _without(lam, spikes, tol=1e-9):
+    keep = np.ones(lam.size, bool)
+    for x, c in spikes:
+        hit = np.nonzero(np.abs(lam - x) < tol)[0]
+        assert hit.size >= c, (x, c, hit.size)
+        keep[hit[:c]] = False
+    return lam[keep]
+
+
+def test_motif_spikes_closed_forms():
+    n, s = 7, 5
+    kn, star = oracle.build_csr(*sg.complete(n)), oracle.build_csr(*sg.star(s))
+    # K_n: closed twins of degree n - 1; spec A = {n - 1, -1 x (n - 1)}, spec L = {0, n x (n - 1)}
+    assert oracle.motif_spikes(kn, "adjacency") == [(-1.0, n - 1)]
+    assert oracle.motif_spikes(kn, "laplacian") == [(float(n), n - 1)]
+    # star: open twins of degree 1; A: 0 x (s - 1), L: 1 x (s - 1)
+    assert oracle.motif_spikes(star, "adjacency") == [(0.0, s - 1)]
+    assert oracle.motif_spikes(star, "laplacian") == [(1.0, s - 1)]
+    # P5 (pendant twins of degree 2): spec A = 2 cos(pi k / 6) holds +-1, spec L = 2 - 2 cos(pi k / 5)
+    # holds (3 +- sqrt 5) / 2
+    p5 = oracle.build_csr(*sg.path(5))
+    sa = oracle.motif_spikes(p5, "adjacency", open_twins=False, closed_twins=False, pendant_twins=True)
+    sl = oracle.motif_spikes(p5, "laplacian", open_twins=False, closed_twins=False, pendant_twins=True)
+    assert sa == [(-1.0, 1), (1.0, 1)]
+    assert np.allclose([x for x, _ in sl], [(3 - np.sqrt(5)) / 2, (3 + np.sqrt(5)) / 2], atol=1e-14)
+    lam_l = np.sort(2 - 2 * np.cos(np.pi * np.arange(5) / 5))
+    assert np.allclose(np.sort(_spec(p5, "laplacian")), lam_l, atol=1e-12)
+
+
+@pytest.mark.parametrize("op", ["adjacency", "laplacian", "normalized_adjacency", "normalized_laplacian"])
+def test_motif_spikes_complete_the_projected_spectrum(op):
+    """All four motifs at once: the class-mean projection commutes with X
+    and spec(X) = spec(P^T X P) plus the spikes, for every operator."""
+    src, dst, n = sg.chung_lu(400, 2.4, 6.0, 91)
+    src, dst, n = sg.add_twin_leaves(src, dst, n, 8, 92)
+    src, dst, n = sg.add_triangle_twins(src, dst, n, 8, 93)
+    src, dst, n = sg.add_pendant_twins(src, dst, n, 4, 3, 94)
+    src, dst, n = sg.add_parallel_paths(src, dst, n, 4, 3, 95)
+    g = oracle.build_csr(src, dst, n)
+    cid, removed, _ = oracle.motif_classes(g, pendant_twins=True, parallel_paths=True)
+    spikes = oracle.motif_spikes(g, op, pendant_twins=True, parallel_paths=True)
+    assert sum(c for _, c in spikes) == removed
+    if op in ("adjacency", "laplacian"):
+        x = oracle.operator_matrix(g, op).toarray()
+    else:
+        x = oracle.dense_h(g)
+        if op == "normalized_laplacian":
+            x = np.eye(g.n) - x
+    p = _p_matrix(cid)
+    assert np.allclose(p @ p.T @ x, x @ p @ p.T, atol=1e-12)
+    lam = np.linalg.eigvalsh(x)
+    lam_r = np.linalg.eigvalsh(p.T @ x @ p)
+    assert np.allclose(np.sort(lam_r), np.sort(_without(lam, spikes)), atol=1e-8)
