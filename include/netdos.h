@@ -243,11 +243,36 @@ int dos_moments_op(dos_graph_t g, int op, double lo, double hi, int M, int Nz,
  *          z_kj (T_m(H) z_j)_k, the same estimator as dos_moments without a
  *          filter, from the direct recurrence.
  * Probes are never projected here (a projected probe would estimate the
- * diagonal of P P^T T_m(H) P P^T instead).  Scratch as for dos_moments.
+ * diagonal of P P^T T_m(H) P P^T instead).  Scratch as for dos_moments, plus,
+ * when the plan has several probe tiles, a buffer of up to 32 moments x tiles
+ * x N floats (at most 256 MB) in which each tile's contribution is stored and
+ * then summed in a fixed order, so C_out is bitwise reproducible.
  * Errors: DOS_EINVAL, DOS_ENOMEM, DOS_ECUDA.
  */
 int ldos_moments(dos_graph_t g, int M, int Nz, uint64_t seed, int prec,
                  float* C_out, double* d_out, void* stream);
+
+/* Layouts of the N x M LDOS matrix (ldos_moments_ex). */
+enum dos_layout {
+  DOS_MOMENT_MAJOR = 0, /* C_out[m * N + k]: one contiguous row per moment */
+  DOS_NODE_MAJOR = 1    /* C_out[k * M + m]: N x M row-major, one row per node */
+};
+
+/*
+ * ldos_moments_ex -- ldos_moments with a choice of output layout.
+ * Paper: §2.2 Eq. (2), Eq. (10), Eq. (12), as ldos_moments; Algorithm 1's
+ * output is the N x M matrix of per-node moments, which DOS_NODE_MAJOR gives
+ * row-major.  The steps produce one moment for all nodes at a time, so with
+ * DOS_NODE_MAJOR (or with several probe tiles) they write a scratch of up to
+ * 32 moments and a fold kernel sums the tiles in a fixed order and writes
+ * the chunk in the layout (through a shared-memory transpose for
+ * DOS_NODE_MAJOR).  Values are identical in both layouts.
+ *   layout  DOS_MOMENT_MAJOR or DOS_NODE_MAJOR;  C_out [device] float[M * N].
+ *   Other arguments, scratch and errors as ldos_moments (DOS_EINVAL for an
+ *   unknown layout).
+ */
+int ldos_moments_ex(dos_graph_t g, int M, int Nz, uint64_t seed, int prec,
+                    int layout, float* C_out, double* d_out, void* stream);
 
 /*
  * ldos_moments_op -- ldos_moments on another operator X (§2.1), mapped by
@@ -261,35 +286,66 @@ int ldos_moments_op(dos_graph_t g, int op, double lo, double hi, int M, int Nz,
                     uint64_t seed, float* C_out, double* d_out,
                     double* interval_out, void* stream);
 
+/* Flags of dos_density / dos_density_weights. */
+enum dos_density_flags {
+  DOS_DENSITY_COUNT_ISOLATED = 1 /* nodes without edges count as eigenvalue 0 */
+};
+
 /*
- * dos_density -- damped spectral histogram from moments.
+ * dos_density -- damped spectral histogram of a graph from its moments.
  * Paper: §2.2 (spectral histogram on equal bins), Eq. (7)-(8) (dual Chebyshev
  * basis, expansion of the DOS), §4.1 (Jackson damping; the factors are the
  * Jackson kernel of the KPM literature for M terms:
- * g_m = [(M-m+1) cos(pi m/(M+1)) + sin(pi m/(M+1)) cot(pi/(M+1))]/(M+1)).
- *   d        [device] double[M] moments d_0 .. d_{M-1}.
- *   n_bins   B >= 1 equal bins over [-1, 1].
+ * g_m = [(M-m+1) cos(pi m/(M+1)) + sin(pi m/(M+1)) cot(pi/(M+1))]/(M+1)),
+ * §3.4 (the filtered density: the reduced operator's series weighted by
+ * r / N plus the removed eigenvalues as point masses).
+ *   d        [device] double[M] moments d_0 .. d_{M-1} (of P^T H P when f is
+ *            given, i.e. dos_moments with that filter).
+ *   n_bins   B >= 1 equal bins over [-1, 1].  M <= 2^20.
  *   kernel   DOS_KERNEL_JACKSON or DOS_KERNEL_NONE (g_m = 1).
- *   scale    multiplies the series part (use r / N_total with a filter and
- *            N / N_total when isolated nodes are counted; 1.0 otherwise).
- *   spikes   [host] double[2 * n_spikes] pairs (lambda, mass) added as point
- *            masses (a point on an interior bin edge splits evenly between
- *            the two bins; +-1 go to the end bins); NULL if n_spikes == 0.
- *            n_spikes <= 64.  M <= 2^20.
+ *   g, f     NULL, NULL: the plain series (scale 1, no point masses).
+ *            Otherwise the whole graph's density: g the graph (may be NULL
+ *            when f is given: f's graph), f a filter of g or NULL.  With
+ *            N_total = N + n_isolated (flag DOS_DENSITY_COUNT_ISOLATED) or N,
+ *            r = N - removed (N without a filter): the series part is scaled
+ *            by r / N_total and every eigenvalue the filter removed (and the
+ *            isolated nodes, at 0, when counted) is a point mass count /
+ *            N_total (dos_density_weights returns these numbers).
+ *   flags    0 or DOS_DENSITY_COUNT_ISOLATED.
  *   hist_out [device] double[B]: bin b gets
  *            scale * (g_0 d_0 I_0b + 2 sum_{m>=1} g_m d_m I_mb) + spikes,
- *            I_mb = integral over bin b of T_m(x) / (pi sqrt(1 - x^2)) dx.
- * Stream-ordered.  Errors: DOS_EINVAL.
+ *            I_mb = integral over bin b of T_m(x) / (pi sqrt(1 - x^2)) dx; a
+ *            point mass within 1e-9 of an interior bin edge splits evenly
+ *            between the two bins, +-1 go to the end bins.
+ * Stream-ordered.  Errors: DOS_EINVAL (null pointer, sizes, a filter of
+ * another graph, more than 64 distinct point masses).
  */
-int dos_density(const double* d, int M, int n_bins, int kernel, double scale,
-                const double* spikes, int n_spikes, double* hist_out,
-                void* stream);
+int dos_density(const double* d, int M, int n_bins, int kernel,
+                dos_graph_t g, dos_filter_t f, uint32_t flags,
+                double* hist_out, void* stream);
+
+/* §3.4 (filtered density weights), §2.2. The numbers dos_density uses for
+ * (g, f, flags) [host outputs, any may be NULL]: scale_out = r / N_total, and
+ * up to `capacity` pairs (lambda, mass) in spikes_out[2 * capacity] in
+ * ascending lambda, mass = count / N_total; *n_spikes the number of pairs.
+ * g may be NULL when f is given.  Errors: DOS_EINVAL. */
+int dos_density_weights(dos_graph_t g, dos_filter_t f, uint32_t flags,
+                        double* scale_out, double* spikes_out, int capacity,
+                        int* n_spikes);
+
+/* §2.2, Eq. (7)-(8), §4.1 with an explicit weight: dos_density's series times
+ * `scale` plus the point masses (lambda, mass) of spikes [host double[2 *
+ * n_spikes], n_spikes <= 64, NULL if 0], placed as in dos_density.
+ * Stream-ordered.  Errors: DOS_EINVAL. */
+int dos_density_raw(const double* d, int M, int n_bins, int kernel,
+                    double scale, const double* spikes, int n_spikes,
+                    double* hist_out, void* stream);
 
 /*
- * §3.1, Eq. (6), (9), (11); the allocation-free form is a project addition.
+ * A project addition (not in the paper): the paper has no counterpart to this
+ * entry point; the computation it runs is dos_moments'.
  * dos_moments_noalloc -- dos_moments (FP32 storage, no filter) for callers
- * that cannot allocate device memory.  The paper has no counterpart; this is
- * a deployment variant of the same computation.
+ * that cannot allocate device memory.
  * Who needs it: a caller whose framework allocator already holds nearly all
  * device memory (a fresh cudaMalloc would fail or force the framework to
  * drop its cache), or a latency-bound caller for which cudaMalloc/cudaFree,
@@ -298,8 +354,9 @@ int dos_density(const double* d, int M, int n_bins, int kernel, double scale,
  * moment partials) lives in one static device array of 16 MiB that every GPU
  * loading the library holds until the process exits.
  *   g, M, Nz, seed, d_out, stream: as for dos_moments (d_out [device]
- *   double[M], caller-allocated).  Results equal dos_moments' (same kernels,
- *   same plan, same reduction order).
+ *   double[M], caller-allocated).  Results are bitwise equal to dos_moments'
+ *   with f = NULL and prec = DOS_FP32: the same kernels, plan and fixed
+ *   reduction order on a different scratch address.
  * The first call on a device looks up the array's device address (once per
  * device, with that device current); make that first call before any stream
  * capture.  All calls share the array and its contents persist between

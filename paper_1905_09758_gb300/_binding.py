@@ -19,6 +19,7 @@ HEADER_PATH = os.path.join(os.path.dirname(_PKG), "include", "netdos.h")
 DOS_OK, DOS_EINVAL, DOS_ENOMEM, DOS_ECUDA, DOS_ETIMEOUT, DOS_EOVERFLOW = range(6)
 PREC = {"fp32": 0, "bf16": 1, "fp16": 2}
 KERNEL = {"none": 0, "jackson": 1}
+LAYOUT = {"moment": 0, "node": 1}
 DOS_INPUT_HOST = 1
 MOTIF = {"open": 1, "closed": 2, "pendant": 4, "parallel": 8}
 OPERATOR = {"normalized_adjacency": 0, "adjacency": 1, "laplacian": 2, "normalized_laplacian": 3}
@@ -60,8 +61,11 @@ _SIGNATURES = {
     "dos_filter_destroy": ([_vp], None),
     "dos_moments": ([_vp, _vp, _i32, _i32, _u64, _i32, _vp, _vp], _i32),
     "ldos_moments": ([_vp, _i32, _i32, _u64, _i32, _vp, _vp, _vp], _i32),
+    "ldos_moments_ex": ([_vp, _i32, _i32, _u64, _i32, _i32, _vp, _vp, _vp], _i32),
     "dos_moments_noalloc": ([_vp, _i32, _i32, _u64, _vp, _vp], _i32),
-    "dos_density": ([_vp, _i32, _i32, _i32, _dbl, _vp, _i32, _vp, _vp], _i32),
+    "dos_density": ([_vp, _i32, _i32, _i32, _vp, _vp, _u32, _vp, _vp], _i32),
+    "dos_density_weights": ([_vp, _vp, _u32, C.POINTER(C.c_double), _vp, _i32, _PI], _i32),
+    "dos_density_raw": ([_vp, _i32, _i32, _i32, _dbl, _vp, _i32, _vp, _vp], _i32),
     "dos_device_status": ([_vp, C.POINTER(C.c_int)], _i32),
     "dos_launch_count": ([], _i64),
     "dos_profile_enable": ([_i32], _i32),
@@ -377,35 +381,69 @@ def dos_moments_noalloc(g: Graph, M: int, Nz: int, seed: int, d_out: torch.Tenso
 
 
 def ldos_moments(g: Graph, M: int, Nz: int, seed: int, prec: str = "fp32", C_out: torch.Tensor | None = None,
-                 d_out: torch.Tensor | None = None, want_d: bool = True, stream=None):
-    """Per-node moments C (float32, shape (M, N): C[m, k] = moment m of compact node k) and,
-    if want_d, the DOS moments from the same recurrence."""
+                 d_out: torch.Tensor | None = None, want_d: bool = True, layout: str = "moment", stream=None):
+    """Per-node moments C and, if want_d, the DOS moments from the same
+    recurrence.  layout "moment": C has shape (M, N), C[m, k] = moment m of
+    compact node k; layout "node": shape (N, M), row k = node k's moments."""
     n = g.n
     dev = torch.device("cuda", torch.cuda.current_device())
+    if layout not in LAYOUT:
+        raise ValueError(f"layout must be one of {sorted(LAYOUT)}")
     if C_out is None:
-        C_out = torch.empty((M, n), dtype=torch.float32, device=dev)
+        C_out = torch.empty((M, n) if layout == "moment" else (n, M), dtype=torch.float32, device=dev)
     _need_cuda(C_out, torch.float32, "C_out", M * n)
     if d_out is None and want_d:
         d_out = torch.empty(M, dtype=torch.float64, device=dev)
     if d_out is not None:
         _need_cuda(d_out, torch.float64, "d_out", M)
-    _check(lib().ldos_moments(g.handle, int(M), int(Nz), int(seed) & (2**64 - 1), PREC[prec], _ptr(C_out),
-                              _ptr(d_out), _stream(stream)))
+    _check(lib().ldos_moments_ex(g.handle, int(M), int(Nz), int(seed) & (2**64 - 1), PREC[prec], LAYOUT[layout],
+                                 _ptr(C_out), _ptr(d_out), _stream(stream)))
     return C_out, d_out
 
 
-def dos_density(d: torch.Tensor, n_bins: int, kernel: str = "jackson", scale: float = 1.0, spikes=(),
-                hist_out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+DOS_DENSITY_COUNT_ISOLATED = 1
+
+
+def dos_density(d: torch.Tensor, n_bins: int, kernel: str = "jackson", g: Graph | None = None,
+                filter: Filter | None = None, count_isolated: bool = True, hist_out: torch.Tensor | None = None,
+                stream=None) -> torch.Tensor:
     """Damped histogram over n_bins equal bins of [-1, 1] (float64 CUDA tensor).
-    spikes: iterable of (lambda, mass) point masses."""
+    Without g and filter: the plain series of d.  With them: the whole graph's
+    density (the library weights the series by r / N_total and adds the
+    removed eigenvalues and, if count_isolated, the isolated nodes as point
+    masses)."""
+    _need_cuda(d, torch.float64, "d")
+    if hist_out is None:
+        hist_out = torch.empty(n_bins, dtype=torch.float64, device=d.device)
+    _need_cuda(hist_out, torch.float64, "hist_out", n_bins)
+    flags = DOS_DENSITY_COUNT_ISOLATED if count_isolated else 0
+    _check(lib().dos_density(_ptr(d), d.numel(), int(n_bins), KERNEL[kernel], None if g is None else g.handle,
+                             None if filter is None else filter.handle, flags, _ptr(hist_out), _stream(stream)))
+    return hist_out
+
+
+def dos_density_weights(g: Graph | None, filter: Filter | None = None, count_isolated: bool = True):
+    """(scale, [(lambda, mass)]) that dos_density applies for (g, filter)."""
+    flags = DOS_DENSITY_COUNT_ISOLATED if count_isolated else 0
+    scale, n = C.c_double(), C.c_int()
+    hg, hf = (None if g is None else g.handle), (None if filter is None else filter.handle)
+    _check(lib().dos_density_weights(hg, hf, flags, C.byref(scale), None, 0, C.byref(n)))
+    buf = (C.c_double * max(1, 2 * n.value))()
+    _check(lib().dos_density_weights(hg, hf, flags, C.byref(scale), buf, n.value, C.byref(n)))
+    return scale.value, [(buf[2 * k], buf[2 * k + 1]) for k in range(n.value)]
+
+
+def dos_density_raw(d: torch.Tensor, n_bins: int, kernel: str = "jackson", scale: float = 1.0, spikes=(),
+                    hist_out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """dos_density with an explicit series weight and point masses (lambda, mass)."""
     _need_cuda(d, torch.float64, "d")
     if hist_out is None:
         hist_out = torch.empty(n_bins, dtype=torch.float64, device=d.device)
     _need_cuda(hist_out, torch.float64, "hist_out", n_bins)
     sp = [float(x) for pair in spikes for x in pair]
     arr = (C.c_double * max(1, len(sp)))(*sp)
-    _check(lib().dos_density(_ptr(d), d.numel(), int(n_bins), KERNEL[kernel], float(scale),
-                             arr if sp else None, len(sp) // 2, _ptr(hist_out), _stream(stream)))
+    _check(lib().dos_density_raw(_ptr(d), d.numel(), int(n_bins), KERNEL[kernel], float(scale),
+                                 arr if sp else None, len(sp) // 2, _ptr(hist_out), _stream(stream)))
     return hist_out
 
 
@@ -443,34 +481,18 @@ def dos_get_plan(g: Graph, Nz: int, prec: str = "fp32") -> dict:
 
 
 # ---------------------------------------------------------------------------
-# assembly of a filtered density (host arithmetic on three scalars)
+# whole-graph densities (the library does the assembly)
 # ---------------------------------------------------------------------------
 def density_with_spikes(d: torch.Tensor, g: Graph, n_bins: int, filter: Filter | None = None,
                         count_isolated: bool = True, kernel: str = "jackson", stream=None) -> torch.Tensor:
-    """Histogram of the whole graph from moments d of the (filtered) operator.
-
-    With a twin filter, d are the moments of P^T H P (r = N - removed
-    eigenvalues); the removed eigenvalues sit at 0 (open twins) and at -1/d
-    (closed twins of degree d) (§3.4).  Nodes without edges contribute
-    eigenvalue 0 too.  The series part is scaled by r / N_total and every
-    removed eigenvalue value becomes a point mass (count / N_total).
-    """
-    scale, spikes = filtered_scale_and_spikes(g, filter, count_isolated)
-    return dos_density(d, n_bins, kernel=kernel, scale=scale, spikes=spikes, stream=stream)
+    """Histogram of the whole graph from moments d of the (filtered) operator
+    (§3.4): dos_density with the graph and the filter."""
+    return dos_density(d, n_bins, kernel=kernel, g=g, filter=filter, count_isolated=count_isolated, stream=stream)
 
 
 def filtered_scale_and_spikes(g: Graph, filter: Filter | None = None, count_isolated: bool = True):
-    """(r / N_total, [(lambda, count / N_total)]): the weight of the filtered
-    operator's density and the point masses of the eigenvalues it leaves out
-    (filtered twins, and isolated nodes at 0 when counted)."""
-    info = g.info()
-    iso = info["n_isolated"] if count_isolated else 0
-    n_total = info["n"] + iso
-    removed = filter.info()["removed"] if filter is not None else 0
-    removed_eigs = dict(dos_filter_spikes(filter)) if filter is not None else {}
-    removed_eigs[0.0] = removed_eigs.get(0.0, 0) + iso
-    spikes = [(lam, c / n_total) for lam, c in sorted(removed_eigs.items()) if c]
-    return (info["n"] - removed) / n_total, spikes
+    """(r / N_total, [(lambda, count / N_total)]) from the library (dos_density_weights)."""
+    return dos_density_weights(g, filter, count_isolated)
 
 
 # ---------------------------------------------------------------------------

@@ -52,10 +52,13 @@ def _stale() -> bool:
 
 def _compile(nvcc: str, src: str, verbose: bool) -> str:
     obj = os.path.join(BUILD, os.path.basename(src).replace(".cu", ".o"))
-    cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj]
+    # sources are named relative to the package, so __FILE__ in the library's
+    # error messages reads "csrc/<file>.cu" wherever the tree was built
+    rel = os.path.relpath(src, PKG)
+    cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-c", rel, "-o", obj]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
-    r = subprocess.run(cmd, capture_output=True, text=True)
+    r = subprocess.run(cmd, capture_output=True, text=True, cwd=PKG)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed on {os.path.basename(src)}:\n{r.stdout}\n{r.stderr}")
     if verbose and r.stderr:

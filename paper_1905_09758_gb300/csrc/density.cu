@@ -4,6 +4,8 @@
 #include <algorithm>
 #include <cmath>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "common.cuh"
 
@@ -102,19 +104,95 @@ static int read_spikes(const double* spikes, int n_spikes, Spikes* sp, const cha
   return DOS_OK;
 }
 
-extern "C" int dos_density(const double* d, int M, int n_bins, int kernel, double scale, const double* spikes,
-                           int n_spikes, double* hist_out, void* stream) {
-  clear_error();
-  if (!d || !hist_out) return fail(DOS_EINVAL, "dos_density: null pointer");
-  if (M < 1 || M > (1 << 20)) return fail(DOS_EINVAL, "dos_density: M must be in [1, 2^20]");
-  if (n_bins < 1 || n_bins > (1 << 20)) return fail(DOS_EINVAL, "dos_density: n_bins must be in [1, 2^20]");
-  if (kernel != DOS_KERNEL_NONE && kernel != DOS_KERNEL_JACKSON) return fail(DOS_EINVAL, "dos_density: kernel");
-  Spikes sp{};
-  NDOS_CHECK(read_spikes(spikes, n_spikes, &sp, "dos_density"));
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
+static int density_launch(const double* d, int M, int n_bins, int kernel, double scale, const Spikes& sp,
+                          double* hist_out, cudaStream_t s, const char* who) {
+  if (!d || !hist_out) return fail(DOS_EINVAL, std::string(who) + ": null pointer");
+  if (M < 1 || M > (1 << 20)) return fail(DOS_EINVAL, std::string(who) + ": M must be in [1, 2^20]");
+  if (n_bins < 1 || n_bins > (1 << 20)) return fail(DOS_EINVAL, std::string(who) + ": n_bins must be in [1, 2^20]");
+  if (kernel != DOS_KERNEL_NONE && kernel != DOS_KERNEL_JACKSON) return fail(DOS_EINVAL, std::string(who) + ": kernel");
   k_density<<<n_bins, 256, 0, s>>>(d, M, n_bins, kernel, scale, sp, hist_out);
   NDOS_LAUNCHED();
   return DOS_OK;
+}
+
+// Weight of the series part and the point masses of a whole-graph density
+// (§3.4 filtered density; nodes without edges carry the eigenvalue 0):
+//   N_total = N + n_isolated (counting isolated nodes) or N,
+//   scale   = r / N_total, r = N - removed (N without a filter),
+//   spikes  = every eigenvalue the filter removed, with isolated nodes added
+//             at 0, as (lambda, count / N_total) in ascending lambda.
+static int density_weights(const Graph* G, const Filter* F, uint32_t flags, double* scale,
+                           std::vector<std::pair<double, int64_t>>* eigs, double* n_total) {
+  if (F && !G) G = F->g;
+  if (F && F->g != G) return fail(DOS_EINVAL, "dos_density: the filter belongs to another graph");
+  if (flags & ~static_cast<uint32_t>(DOS_DENSITY_COUNT_ISOLATED)) return fail(DOS_EINVAL, "dos_density: unknown flags");
+  eigs->clear();
+  if (!G) {
+    *scale = 1.0;
+    *n_total = 0.0;
+    return DOS_OK;
+  }
+  const int64_t iso = (flags & DOS_DENSITY_COUNT_ISOLATED) ? G->n_isolated : 0;
+  const int64_t total = G->n + iso;
+  if (total < 1) return fail(DOS_EINVAL, "dos_density: the graph has no nodes");
+  const int64_t removed = F ? F->removed : 0;
+  if (F) *eigs = F->spikes;  // ascending lambda
+  if (iso > 0) {
+    auto it = std::find_if(eigs->begin(), eigs->end(), [](const std::pair<double, int64_t>& e) { return e.first >= 0.0; });
+    if (it != eigs->end() && it->first == 0.0)
+      it->second += iso;
+    else
+      eigs->insert(it, {0.0, iso});
+  }
+  eigs->erase(std::remove_if(eigs->begin(), eigs->end(), [](const std::pair<double, int64_t>& e) { return e.second == 0; }),
+              eigs->end());
+  *scale = static_cast<double>(G->n - removed) / static_cast<double>(total);
+  *n_total = static_cast<double>(total);
+  return DOS_OK;
+}
+
+extern "C" int dos_density(const double* d, int M, int n_bins, int kernel, dos_graph_t g, dos_filter_t f,
+                           uint32_t flags, double* hist_out, void* stream) {
+  clear_error();
+  double scale = 1.0, n_total = 0.0;
+  std::vector<std::pair<double, int64_t>> eigs;
+  NDOS_CHECK(density_weights(reinterpret_cast<const Graph*>(g), reinterpret_cast<const Filter*>(f), flags, &scale,
+                             &eigs, &n_total));
+  if (static_cast<int>(eigs.size()) > kMaxSpikes) return fail(DOS_EINVAL, "dos_density: more than 64 distinct spikes");
+  Spikes sp{};
+  sp.n = static_cast<int>(eigs.size());
+  for (int k = 0; k < sp.n; ++k) {
+    sp.lam[k] = eigs[k].first;
+    sp.mass[k] = static_cast<double>(eigs[k].second) / n_total;
+  }
+  return density_launch(d, M, n_bins, kernel, scale, sp, hist_out, static_cast<cudaStream_t>(stream), "dos_density");
+}
+
+extern "C" int dos_density_weights(dos_graph_t g, dos_filter_t f, uint32_t flags, double* scale_out,
+                                   double* spikes_out, int capacity, int* n_spikes) {
+  clear_error();
+  if (!g && !f) return fail(DOS_EINVAL, "dos_density_weights: no graph and no filter");
+  if (capacity < 0 || (capacity > 0 && !spikes_out)) return fail(DOS_EINVAL, "dos_density_weights: bad buffer");
+  double scale = 1.0, n_total = 0.0;
+  std::vector<std::pair<double, int64_t>> eigs;
+  NDOS_CHECK(density_weights(reinterpret_cast<const Graph*>(g), reinterpret_cast<const Filter*>(f), flags, &scale,
+                             &eigs, &n_total));
+  if (scale_out) *scale_out = scale;
+  if (n_spikes) *n_spikes = static_cast<int>(eigs.size());
+  for (int k = 0; k < static_cast<int>(eigs.size()) && k < capacity; ++k) {
+    spikes_out[2 * k] = eigs[k].first;
+    spikes_out[2 * k + 1] = static_cast<double>(eigs[k].second) / n_total;
+  }
+  return DOS_OK;
+}
+
+extern "C" int dos_density_raw(const double* d, int M, int n_bins, int kernel, double scale, const double* spikes,
+                               int n_spikes, double* hist_out, void* stream) {
+  clear_error();
+  Spikes sp{};
+  NDOS_CHECK(read_spikes(spikes, n_spikes, &sp, "dos_density_raw"));
+  return density_launch(d, M, n_bins, kernel, scale, sp, hist_out, static_cast<cudaStream_t>(stream),
+                        "dos_density_raw");
 }
 
 extern "C" int dos_density_batched(const double* d, int M, int64_t n_graphs, int n_bins, int kernel,

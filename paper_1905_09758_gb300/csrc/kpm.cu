@@ -78,10 +78,45 @@ __global__ void k_moments_from_raw(const double* __restrict__ raw, int M, int do
   }
 }
 
-__global__ void k_fill_f32(float* __restrict__ p, int64_t n, float v) {
+__global__ void k_fill_f32(float* __restrict__ p, int64_t n, int64_t stride, float v) {
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x)
-    p[i] = v;
+    p[i * stride] = v;
+}
+
+// LDOS output of a chunk of moments [m0, m0 + cnt) from the step scratch
+// part[(m % ch) * tiles + t][k] (one row per tile): the tiles' values are
+// summed in tile order and written moment-major (out[m * n + k]) or
+// node-major (out[k * M + m], through a 32 x 32 shared-memory transpose so
+// both sides stay coalesced).  Block (32, 8).
+template <bool NODE_MAJOR>
+__global__ void __launch_bounds__(256) k_ldos_fold(const float* __restrict__ part, int tiles, int ch, int64_t n,
+                                                   int m0, int cnt, int M, float* __restrict__ out) {
+  __shared__ float tile_s[32][33];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int64_t k0 = static_cast<int64_t>(blockIdx.x) * 32; k0 < n; k0 += static_cast<int64_t>(gridDim.x) * 32) {
+    for (int r0 = 0; r0 < cnt; r0 += 32) {
+      for (int r = ty; r < 32; r += 8) {
+        const int64_t k = k0 + tx;
+        const int m = m0 + r0 + r;
+        float v = 0.f;
+        if (k < n && r0 + r < cnt) {
+          const float* src = part + static_cast<size_t>(m % ch) * tiles * n + k;
+          for (int t = 0; t < tiles; ++t) v += src[static_cast<size_t>(t) * n];
+          if (!NODE_MAJOR) out[static_cast<size_t>(m) * n + k] = v;
+        }
+        tile_s[r][tx] = v;
+      }
+      if (NODE_MAJOR) {
+        __syncthreads();
+        for (int j = ty; j < 32; j += 8) {
+          const int64_t k = k0 + j;
+          if (k < n && r0 + tx < cnt) out[static_cast<size_t>(k) * M + m0 + r0 + tx] = tile_s[tx][j];
+        }
+        __syncthreads();
+      }
+    }
+  }
 }
 
 
@@ -212,7 +247,7 @@ struct OpSpec {
 
 template <typename T>
 static int run_steps(const Graph* G, const Filter* F, const Plan& plan, int M, int Nz, uint64_t seed, int mode,
-                     double* d_out, float* C_out, cudaStream_t s, const OpSpec& op = OpSpec()) {
+                     double* d_out, float* C_out, cudaStream_t s, const OpSpec& op = OpSpec(), int layout = 0) {
   constexpr int V = VecT<T>::N;
   const int64_t n = G->n;
   const bool ldos = mode == kModeLdos || mode == kModeLdosOp;
@@ -224,7 +259,7 @@ static int run_steps(const Graph* G, const Filter* F, const Plan& plan, int M, i
 
   T *ua = nullptr, *ub = nullptr;
   double *partial = nullptr, *raw = nullptr;
-  float* csum = nullptr;
+  float *csum = nullptr, *lpart = nullptr;
   int st = DOS_OK;
   const auto cleanup = [&]() {
     dfree(ua, s);
@@ -232,6 +267,7 @@ static int run_steps(const Graph* G, const Filter* F, const Plan& plan, int M, i
     dfree(partial, s);
     dfree(raw, s);
     dfree(csum, s);
+    dfree(lpart, s);
   };
   if ((st = dalloc_t(&ua, elems, s)) || (st = dalloc_t(&ub, elems, s)) ||
       (st = dalloc_t(&partial, static_cast<size_t>(n_raw) * width, s)) || (st = dalloc_t(&raw, n_raw, s))) {
@@ -272,9 +308,31 @@ static int run_steps(const Graph* G, const Filter* F, const Plan& plan, int M, i
   const int init_grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((chunks + 255) / 256, width)));
   if (st == DOS_OK) st = launch_init<T>(ip, init_grid, s);
 
+  // LDOS output.  One tile and the moment-major layout: every step stores
+  // its row of C_out directly.  Otherwise the steps store one row per tile
+  // into a scratch of `ch` moments, and k_ldos_fold sums the tiles in a fixed
+  // order into the requested layout once a chunk of moments is complete.
+  const bool node_major = layout == 1;
+  const bool fold = ldos && (plan.tiles > 1 || node_major);
+  int ch = 1;
+  if (fold && st == DOS_OK) {
+    const double row = 4.0 * static_cast<double>(n) * plan.tiles;
+    ch = static_cast<int>(std::max(1.0, std::min(32.0, std::floor(256.0e6 / row))));
+    st = dalloc_t(&lpart, static_cast<size_t>(ch) * plan.tiles * n, s);
+  }
+  const auto fold_chunk = [&](int m0, int cnt) {
+    const unsigned blocks = static_cast<unsigned>(std::min<int64_t>((n + 31) / 32, 16LL * num_sms()));
+    if (node_major)
+      k_ldos_fold<true><<<blocks, dim3(32, 8), 0, s>>>(lpart, plan.tiles, ch, n, m0, cnt, M, C_out);
+    else
+      k_ldos_fold<false><<<blocks, dim3(32, 8), 0, s>>>(lpart, plan.tiles, ch, n, m0, cnt, M, C_out);
+    count_launch();
+    cu(cudaGetLastError(), "k_ldos_fold");
+  };
   if (ldos && st == DOS_OK) {
-    if (plan.tiles > 1) cu(cudaMemsetAsync(C_out, 0, sizeof(float) * static_cast<size_t>(M) * n, s), "memset C");
-    k_fill_f32<<<std::min<unsigned>(4096, std::max<unsigned>(1, ceil_div(n, 256))), 256, 0, s>>>(C_out, n, 1.0f);
+    // moment 0: C[0][k] = z_k . z_k / Nz = 1 for Rademacher probes
+    k_fill_f32<<<std::min<unsigned>(4096, std::max<unsigned>(1, ceil_div(n, 256))), 256, 0, s>>>(
+        C_out, n, node_major ? M : 1, 1.0f);
     count_launch();
     cu(cudaGetLastError(), "k_fill_f32");
   }
@@ -295,7 +353,7 @@ static int run_steps(const Graph* G, const Filter* F, const Plan& plan, int M, i
   prm.nz = Nz;
   prm.inv_nz = 1.0f / static_cast<float>(Nz);
   prm.seed = seed;
-  prm.ldos_atomic = plan.tiles > 1 ? 1 : 0;
+  prm.ldos_tile_stride = fold && plan.tiles > 1 ? n : 0;
   prm.op = op.kind;
   prm.op_c = static_cast<float>(op.c);
   prm.op_inv_r = static_cast<float>(op.inv_r);
@@ -307,11 +365,18 @@ static int run_steps(const Graph* G, const Filter* F, const Plan& plan, int M, i
     prm.u_pn = (k & 1) ? ua : ub;
     prm.first = k == 0 ? 1 : 0;
     prm.partial = partial + static_cast<size_t>(1 + static_cast<int64_t>(k) * n_dots) * width;
-    prm.ldos = ldos ? C_out + static_cast<size_t>(k + 1) * n : nullptr;
+    const int m = k + 1;  // the LDOS moment this step produces
+    prm.ldos = !ldos ? nullptr
+                     : (fold ? lpart + static_cast<size_t>(m % ch) * plan.tiles * n : C_out + static_cast<size_t>(m) * n);
     if (prof) profile_begin(s);
     st = launch_step<T>(plan, op.kind == 0 ? (ldos ? kModeLdos : kModeDos) : (ldos ? kModeLdosOp : kModeDosOp), prm,
                         s, side);
     if (prof) profile_end(s);
+    // a chunk is complete at its last moment or at M - 1 (moment 0 is filled above)
+    if (fold && st == DOS_OK && ((m + 1) % ch == 0 || m == M - 1)) {
+      const int m0 = std::max(1, (m / ch) * ch);
+      fold_chunk(m0, m - m0 + 1);
+    }
   }
   if (st == DOS_OK) {
     k_reduce_partials<<<static_cast<unsigned>(n_raw), 256, 0, s>>>(partial, width, raw);
@@ -329,7 +394,7 @@ static int run_steps(const Graph* G, const Filter* F, const Plan& plan, int M, i
 }
 
 static int run_kpm(const Graph* G, const Filter* F, int M, int Nz, uint64_t seed, int prec, int mode,
-                   double* d_out, float* C_out, cudaStream_t s, const OpSpec& op = OpSpec()) {
+                   double* d_out, float* C_out, cudaStream_t s, const OpSpec& op = OpSpec(), int layout = 0) {
   if (!G) return fail(DOS_EINVAL, "null graph");
   if (G->n < 1) return fail(DOS_EINVAL, "graph has no edges");
   if (M < 1 || M > (1 << 20)) return fail(DOS_EINVAL, "M must be in [1, 2^20]");
@@ -344,11 +409,11 @@ static int run_kpm(const Graph* G, const Filter* F, int M, int Nz, uint64_t seed
   NDOS_CHECK(make_plan(G, Nz, prec, mode, &plan));
   switch (prec) {
     case DOS_BF16:
-      return run_steps<__nv_bfloat16>(G, F, plan, M, Nz, seed, mode, d_out, C_out, s, op);
+      return run_steps<__nv_bfloat16>(G, F, plan, M, Nz, seed, mode, d_out, C_out, s, op, layout);
     case DOS_FP16:
-      return run_steps<__half>(G, F, plan, M, Nz, seed, mode, d_out, C_out, s, op);
+      return run_steps<__half>(G, F, plan, M, Nz, seed, mode, d_out, C_out, s, op, layout);
     default:
-      return run_steps<float>(G, F, plan, M, Nz, seed, mode, d_out, C_out, s, op);
+      return run_steps<float>(G, F, plan, M, Nz, seed, mode, d_out, C_out, s, op, layout);
   }
 }
 
@@ -421,6 +486,15 @@ int ldos_moments(dos_graph_t g, int M, int Nz, uint64_t seed, int prec, float* C
   if (!C_out) return fail(DOS_EINVAL, "ldos_moments: C_out is NULL");
   return run_kpm(reinterpret_cast<const Graph*>(g), nullptr, M, Nz, seed, prec, kModeLdos, d_out, C_out,
                  static_cast<cudaStream_t>(stream));
+}
+
+int ldos_moments_ex(dos_graph_t g, int M, int Nz, uint64_t seed, int prec, int layout, float* C_out,
+                    double* d_out, void* stream) {
+  clear_error();
+  if (!C_out) return fail(DOS_EINVAL, "ldos_moments_ex: C_out is NULL");
+  if (layout != DOS_MOMENT_MAJOR && layout != DOS_NODE_MAJOR) return fail(DOS_EINVAL, "ldos_moments_ex: layout");
+  return run_kpm(reinterpret_cast<const Graph*>(g), nullptr, M, Nz, seed, prec, kModeLdos, d_out, C_out,
+                 static_cast<cudaStream_t>(stream), OpSpec(), layout);
 }
 
 int dos_moments_op(dos_graph_t g, int op, double lo, double hi, int M, int Nz, uint64_t seed, int prec,

@@ -211,8 +211,8 @@ struct StepParams {
   // weight d_i)
   int op;
   float op_c, op_inv_r;
-  float* ldos;      // LDOS: C_out + m * n_compact, indexed by compact id
-  int ldos_atomic;  // 1 when several tiles add into the same C entry
+  float* ldos;      // LDOS: this step's output row, indexed by compact id
+  int64_t ldos_tile_stride;  // tile j writes ldos + j * stride (0: a single tile)
   int* err;         // device error word
 };
 
@@ -305,11 +305,9 @@ __device__ __forceinline__ void step_epilogue(const StepParams& prm, bool active
       // sum_j z_j (V_{k+1})_j of this tile (V = S^{-1} U on H, U on X~)
       const float vsum = MD::op ? prod0 : prod0 * sqrtf(fd);
       dd0 += static_cast<double>(vsum);
-      float* dst = prm.ldos + compact;
-      if (prm.ldos_atomic)
-        atomicAdd(dst, vsum * prm.inv_nz);
-      else
-        *dst = vsum * prm.inv_nz;
+      // one plain store per (tile, node); several tiles are summed afterwards
+      // in a fixed order (k_ldos_fold), so the result is reproducible
+      prm.ldos[static_cast<size_t>(tile) * prm.ldos_tile_stride + compact] = vsum * prm.inv_nz;
     }
   }
 }

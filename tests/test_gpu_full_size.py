@@ -10,8 +10,9 @@ times (automatic plan), against the FP64 oracle.
   ~4e7 nodes): per-graph moments at M = 200, Nz = 16 with the autotuned plan,
   sampled graphs checked one by one against the oracle run on that graph alone.
 * Barabasi-Albert m = 8, N = 20M (3.2e8 nonzeros): CSR rows and the first LDOS
-  moment of sampled nodes from their neighbourhoods in the edge list; BF16 /
-  FP16 storage against FP32 at M = 1000, Nz = 32.
+  moment of sampled nodes from their neighbourhoods in the edge list, LDOS
+  moments m <= 3 of sampled nodes from the oracle's CSR; BF16 / FP16 storage
+  against FP32 at M = 1000, Nz = 32.
 """
 import numpy as np
 import pytest
@@ -86,6 +87,46 @@ def test_full_ldos_every_node(chung_lu_1m):
     assert np.all(c[0] == 1.0)
     assert np.abs(c.T - cref).max() <= TOL_C
     assert np.abs(dl.cpu().numpy() - mu / (ref.n * nz)).max() <= TOL_D
+
+
+def test_full_filtered_histogram_through_the_c_abi(chung_lu_1m):
+    """The filtered whole-graph histogram of the 1.1M-node workload made by
+    C-ABI calls alone (ctypes straight to the library: CSR build, twin
+    filter, filtered moments, dos_density with the graph and the filter),
+    against the oracle's filtered moments, scale r / N_total and point mass
+    at 0 (§3.4)."""
+    import ctypes as C
+
+    s, d, n, ref, _ = chung_lu_1m
+    lib = nd.lib()
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    src, dst = torch.from_numpy(s).cuda(), torch.from_numpy(d).cuda()
+    g, f = C.c_void_p(), C.c_void_p()
+    assert lib.dos_build_csr(C.c_void_p(src.data_ptr()), C.c_void_p(dst.data_ptr()), src.numel(), n, 0, stream,
+                             C.byref(g)) == nd.DOS_OK
+    try:
+        assert lib.dos_motif_filter(g, stream, C.byref(f)) == nd.DOS_OK
+        m, nz, bins, seed = 20, 8, 200, 77
+        dm = torch.empty(m, dtype=torch.float64, device="cuda")
+        hist = torch.empty(bins, dtype=torch.float64, device="cuda")
+        assert lib.dos_moments(g, f, m, nz, C.c_uint64(seed), 0, C.c_void_p(dm.data_ptr()),  # prec DOS_FP32
+                               stream) == nd.DOS_OK
+        assert lib.dos_density(C.c_void_p(dm.data_ptr()), m, bins, 1, g, f, nd.DOS_DENSITY_COUNT_ISOLATED,
+                               C.c_void_p(hist.data_ptr()), stream) == nd.DOS_OK
+        torch.cuda.synchronize()
+        h = hist.cpu().numpy()
+    finally:
+        if f.value:
+            lib.dos_filter_destroy(f)
+        lib.dos_graph_destroy(g)
+    cid, removed = oracle.twin_classes(ref)
+    z = oracle.project_probes(oracle.probes(seed, ref.old_id, nz), cid)
+    d_ref = oracle.kpm_doubled(ref, z, m) / ((ref.n - removed) * nz)
+    n_total = ref.n + ref.n_isolated
+    h_ref = (ref.n - removed) / n_total * oracle.histogram(d_ref, bins)
+    h_ref += oracle.point_mass_histogram([0.0], [(removed + ref.n_isolated) / n_total], bins)
+    assert abs(h.sum() - 1.0) < 1e-9
+    assert np.abs(h - h_ref).max() <= 1e-5
 
 
 def test_full_m500_properties(chung_lu_1m):
@@ -168,6 +209,38 @@ def test_ba_20m_sampled_rows_and_first_ldos_moment(barabasi_albert_20m):
         w = 1.0 / np.sqrt(float(deg[k]) * deg[nb].astype(np.float64))
         c1_ref = float(zk @ (w @ zl)) / nz
         assert abs(c1[k] - c1_ref) <= TOL_C, (k, c1[k], c1_ref)
+
+
+def test_ba_20m_sampled_ldos_moments_m3(barabasi_albert_20m):
+    """LDOS moments C[m][k], m <= 3, of sampled nodes of the 20M-node BA graph
+    (M = 4, Nz = 32) against the oracle: T_1 Z = H Z on every node, then
+    T_2 Z on the sampled nodes' neighbours and T_3 Z on the nodes, from the
+    oracle's CSR of the edge list (Eq. (6), (12))."""
+    import scipy.sparse as sp
+
+    s, d, n, g = barabasi_albert_20m
+    nz, seed = 32, 41
+    c, _ = nd.ldos_moments(g, 4, nz, seed)
+    c = c.cpu().numpy()
+    ref = oracle.build_csr(s, d, n)
+    h = oracle.h_sparse(ref)
+    rng = np.random.default_rng(12)
+    sample = np.unique(np.concatenate([rng.choice(ref.n, 32, replace=False), np.arange(4), [ref.n - 1]]))
+    z = oracle.probes(seed, ref.old_id, nz)
+    v1 = h @ z  # T_1 Z on every node
+    nb = np.unique(np.concatenate([ref.col[ref.row_ptr[k]:ref.row_ptr[k + 1]] for k in sample]))
+    v2_nb = 2.0 * (h[nb] @ v1) - z[nb]  # T_2 Z on the neighbours
+    v2 = np.zeros((ref.n, nz))
+    v2[nb] = v2_nb
+    v2_s = 2.0 * (h[sample] @ v1) - z[sample]
+    v3_s = 2.0 * (sp.csr_matrix(h[sample]) @ v2) - v1[sample]
+    zs = z[sample]
+    want = np.stack([np.ones(sample.size), (zs * v1[sample]).sum(1) / nz, (zs * v2_s).sum(1) / nz,
+                     (zs * v3_s).sum(1) / nz])
+    got = c[:, sample]
+    err = np.abs(got - want)
+    print(f"BA 20M sampled LDOS m<=3: max error {err.max():.2e}")
+    assert err.max() <= TOL_C
 
 
 def test_ba_20m_mixed_precision_at_m1000(barabasi_albert_20m):

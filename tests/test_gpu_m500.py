@@ -1,0 +1,125 @@
+"""GPU parity at the benchmark's moment count, M = 500, Nz = 64.
+
+* Filtered and plain DOS moments (doubling, 250 fused steps) on the
+  Chung-Lu-with-twins graph (6.6k nodes) and the hub graph (CTA-per-row path),
+  element by element against oracle.kpm_doubled on the same probes:
+  |d_gpu - d_oracle| <= 1e-5 (the FP32 moment tolerance, §3.1 Eq. (9), (11)).
+* LDOS moments (direct recurrence, 499 fused steps) on the same graphs:
+  every entry of the N x M matrix against oracle.kpm_direct, and the DOS
+  moments of the direct run.
+* The benchmark's own case: the filtered DOS of the 1.1M-node Chung-Lu graph
+  with twin leaves at M = 500, Nz = 64, seed 2025, against the oracle run on
+  probe-column subsets in worker processes (Eq. (11) sums over probes).
+
+LDOS tolerance at m = 500, derived as for m = 100 in test_gpu_parity.py:
+every step rounds each stored entry with relative error u = 2^-24 ~ 6e-8,
+and the Chebyshev recurrence carries an error made at step s into step m with
+a factor |U_{m-s}| <= m - s + 1; errors of independent sign accumulate like a
+random walk, sqrt(sum_s (m - s + 1)^2) u ~ u m^1.5 / sqrt(3) = 3.9e-4 at
+m = 500 before the 1/Nz average over probes.  That estimate is the asserted
+per-entry bound (an FP32 emulation of the recurrence on the 6.6k-node graph
+reaches 7.1e-5 at m = 499; the error grows about as m^2 along the lambda = 1
+eigenvector, 2.8e-6 at m = 100).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synthgraphs as sg
+
+pytestmark = pytest.mark.gpu
+
+nd = pytest.importorskip("paper_1905_09758_gb300")
+
+TOL_D = 1e-5
+TOL_C500 = 2.0**-24 * 500**1.5 / np.sqrt(3.0)  # 3.9e-4
+M, NZ = 500, 64
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1905_09758_gb300.build import build
+
+    build()
+    nd.dos_set_plan(0, 0)
+    yield
+    nd.dos_set_plan(0, 0)
+
+
+def _graphs():
+    s, d, n = sg.chung_lu(6000, 2.5, 12.0, 7)
+    yield "cl_twins", sg.add_twin_leaves(s, d, n, 300, 8)
+    s, d, n = sg.erdos_renyi(4000, 0.003, 2)
+    hub = np.zeros(3000, np.int64)
+    leaves = 1 + np.arange(3000, dtype=np.int64)
+    yield "hub", (np.concatenate([s, hub, [5, 5, 9]]), np.concatenate([d, leaves, [5, 9, 5]]), n)
+
+
+GRAPHS = dict(_graphs())
+
+
+def _gpu_graph(src, dst, n):
+    return nd.dos_build_csr(torch.from_numpy(np.ascontiguousarray(src, np.int64)).cuda(),
+                            torch.from_numpy(np.ascontiguousarray(dst, np.int64)).cuda(), n)
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+@pytest.mark.parametrize("filtered", [False, True])
+def test_dos_moments_m500(name, filtered):
+    src, dst, n = GRAPHS[name]
+    ref = oracle.build_csr(src, dst, n)
+    g = _gpu_graph(src, dst, n)
+    seed = 2025
+    z = oracle.probes(seed, ref.old_id, NZ)
+    r = ref.n
+    f = None
+    if filtered:
+        f = nd.dos_motif_filter(g)
+        cid, removed = oracle.twin_classes(ref)
+        z = oracle.project_probes(z, cid)
+        r = ref.n - removed
+    d = nd.dos_moments(g, M, NZ, seed, filter=f).cpu().numpy()
+    d_ref = oracle.kpm_doubled(ref, z, M) / (r * NZ)
+    err = np.abs(d - d_ref)
+    print(f"{name} filtered={filtered} M=500: max |d - d_oracle| = {err.max():.2e}")
+    assert abs(d[0] - 1.0) < 1e-12
+    assert err.max() <= TOL_D
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+def test_ldos_moments_m500(name):
+    src, dst, n = GRAPHS[name]
+    ref = oracle.build_csr(src, dst, n)
+    g = _gpu_graph(src, dst, n)
+    seed = 2032
+    c, dl = nd.ldos_moments(g, M, NZ, seed)
+    z = oracle.probes(seed, ref.old_id, NZ)
+    mu, cref = oracle.kpm_direct(ref, z, M, ldos=True)
+    c = c.cpu().numpy()
+    err_c = np.abs(c.T - cref)
+    err_d = np.abs(dl.cpu().numpy() - mu / (ref.n * NZ))
+    print(f"{name} M=500: max |C - C_oracle| = {err_c.max():.2e} (bound {TOL_C500:.2e}), "
+          f"max |d - d_oracle| = {err_d.max():.2e}")
+    assert np.all(c[0] == 1.0)
+    assert err_c.max() <= TOL_C500
+    assert err_d.max() <= TOL_D
+
+
+def test_full_filtered_dos_m500_chung_lu_1m():
+    """The benchmark's filtered DOS (M = 500, Nz = 64, seed 2025) on the
+    1.1M-node graph in the benchmark's automatic plan, against the oracle."""
+    import oracle_pool
+
+    spec = ("chung_lu_twins", 1_000_000, 2.5, 20.0, 50_000, 2025)
+    s, d, n = sg.add_twin_leaves(*sg.chung_lu(1_000_000, 2.5, 20.0, 2025), 50_000, 2026)
+    g = _gpu_graph(s, d, n)
+    del s, d
+    f = nd.dos_motif_filter(g)
+    dg = nd.dos_moments(g, M, NZ, 2025, filter=f).cpu().numpy()
+    d_ref = oracle_pool.doubled_moments(spec, 2025, NZ, M, filtered=True)
+    err = np.abs(dg - d_ref)
+    print(f"1.1M nodes filtered M=500: max |d - d_oracle| = {err.max():.2e} at m = {int(err.argmax())}")
+    assert err.max() <= TOL_D

@@ -207,7 +207,7 @@ def test_density_spikes_and_scale():
     d = np.zeros(10)
     d[0] = 1.0
     spikes = [(0.0, 0.25), (-1.0, 0.1), (0.33, 0.05)]
-    h = nd.dos_density(torch.from_numpy(d).cuda(), 4, scale=0.6, spikes=spikes).cpu().numpy()
+    h = nd.dos_density_raw(torch.from_numpy(d).cuda(), 4, scale=0.6, spikes=spikes).cpu().numpy()
     ref = 0.6 * oracle.histogram(d, 4) + oracle.point_mass_histogram([s[0] for s in spikes], [s[1] for s in spikes], 4)
     assert np.abs(h - ref).max() <= 1e-12
 
@@ -403,3 +403,30 @@ def test_all_motif_filters_bit_exact_and_moments(name):
     z = oracle.project_probes(oracle.probes(27, ref.old_id, nz), cid_ref)
     d_ref = oracle.kpm_doubled(ref, z, m) / ((ref.n - removed) * nz)
     assert np.abs(d - d_ref).max() <= TOL_D
+
+
+@pytest.mark.parametrize("t", [16, 64])
+def test_ldos_layouts_equal_and_reproducible(t):
+    """ldos_moments_ex: the node-major N x M matrix is the transpose of the
+    moment-major one bit for bit, repeated runs agree bit for bit (several
+    probe tiles are summed in a fixed order), and both match the oracle."""
+    src, dst, n = GRAPHS["hub"]
+    ref = oracle.build_csr(src, dst, n)
+    g = _gpu_graph(src, dst, n)
+    m, nz, seed = 37, 70, 8
+    nd.dos_set_plan(t, 0)
+    try:
+        assert nd.dos_get_plan(g, nz)["tiles"] == -(-nz // t)
+        c_mm, d_mm = nd.ldos_moments(g, m, nz, seed)
+        c_mm2, _ = nd.ldos_moments(g, m, nz, seed)
+        c_nm, d_nm = nd.ldos_moments(g, m, nz, seed, layout="node")
+    finally:
+        nd.dos_set_plan(0, 0)
+    c_mm, c_mm2, c_nm = c_mm.cpu().numpy(), c_mm2.cpu().numpy(), c_nm.cpu().numpy()
+    assert c_nm.shape == (ref.n, m)
+    assert np.array_equal(c_mm, c_mm2)
+    assert np.array_equal(c_nm, c_mm.T)
+    assert np.array_equal(d_mm.cpu().numpy(), d_nm.cpu().numpy())
+    z = oracle.probes(seed, ref.old_id, nz)
+    _, cref = oracle.kpm_direct(ref, z, m, ldos=True)
+    assert np.abs(c_nm - cref).max() <= TOL_C

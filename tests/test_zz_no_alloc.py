@@ -54,7 +54,9 @@ def test_noalloc_matches_dos_moments_on_consecutive_calls():
         g, M, Nz, seed = cases[idx]
         out = _noalloc(g, M, Nz, seed)
         assert np.all(np.isfinite(out))
+        # same kernels, plan and fixed-order reduction as dos_moments: equal bits
         assert np.abs(out - refs[idx]).max() <= TOL_D
+        assert np.array_equal(out, refs[idx]), np.abs(out - refs[idx]).max()
 
 
 def test_noalloc_rejects_sizes_beyond_the_static_scratch():
