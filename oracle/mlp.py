@@ -21,7 +21,8 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["mlp_init", "mlp_forward", "mlp_loss_grad", "adam_step", "mlp_features", "normalize_hist"]
+__all__ = ["mlp_init", "mlp_forward", "mlp_loss_grad", "adam_step", "graph_stats", "mlp_features",
+           "normalize_hist"]
 
 
 def mlp_init(sizes, rng: np.random.Generator):
@@ -82,15 +83,34 @@ def adam_step(params, grads, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
     return out_p, out_m, out_v
 
 
-def mlp_features(hist, d, k):
-    """Feature row per graph: [B * bin masses of the histogram, d_1 .. d_{k-1}].
+def graph_stats(deg, nz: int):
+    """Degree statistics of a graph's non-isolated nodes and its noise level:
+    (mean degree, mean squared degree, largest degree, N * Nz)."""
+    deg = np.asarray(deg, np.float64)
+    return np.array([deg.mean(), np.mean(deg * deg), deg.max(), deg.size * float(nz)])
+
+
+def mlp_features(hist, d, k, stats=None):
+    """Feature row per graph: [B * bin masses of the histogram, d_1 .. d_{k-1}]
+    and, with stats (rows of graph_stats), four more entries
+
+        log(mean d) / 10,  (log(mean d^2) / 2 - log(mean d)) / 10,
+        log(max d) / 10,   log(N Nz) / 10
+
+    (the typical degree, its spread, the hub size and the number of probe
+    entries that set the moments' noise; the / 10 keeps them O(1)).
 
     B * mass is the mean density over a bin scaled to [-1, 1] (O(1) values);
     d_0 = 1 after normalisation carries no information and is left out.
     """
     hist = np.asarray(hist, np.float64)
     d = np.asarray(d, np.float64)
-    return np.concatenate([hist.shape[1] * hist, d[:, 1:k]], axis=1)
+    parts = [hist.shape[1] * hist, d[:, 1:k]]
+    if stats is not None:
+        st = np.asarray(stats, np.float64).reshape(-1, 4)
+        mean, sq, mx, nnz = st[:, 0], st[:, 1], st[:, 2], st[:, 3]
+        parts.append(np.stack([np.log(mean), 0.5 * np.log(sq) - np.log(mean), np.log(mx), np.log(nnz)], axis=1) / 10.0)
+    return np.concatenate(parts, axis=1)
 
 
 def normalize_hist(hist):

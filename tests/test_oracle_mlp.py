@@ -66,6 +66,19 @@ def test_features_hand_example():
     assert np.array_equal(x, [[0.5, 1.5, 0.5]])
 
 
+def test_graph_stats_and_degree_features_hand_example():
+    # degrees of the star K_{1,3}: 3, 1, 1, 1
+    st = oracle.graph_stats([3, 1, 1, 1], 8)
+    assert np.array_equal(st, [1.5, 3.0, 3.0, 32.0])
+    x = oracle.mlp_features([[0.5, 0.5]], [[1.0, 0.2]], 2, stats=[st])
+    want = [1.0, 1.0, 0.2, np.log(1.5) / 10, (0.5 * np.log(3.0) - np.log(1.5)) / 10, np.log(3.0) / 10,
+            np.log(32.0) / 10]
+    assert np.allclose(x, [want], rtol=0, atol=1e-15)
+    # a regular graph has no degree spread
+    x = oracle.mlp_features([[1.0]], [[1.0]], 1, stats=[oracle.graph_stats([4, 4, 4, 4, 4], 1)])
+    assert abs(x[0, 2]) < 1e-15 and abs(x[0, 1] - np.log(4.0) / 10) < 1e-15
+
+
 def test_normalize_hist_hand_example():
     t = oracle.normalize_hist([[-0.1, 0.3, 0.1], [-1.0, 0.0, -2.0]])
     assert np.allclose(t, [[0.0, 0.75, 0.25], [1 / 3, 1 / 3, 1 / 3]], rtol=0, atol=1e-15)
