@@ -663,12 +663,25 @@ int dos_mlp_train_step(dos_mlp_t net, const float* x, const float* t,
 /* Project addition (learned reconstruction; inputs from §3.1, §4.1).
  * Feature rows for the network, one per graph g < n_graphs:
  *   x_out[g] = [ n_bins * hist[g * n_bins + b] for b < n_bins,
- *                d[g * ld_d + m] for 1 <= m < K ]      (n_bins + K - 1 floats)
- * hist [device] double (a Jackson histogram, e.g. dos_density_batched),
- * d [device] double moments (row stride ld_d >= K).  Errors: DOS_EINVAL. */
+ *                d[g * ld_d + m] for 1 <= m < K,
+ *                and, when stats is not NULL, with (mu1, mu2, dmax, e) =
+ *                stats[4 g .. 4 g + 3] as dos_graph_stats returns them:
+ *                log(mu1) / 10, (log(mu2) / 2 - log(mu1)) / 10,
+ *                log(dmax) / 10, log(e) / 10 ]
+ * (n_bins + K - 1, plus 4 with stats, floats per row).  hist [device]
+ * double (a Jackson histogram, e.g. dos_density_batched), d [device] double
+ * moments (row stride ld_d >= K), stats [device] double[4 n_graphs] or NULL.
+ * Errors: DOS_EINVAL. */
 int dos_mlp_features(const double* hist, int n_bins, const double* d,
-                     int ld_d, int K, int64_t n_graphs, float* x_out,
-                     void* stream);
+                     int ld_d, int K, const double* stats, int64_t n_graphs,
+                     float* x_out, void* stream);
+
+/* Project addition (learned reconstruction: the network's degree inputs).
+ * Degree statistics of a graph's non-isolated nodes and its noise level:
+ * stats_out [device] double[4] = (mean degree, mean squared degree, largest
+ * degree, N * Nz); the sums are exact (64-bit integers).  Stream-ordered.
+ * Errors: DOS_EINVAL. */
+int dos_graph_stats(dos_graph_t g, int Nz, double* stats_out, void* stream);
 
 /* Density from the network's output: hist_out[r][b] = scale * probs[r][b]
  * plus point masses (lambda, mass) pairs in `spikes` [host, n_spikes <= 64],

@@ -85,7 +85,8 @@ _SIGNATURES = {
     "dos_mlp_forward": ([_vp, _vp, _i32, _vp, _vp], _i32),
     "dos_mlp_loss_grad": ([_vp, _vp, _vp, _i32, _vp, _vp, _vp], _i32),
     "dos_mlp_train_step": ([_vp, _vp, _vp, _vp, _i32, C.c_float, _vp, _vp], _i32),
-    "dos_mlp_features": ([_vp, _i32, _vp, _i32, _i32, _i64, _vp, _vp], _i32),
+    "dos_mlp_features": ([_vp, _i32, _vp, _i32, _i32, _vp, _i64, _vp, _vp], _i32),
+    "dos_graph_stats": ([_vp, _i32, _vp, _vp], _i32),
     "dos_hist_normalize": ([_vp, _i32, _i64, _vp, _vp], _i32),
     "dos_hist_assemble": ([_vp, _i32, _i64, _dbl, _vp, _i32, _vp, _vp], _i32),
     "dos_lanczos": ([_vp, _i32, _i32, _u64, _vp, _vp, _vp, _vp], _i32),
@@ -594,20 +595,33 @@ def dos_mlp_train_step(net: Mlp, x: torch.Tensor, t: torch.Tensor, lr: float, id
     return loss
 
 
-def dos_mlp_features(hist: torch.Tensor, d: torch.Tensor, K: int, x_out: torch.Tensor | None = None,
-                     stream=None) -> torch.Tensor:
-    """Feature rows [n_bins * hist, d_1 .. d_{K-1}] (n_graphs, n_bins + K - 1), float32."""
+def dos_mlp_features(hist: torch.Tensor, d: torch.Tensor, K: int, stats: torch.Tensor | None = None,
+                     x_out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Feature rows [n_bins * hist, d_1 .. d_{K-1}] (+ 4 degree / noise entries
+    with stats of shape (n_graphs, 4)), float32 (n_graphs, F)."""
     _need_cuda(hist, torch.float64, "hist")
     _need_cuda(d, torch.float64, "d")
     ng, B = hist.shape
     if d.shape[0] != ng or d.shape[1] < K:
         raise ValueError("d must have shape (n_graphs, >= K)")
+    if stats is not None:
+        _need_cuda(stats, torch.float64, "stats", 4 * ng)
+    F = B + K - 1 + (4 if stats is not None else 0)
     if x_out is None:
-        x_out = torch.empty((ng, B + K - 1), dtype=torch.float32, device=hist.device)
-    _need_cuda(x_out, torch.float32, "x_out", ng * (B + K - 1))
-    _check(lib().dos_mlp_features(_ptr(hist), int(B), _ptr(d), int(d.shape[1]), int(K), int(ng), _ptr(x_out),
-                                  _stream(stream)))
+        x_out = torch.empty((ng, F), dtype=torch.float32, device=hist.device)
+    _need_cuda(x_out, torch.float32, "x_out", ng * F)
+    _check(lib().dos_mlp_features(_ptr(hist), int(B), _ptr(d), int(d.shape[1]), int(K), _ptr(stats), int(ng),
+                                  _ptr(x_out), _stream(stream)))
     return x_out
+
+
+def dos_graph_stats(g: Graph, Nz: int, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """(mean degree, mean squared degree, largest degree, N * Nz), float64 CUDA (4,)."""
+    if out is None:
+        out = torch.empty(4, dtype=torch.float64, device=torch.device("cuda", torch.cuda.current_device()))
+    _need_cuda(out, torch.float64, "out", 4)
+    _check(lib().dos_graph_stats(g.handle, int(Nz), _ptr(out), _stream(stream)))
+    return out
 
 
 def dos_hist_normalize(hist: torch.Tensor, t_out: torch.Tensor | None = None, stream=None) -> torch.Tensor:

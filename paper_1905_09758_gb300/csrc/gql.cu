@@ -26,7 +26,7 @@
 #include <algorithm>
 #include <cmath>
 
-#include "common.cuh"
+#include "kpm_kernels.cuh"  // gather_list, cp.async staging helpers
 
 namespace netdos {
 namespace {
@@ -165,6 +165,146 @@ __global__ void __launch_bounds__(kLzThreads) k_lz_apply(int op, const int64_t* 
     if (slot == 0) lz_row_out(op, i, static_cast<float>(deg[i]), acc, ib, nzp, ch, w_cur, y, a0, a1, a2, a3);
   }
   if (slot == 0) {
+    red[warp][4 * ch + 0] = a0;
+    red[warp][4 * ch + 1] = a1;
+    red[warp][4 * ch + 2] = a2;
+    red[warp][4 * ch + 3] = a3;
+  }
+  __syncthreads();
+  for (int p = threadIdx.x; p < 4 * Q; p += kLzThreads) {
+    double sum = 0.0;
+    for (int w = 0; w < kLzWarps; ++w) sum += red[w][p];
+    part[static_cast<size_t>(blockIdx.x) * nzp + p] = sum;
+  }
+}
+
+// apply, light rows [row0, n) (degree < kMediumDeg): the staged pipeline of
+// the Chebyshev step's light kernel.  Each warp takes rounds of R = 32 / Q
+// consecutive rows (Q lanes per row, one 16-byte chunk each); while it
+// gathers for one round its lanes have already issued cp.async copies of the
+// next round's row offsets, column indices and own rows W_k into the other
+// shared-memory slot, and lane 0 has loaded the CSR range of the round after.
+template <int Q>
+struct LzRound {
+  static constexpr int R = 32 / Q;
+  static constexpr int RP = (((R + 3) * 8) + 15) / 16 * 16;
+  static constexpr int COL = ((R * (kMediumDeg - 1) + 8) * 4 + 15) / 16 * 16;
+  static constexpr int OWN = R * Q * 16;
+  static constexpr int off_col = RP, off_own = RP + COL;
+  static constexpr int SLOT = RP + COL + OWN;
+  static constexpr int WARP = 2 * SLOT;
+};
+
+template <int Q>
+__global__ void __launch_bounds__(kLzThreads) k_lz_apply_light(int op, const int64_t* __restrict__ row_ptr,
+                                                               const int32_t* __restrict__ col, int64_t row0,
+                                                               int64_t n, int nzp, const float* __restrict__ w_cur,
+                                                               const float* __restrict__ inv_b, float* __restrict__ y,
+                                                               double* __restrict__ part) {
+  using L = LzRound<Q>;
+  constexpr int R = L::R;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ double red[kLzWarps][4 * Q];
+  unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int grp = lane / Q, ch = lane % Q;
+  unsigned char* wbuf = smem + warp * L::WARP;
+  const float4 ib = reinterpret_cast<const float4*>(inv_b)[ch];
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  const int64_t n_rounds = (n - row0 + R - 1) / R;
+  const int64_t nw = static_cast<int64_t>(gridDim.x) * kLzWarps;
+  auto rows_of = [&](int64_t rd, int64_t& r0, int64_t& r1) {
+    r0 = row0 + rd * R;
+    r1 = r0 + R < n ? r0 + R : n;
+  };
+  auto issue = [&](int64_t rd, int sl_i, int64_t e0, int64_t e1) {
+    int64_t r0, r1;
+    rows_of(rd, r0, r1);
+    unsigned char* sl = wbuf + sl_i * L::SLOT;
+    const int64_t r0a = r0 & ~int64_t(1), ea = e0 & ~int64_t(3);
+    warp_copy16(sl, reinterpret_cast<const unsigned char*>(row_ptr + r0a), (r1 + 2 - r0a) >> 1, lane);
+    warp_copy16(sl + L::off_col, reinterpret_cast<const unsigned char*>(col + ea), (((e1 + 3) & ~int64_t(3)) - ea) >> 2,
+                lane);
+    warp_copy16(sl + L::off_own, reinterpret_cast<const unsigned char*>(w_cur + static_cast<size_t>(r0) * nzp),
+                (r1 - r0) * Q, lane);
+  };
+  auto range_of = [&](int64_t rd, int64_t& e0, int64_t& e1) {
+    e0 = e1 = 0;
+    if (lane == 0 && rd < n_rounds) {
+      int64_t r0, r1;
+      rows_of(rd, r0, r1);
+      e0 = row_ptr[r0];
+      e1 = row_ptr[r1];
+    }
+  };
+  int64_t cur = static_cast<int64_t>(blockIdx.x) * kLzWarps + warp;
+  int64_t nb0, nb1;
+  {
+    int64_t e0, e1;
+    range_of(cur, e0, e1);
+    range_of(cur + nw, nb0, nb1);
+    e0 = __shfl_sync(0xffffffffu, e0, 0);
+    e1 = __shfl_sync(0xffffffffu, e1, 0);
+    if (cur < n_rounds) issue(cur, 0, e0, e1);
+    cp_async_commit();
+  }
+  for (int it = 0; cur < n_rounds; ++it, cur += nw) {
+    const int s = it & 1;
+    {
+      const int64_t e0 = __shfl_sync(0xffffffffu, nb0, 0), e1 = __shfl_sync(0xffffffffu, nb1, 0);
+      if (cur + nw < n_rounds) issue(cur + nw, s ^ 1, e0, e1);
+      cp_async_commit();
+      range_of(cur + 2 * nw, nb0, nb1);
+    }
+    cp_async_wait<1>();
+    __syncwarp();
+    int64_t r0, r1;
+    rows_of(cur, r0, r1);
+    const unsigned char* sl = wbuf + s * L::SLOT;
+    const int64_t r0a = r0 & ~int64_t(1);
+    const int64_t* rp = reinterpret_cast<const int64_t*>(sl) + (r0 - r0a);
+    const int64_t ea = rp[0] & ~int64_t(3);
+    const bool active = r0 + grp < r1;
+    int64_t beg = 0, end = 0;
+    if (active) {
+      beg = rp[grp];
+      end = rp[grp + 1];
+    }
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    gather_list<float, Q, 1>(reinterpret_cast<const uint4*>(w_cur), reinterpret_cast<const int32_t*>(sl + L::off_col) +
+                                                                         (beg - ea),
+                             static_cast<int>(end - beg), 0, ch, acc);
+    if (active) {
+      const float4 own = *reinterpret_cast<const float4*>(sl + L::off_own + (grp * Q + ch) * 16);
+      const float dd = static_cast<float>(end - beg);
+      float4 v = make_float4(acc[0], acc[1], acc[2], acc[3]);
+      float wd = 1.0f;
+      if (op == kLzH) {
+        const float sc = 1.0f / dd;
+        v = make_float4(acc[0] * sc, acc[1] * sc, acc[2] * sc, acc[3] * sc);
+        wd = dd;
+      } else if (op == kLzL) {
+        v = make_float4(dd * own.x - acc[0], dd * own.y - acc[1], dd * own.z - acc[2], dd * own.w - acc[3]);
+      }
+      const float4 out = make_float4(v.x * ib.x, v.y * ib.y, v.z * ib.z, v.w * ib.w);
+      reinterpret_cast<float4*>(y + static_cast<size_t>(r0 + grp) * nzp)[ch] = out;
+      a0 += static_cast<double>(wd * (own.x * ib.x) * out.x);
+      a1 += static_cast<double>(wd * (own.y * ib.y) * out.y);
+      a2 += static_cast<double>(wd * (own.z * ib.z) * out.z);
+      a3 += static_cast<double>(wd * (own.w * ib.w) * out.w);
+    }
+    __syncwarp();
+  }
+  cp_async_wait<0>();
+  // sum over the R row groups of the warp, then over the warps
+#pragma unroll
+  for (int o = Q; o < 32; o <<= 1) {
+    a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+    a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+    a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+    a3 += __shfl_xor_sync(0xffffffffu, a3, o);
+  }
+  if (grp == 0) {
     red[warp][4 * ch + 0] = a0;
     red[warp][4 * ch + 1] = a1;
     red[warp][4 * ch + 2] = a2;
@@ -481,17 +621,31 @@ template <int Q>
 int lanczos_steps(const Graph* G, int op, int m, int nz, int nzp, float* w_cur, float* w_pn, float* y,
                   LanczosState st, int grid, double stop, cudaStream_t s) {
   const unsigned gp = static_cast<unsigned>(nzp);  // a warp per padded probe
-  const int64_t nh = G->n_heavy;
-  const int parts = grid + static_cast<int>(nh);  // apply partials: light CTAs, then heavy rows
+  // light rows go through the staged kernel when a round has at most 16 rows
+  // (Q >= 2); with one chunk per row its staging would not fit in shared memory
+  const int64_t nh = G->n_heavy, nm = Q >= 2 ? G->n_mid : G->n;
+  // apply partials: medium-row CTAs [0, grid), light-row CTAs [grid, 2 grid), heavy rows after
+  const int parts = 2 * grid + static_cast<int>(nh);
+  const int smem = kLzWarps * LzRound<Q>::WARP + 128;
+  static int s_attr[64] = {};  // the shared-memory limit, raised once per device
+  NDOS_CHECK(raise_smem_limit(reinterpret_cast<const void*>(k_lz_apply_light<Q>), s_attr, smem));
   for (int k = 0; k < m; ++k) {
     if (nh > 0) {
       k_lz_apply_heavy<Q><<<static_cast<unsigned>(nh), kLzThreads, 0, s>>>(
-          op, G->p_row_ptr, G->p_col, G->p_deg, nzp, w_cur, st.inv_b, y, st.part + static_cast<size_t>(grid) * nzp);
+          op, G->p_row_ptr, G->p_col, G->p_deg, nzp, w_cur, st.inv_b, y,
+          st.part + static_cast<size_t>(2 * grid) * nzp);
       NDOS_LAUNCHED();
     }
-    k_lz_apply<Q><<<grid, kLzThreads, 0, s>>>(op, G->p_row_ptr, G->p_col, G->p_deg, nh, G->n, nzp, w_cur, st.inv_b,
-                                             y, st.part);
+    k_lz_apply<Q><<<grid, kLzThreads, 0, s>>>(op, G->p_row_ptr, G->p_col, G->p_deg, nh, nm, nzp, w_cur, st.inv_b, y,
+                                             st.part);
     NDOS_LAUNCHED();
+    if (nm < G->n) {
+      k_lz_apply_light<Q><<<grid, kLzThreads, smem, s>>>(op, G->p_row_ptr, G->p_col, nm, G->n, nzp, w_cur, st.inv_b,
+                                                         y, st.part + static_cast<size_t>(grid) * nzp);
+      NDOS_LAUNCHED();
+    } else {
+      NDOS_CUDA(cudaMemsetAsync(st.part + static_cast<size_t>(grid) * nzp, 0, sizeof(double) * grid * nzp, s));
+    }
     k_lz_alpha<<<gp, 32, 0, s>>>(nz, nzp, m, k, parts, st);
     NDOS_LAUNCHED();
     k_lz_update<Q><<<grid, kLzThreads, 0, s>>>(op, G->p_deg, G->n, nzp, y, w_cur, w_pn, st.c1, st.c2, st.part);
@@ -530,7 +684,7 @@ int run_lanczos(const Graph* G, int op, int M, int Nz, uint64_t seed, double* al
   NDOS_CHECK(t.get(&y, n * nzp));
   NDOS_CHECK(t.get(&fl, 3 * nzp));
   NDOS_CHECK(t.get(&dbl, 2 * nzp));
-  NDOS_CHECK(t.get(&part, (static_cast<int64_t>(grid) + G->n_heavy) * nzp));
+  NDOS_CHECK(t.get(&part, (2 * static_cast<int64_t>(grid) + G->n_heavy) * nzp));
   LanczosState st{alpha_out, beta_out, steps_out, dbl, dbl + nzp, fl, fl + nzp, fl + 2 * nzp, part};
   NDOS_CUDA(cudaMemsetAsync(alpha_out, 0, sizeof(double) * Nz * M, s));
   NDOS_CUDA(cudaMemsetAsync(beta_out, 0, sizeof(double) * Nz * M, s));

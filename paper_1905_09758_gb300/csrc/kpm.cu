@@ -85,13 +85,16 @@ __global__ void k_fill_f32(float* __restrict__ p, int64_t n, int64_t stride, flo
 }
 
 // LDOS output of a chunk of moments [m0, m0 + cnt) from the step scratch
-// part[(m % ch) * tiles + t][k] (one row per tile): the tiles' values are
-// summed in tile order and written moment-major (out[m * n + k]) or
-// node-major (out[k * M + m], through a 32 x 32 shared-memory transpose so
-// both sides stay coalesced).  Block (32, 8).
+// part[(m % ch) * tiles + t][p] (one row per tile, indexed by the position p
+// of the degree-sorted order, so the steps' stores are coalesced): for every
+// compact node k the tiles' values at p = pos[k] are summed in tile order and
+// written moment-major (out[m * n + k]) or node-major (out[k * M + m], through
+// a 32 x 32 shared-memory transpose so the writes stay coalesced).
+// Block (32, 8).
 template <bool NODE_MAJOR>
-__global__ void __launch_bounds__(256) k_ldos_fold(const float* __restrict__ part, int tiles, int ch, int64_t n,
-                                                   int m0, int cnt, int M, float* __restrict__ out) {
+__global__ void __launch_bounds__(256) k_ldos_fold(const float* __restrict__ part, const int32_t* __restrict__ pos,
+                                                   int tiles, int ch, int64_t n, int m0, int cnt, int M,
+                                                   float* __restrict__ out) {
   __shared__ float tile_s[32][33];
   const int tx = threadIdx.x, ty = threadIdx.y;
   for (int64_t k0 = static_cast<int64_t>(blockIdx.x) * 32; k0 < n; k0 += static_cast<int64_t>(gridDim.x) * 32) {
@@ -101,7 +104,7 @@ __global__ void __launch_bounds__(256) k_ldos_fold(const float* __restrict__ par
         const int m = m0 + r0 + r;
         float v = 0.f;
         if (k < n && r0 + r < cnt) {
-          const float* src = part + static_cast<size_t>(m % ch) * tiles * n + k;
+          const float* src = part + static_cast<size_t>(m % ch) * tiles * n + pos[k];
           for (int t = 0; t < tiles; ++t) v += src[static_cast<size_t>(t) * n];
           if (!NODE_MAJOR) out[static_cast<size_t>(m) * n + k] = v;
         }
@@ -119,6 +122,20 @@ __global__ void __launch_bounds__(256) k_ldos_fold(const float* __restrict__ par
   }
 }
 
+
+static std::mutex g_smem_mu;
+
+int raise_smem_limit(const void* kernel, int* limits, int smem) {
+  int dev = 0;
+  NDOS_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(DOS_EINVAL, "device ordinal out of range");
+  std::lock_guard<std::mutex> lk(g_smem_mu);
+  if (smem > limits[dev]) {
+    NDOS_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    limits[dev] = smem;
+  }
+  return DOS_OK;
+}
 
 static int g_force_t = 0;  // 0 = planner's choice
 static int g_force_ctas = 0;  // light-row CTAs per SM, 0 = as many as fit
@@ -323,9 +340,9 @@ static int run_steps(const Graph* G, const Filter* F, const Plan& plan, int M, i
   const auto fold_chunk = [&](int m0, int cnt) {
     const unsigned blocks = static_cast<unsigned>(std::min<int64_t>((n + 31) / 32, 16LL * num_sms()));
     if (node_major)
-      k_ldos_fold<true><<<blocks, dim3(32, 8), 0, s>>>(lpart, plan.tiles, ch, n, m0, cnt, M, C_out);
+      k_ldos_fold<true><<<blocks, dim3(32, 8), 0, s>>>(lpart, G->compact_to_p, plan.tiles, ch, n, m0, cnt, M, C_out);
     else
-      k_ldos_fold<false><<<blocks, dim3(32, 8), 0, s>>>(lpart, plan.tiles, ch, n, m0, cnt, M, C_out);
+      k_ldos_fold<false><<<blocks, dim3(32, 8), 0, s>>>(lpart, G->compact_to_p, plan.tiles, ch, n, m0, cnt, M, C_out);
     count_launch();
     cu(cudaGetLastError(), "k_ldos_fold");
   };
@@ -354,6 +371,7 @@ static int run_steps(const Graph* G, const Filter* F, const Plan& plan, int M, i
   prm.inv_nz = 1.0f / static_cast<float>(Nz);
   prm.seed = seed;
   prm.ldos_tile_stride = fold && plan.tiles > 1 ? n : 0;
+  prm.ldos_by_position = fold ? 1 : 0;
   prm.op = op.kind;
   prm.op_c = static_cast<float>(op.c);
   prm.op_inv_r = static_cast<float>(op.inv_r);

@@ -131,54 +131,46 @@ __device__ __forceinline__ uint4 ld_stream(const uint4* p) { return __ldcs(p); }
 __device__ __forceinline__ void st_stream(uint4* p, const uint4& v) { __stcs(p, v); }
 __device__ __forceinline__ int32_t ld_col(const int32_t* p) { return __ldcs(p); }
 
-// ---- TMA bulk copies and mbarriers (inline PTX) ------------------------------
+// ---- asynchronous global -> shared copies (cp.async, inline PTX) ------------
+// Each lane copies 16-byte chunks straight into shared memory without going
+// through registers; a warp commits one group per work item and waits with
+// cp.async.wait_group, so no load of the CSR or of the streamed rows sits on
+// the critical path and no thread spins on a flag.
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
-__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-// Every wait is bounded: after kWaitLimitNs the caller gets false and must
-// record the failure and leave.
-constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = global_ns();
-  while (!mbar_try_wait(bar, parity))
-    if (global_ns() - t0 > kWaitLimitNs) return false;
-  return true;
-}
-// global -> shared bulk copy completing on `bar` (16-byte aligned, size % 16 == 0)
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_u32(dst)),
-               "l"(src), "r"(bytes), "r"(smem_u32(bar))
-               : "memory");
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// device error word codes (dos_device_status)
-constexpr int kErrWaitTimeout = 1;
+// copy `chunks` 16-byte chunks src -> dst, spread over the warp's lanes
+__device__ __forceinline__ void warp_copy16(unsigned char* dst, const unsigned char* src, int64_t chunks, int lane) {
+  for (int64_t k = lane; k < chunks; k += 32) cp_async16(dst + 16 * k, src + 16 * k);
+}
+
+// Per-thread sum of FP32 terms kept as an unevaluated pair hi + lo (Knuth's
+// TwoSum error-free transformation): about 48 significant bits from FP32
+// instructions, where FP64 adds would occupy GB300's narrow FP64 pipe.
+struct SumFF {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float s = hi + x;
+    const float bp = s - hi;
+    lo += (hi - (s - bp)) + (x - bp);
+    hi = s;
+  }
+  __device__ __forceinline__ double value() const { return static_cast<double>(hi) + static_cast<double>(lo); }
+};
+struct SumD {
+  double v = 0.0;
+  __device__ __forceinline__ void add(float x) { v += static_cast<double>(x); }
+  __device__ __forceinline__ double value() const { return v; }
+};
 
 struct StepParams {
   const int64_t* __restrict__ row_ptr;   // [n+1] degree-sorted CSR (allocation padded to n+3)
@@ -211,19 +203,19 @@ struct StepParams {
   // weight d_i)
   int op;
   float op_c, op_inv_r;
-  float* ldos;      // LDOS: this step's output row, indexed by compact id
+  float* ldos;      // LDOS: this step's output row
   int64_t ldos_tile_stride;  // tile j writes ldos + j * stride (0: a single tile)
+  int ldos_by_position;      // 1: rows indexed by position (scratch, coalesced), 0: by compact id (C_out)
   int* err;         // device error word
 };
 
 // Epilogue of one row: recurrence update, store, fused dots / LDOS.
 // Executed by all 32 lanes of a warp (the Q-lane reductions are warp
 // shuffles); `active` lanes own a row whose neighbour sum is in acc.
-template <typename T, int Q, int MODE>
+template <typename T, int Q, int MODE, typename ACC>
 __device__ __forceinline__ void step_epilogue(const StepParams& prm, bool active, int64_t p, int ql, int tile,
                                               const float* acc, const float* prev, const float* own, float fd,
-                                              uint32_t orig, int32_t compact, bool owner, double& dd0,
-                                              double& dd1) {
+                                              uint32_t orig, int32_t compact, bool owner, ACC& dd0, ACC& dd1) {
   constexpr int V = VecT<T>::N;
   constexpr int TW = Q * V;
   using MD = ModeOf<MODE>;
@@ -299,15 +291,16 @@ __device__ __forceinline__ void step_epilogue(const StepParams& prm, bool active
   if (active && owner) {
     if (!MD::ldos) {
       const float wd = MD::op ? 1.0f : fd;  // <V_a, V_b> = sum_i w_i <U_a, U_b>_i
-      dd0 += static_cast<double>(wd * prod0);
-      dd1 += static_cast<double>(wd * prod1);
+      dd0.add(wd * prod0);
+      dd1.add(wd * prod1);
     } else {
       // sum_j z_j (V_{k+1})_j of this tile (V = S^{-1} U on H, U on X~)
       const float vsum = MD::op ? prod0 : prod0 * sqrtf(fd);
-      dd0 += static_cast<double>(vsum);
+      dd0.add(vsum);
       // one plain store per (tile, node); several tiles are summed afterwards
       // in a fixed order (k_ldos_fold), so the result is reproducible
-      prm.ldos[static_cast<size_t>(tile) * prm.ldos_tile_stride + compact] = vsum * prm.inv_nz;
+      const int64_t k = prm.ldos_by_position ? p : static_cast<int64_t>(compact);
+      prm.ldos[static_cast<size_t>(tile) * prm.ldos_tile_stride + k] = vsum * prm.inv_nz;
     }
   }
 }
@@ -386,7 +379,7 @@ __global__ void __launch_bounds__(kStepThreads) k_cheb_heavy(const StepParams pr
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int slot = tid / Q, ql = tid % Q;
   const uint4* ubase = reinterpret_cast<const uint4*>(prm.u_cur) + static_cast<size_t>(tile) * prm.n * Q;
-  double dd0 = 0.0, dd1 = 0.0;
+  SumD dd0, dd1;
   for (int64_t p = blockIdx.x; p < prm.n_heavy; p += gridDim.x) {
     const int64_t beg = prm.row_ptr[p], end = prm.row_ptr[p + 1];
     // epilogue operands, loaded early by warp 0
@@ -442,95 +435,156 @@ __global__ void __launch_bounds__(kStepThreads) k_cheb_heavy(const StepParams pr
     }
     __syncthreads();
   }
-  block_sum2<kStepWarps>(dd0, dd1);
+  double a0 = dd0.value(), a1 = dd1.value();
+  block_sum2<kStepWarps>(a0, a1);
   if (threadIdx.x == 0) {
     const size_t i = static_cast<size_t>(tile) * gridDim.x + blockIdx.x;
-    prm.partial[i] = dd0;
-    if (!ModeOf<MODE>::ldos) prm.partial[prm.part_width + i] = dd1;
+    prm.partial[i] = a0;
+    if (!ModeOf<MODE>::ldos) prm.partial[prm.part_width + i] = a1;
   }
 }
 
 // ---------------------------------------------------------------------------
 // Medium rows (kMediumDeg <= degree < kHeavyDeg): a warp per row, 32/Q
-// neighbour slots; each block of 256 column indices is staged in the warp's
-// shared memory with coalesced loads before its gathers.  Grid (ctas, T).
+// neighbour slots.  A warp's rows are cut into chunks of kMediumCols column
+// indices; while it gathers for one chunk, its lanes have already issued the
+// cp.async copy of the next chunk (of this row or of its next row) into the
+// other shared-memory slot, and lane 0 keeps the CSR ranges of its next two
+// rows loaded, so no CSR load is on the warp's critical path.  Grid (ctas, T).
 // ---------------------------------------------------------------------------
-constexpr int kMediumCols = 256;  // staged indices per warp per block
+constexpr int kMediumCols = 256;                    // column indices per chunk
+constexpr int kMediumSlot = (kMediumCols + 8) * 4;  // a chunk rounded out to 16-byte copies
 
 template <typename T, int Q, int MODE>
 __global__ void __launch_bounds__(kStepThreads) k_cheb_medium(const StepParams prm) {
   constexpr int V = VecT<T>::N;
   constexpr int TW = Q * V;
   constexpr int PS = 32 / Q;  // neighbour slots per row
-  __shared__ int32_t s_col[kStepWarps][kMediumCols];
+  using MD = ModeOf<MODE>;
+  __shared__ __align__(16) unsigned char s_col[kStepWarps][2][kMediumSlot];
   const int tile = blockIdx.y;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int slot = lane / Q, ql = lane % Q;
   const uint4* ubase = reinterpret_cast<const uint4*>(prm.u_cur) + static_cast<size_t>(tile) * prm.n * Q;
-  double dd0 = 0.0, dd1 = 0.0;
-  const int64_t w0 = static_cast<int64_t>(blockIdx.x) * kStepWarps + warp;
+  SumD dd0, dd1;
   const int64_t nw = static_cast<int64_t>(gridDim.x) * kStepWarps;
-  for (int64_t p = prm.n_heavy + w0; p < prm.n_mid; p += nw) {
-    const int64_t beg = prm.row_ptr[p], end = prm.row_ptr[p + 1];
-    const size_t off = (static_cast<size_t>(tile) * prm.n + p) * TW + ql * V;
-    float prev[V], own[V];
-#pragma unroll
-    for (int v = 0; v < V; ++v) prev[v] = own[v] = 0.f;
+  const int64_t end_row = prm.n_mid;
+  // rows a (current), b (next) and c (after next) of this warp; lane 0 loads
+  // the CSR ranges, which are broadcast when a row moves up
+  int64_t pa = prm.n_heavy + static_cast<int64_t>(blockIdx.x) * kStepWarps + warp;
+  if (pa < end_row) {  // a warp without rows only joins the CTA reduction
+    int64_t pb = pa + nw, pc = pb + nw;
+    int64_t ba = 0, ea = 0, bb = 0, eb = 0, bc = 0, ec = 0;
+    if (lane == 0) {
+      ba = prm.row_ptr[pa];
+      ea = prm.row_ptr[pa + 1];
+      if (pb < end_row) {
+        bb = prm.row_ptr[pb];
+        eb = prm.row_ptr[pb + 1];
+      }
+      if (pc < end_row) {
+        bc = prm.row_ptr[pc];
+        ec = prm.row_ptr[pc + 1];
+      }
+    }
+    ba = __shfl_sync(0xffffffffu, ba, 0);
+    ea = __shfl_sync(0xffffffffu, ea, 0);
+    bb = __shfl_sync(0xffffffffu, bb, 0);
+    eb = __shfl_sync(0xffffffffu, eb, 0);
+    auto issue = [&](int sl, int64_t e0, int64_t e1) {
+      const int64_t ea4 = e0 & ~int64_t(3);
+      const int64_t hi = e0 + kMediumCols < e1 ? e0 + kMediumCols : e1;
+      warp_copy16(s_col[warp][sl], reinterpret_cast<const unsigned char*>(prm.col + ea4), (((hi + 3) & ~int64_t(3)) - ea4) >> 2,
+                  lane);
+    };
+    issue(0, ba, ea);
+    cp_async_commit();
+    int64_t ca = ba;  // start of the current chunk of row a
+    float acc[V], prev[V], own[V];
     uint32_t orig = 0;
     int32_t compact = 0;
-    if (!prm.first) unpack16<T>(ld_stream(reinterpret_cast<const uint4*>(reinterpret_cast<const T*>(prm.u_pn) + off)), prev);
-    if (ModeOf<MODE>::own)
-      unpack16<T>(ld_gather(reinterpret_cast<const uint4*>(reinterpret_cast<const T*>(prm.u_cur) + off)), own);
-    if (ModeOf<MODE>::ldos) {
-      orig = static_cast<uint32_t>(prm.orig[p]);
-      compact = prm.compact[p];
-    }
-    float acc[V];
-#pragma unroll
-    for (int v = 0; v < V; ++v) acc[v] = 0.f;
-    for (int64_t e0 = beg; e0 < end; e0 += kMediumCols) {
-#pragma unroll
-      for (int i = 0; i < kMediumCols / 32; ++i) {
-        const int64_t e = e0 + lane + 32 * i;
-        s_col[warp][lane + 32 * i] = e < end ? ld_col(prm.col + e) : 0;
+  #pragma unroll
+    for (int v = 0; v < V; ++v) acc[v] = prev[v] = own[v] = 0.f;
+    for (int it = 0;; ++it) {
+      const int s = it & 1;
+      const bool more = ca + kMediumCols < ea;  // row a has another chunk
+      if (more)
+        issue(s ^ 1, ca + kMediumCols, ea);
+      else if (pb < end_row)
+        issue(s ^ 1, bb, eb);
+      cp_async_commit();
+      if (ca == ba) {
+        // first chunk of row a: its epilogue operands, loaded now and used after the gathers
+        const size_t off = (static_cast<size_t>(tile) * prm.n + pa) * TW + ql * V;
+        if (!prm.first)
+          unpack16<T>(ld_stream(reinterpret_cast<const uint4*>(reinterpret_cast<const T*>(prm.u_pn) + off)), prev);
+        if (MD::own) unpack16<T>(ld_gather(reinterpret_cast<const uint4*>(reinterpret_cast<const T*>(prm.u_cur) + off)), own);
+        if (MD::ldos) {
+          orig = static_cast<uint32_t>(prm.orig[pa]);
+          compact = prm.compact[pa];
+        }
       }
+      cp_async_wait<1>();
       __syncwarp();
-      const int cnt = static_cast<int>(end - e0 < kMediumCols ? end - e0 : kMediumCols);
-      gather_list<T, Q, PS>(ubase, s_col[warp], cnt, slot, ql, acc);
-      __syncwarp();
+      const int cnt = static_cast<int>(ea - ca < kMediumCols ? ea - ca : kMediumCols);
+      gather_list<T, Q, PS>(ubase, reinterpret_cast<const int32_t*>(s_col[warp][s]) + (ca - (ca & ~int64_t(3))), cnt,
+                            slot, ql, acc);
+      __syncwarp();  // the slot is read; it is refilled next iteration
+      if (more) {
+        ca += kMediumCols;
+        continue;
+      }
+      // last chunk of row a: sum the slots and finish the row
+  #pragma unroll
+      for (int o = Q; o < 32; o <<= 1)
+  #pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], o);
+      step_epilogue<T, Q, MODE>(prm, true, pa, ql, tile, acc, prev, own, static_cast<float>(ea - ba), orig, compact,
+                                lane == 0, dd0, dd1);
+  #pragma unroll
+      for (int v = 0; v < V; ++v) acc[v] = prev[v] = own[v] = 0.f;
+      if (pb >= end_row) break;
+      // rows move up: a <- b, b <- c, c <- the next row (range loaded by lane 0)
+      pa = pb;
+      ba = bb;
+      ea = eb;
+      ca = ba;
+      pb = pc;
+      bb = __shfl_sync(0xffffffffu, bc, 0);
+      eb = __shfl_sync(0xffffffffu, ec, 0);
+      pc = pb + nw;
+      if (lane == 0 && pc < end_row) {
+        bc = prm.row_ptr[pc];
+        ec = prm.row_ptr[pc + 1];
+      }
     }
-#pragma unroll
-    for (int o = Q; o < 32; o <<= 1)
-#pragma unroll
-      for (int v = 0; v < V; ++v) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], o);
-    step_epilogue<T, Q, MODE>(prm, true, p, ql, tile, acc, prev, own, static_cast<float>(end - beg), orig, compact,
-                              lane == 0, dd0, dd1);
   }
-  block_sum2<kStepWarps>(dd0, dd1);
+  cp_async_wait<0>();
+  double a0 = dd0.value(), a1 = dd1.value();
+  block_sum2<kStepWarps>(a0, a1);
   if (threadIdx.x == 0) {
     const size_t i = static_cast<size_t>(prm.mid_part_off) + static_cast<size_t>(tile) * gridDim.x + blockIdx.x;
-    prm.partial[i] = dd0;
-    if (!ModeOf<MODE>::ldos) prm.partial[prm.part_width + i] = dd1;
+    prm.partial[i] = a0;
+    if (!MD::ldos) prm.partial[prm.part_width + i] = a1;
   }
 }
 
 // ---------------------------------------------------------------------------
 // Light rows (degree < kMediumDeg), the bulk of a sparse graph: every warp
-// runs its own two-slot TMA pipeline over "rounds" of R = 32/Q consecutive
-// rows (a group of Q lanes per row, one 16-byte chunk of the tile row each).
-// Work items (tile, round) are dealt to warps round-robin in tile-major
-// order.  While the warp gathers for item i, lane 0 has already issued the
-// bulk copies of item i+1 into the other slot: the row offsets, the column
-// indices, the U_{k-1} rows and the own U_k rows (DOS) or the original /
-// compact ids (LDOS), completing on the slot's mbarrier.  The row offsets of
-// item i+2 are loaded one iteration ahead, so no global load of the CSR or of
-// the streamed blocks is on the warp's critical path: only the gathers of
-// U_k rows are.
+// works through "rounds" of R = 32/Q consecutive rows (a group of Q lanes per
+// row, one 16-byte chunk of the tile row each).  Work items (tile, round) are
+// dealt to warps round-robin in tile-major order, so concurrently running
+// warps gather from one tile of U_k.  Each warp double-buffers its items in
+// shared memory: while it gathers for item i, its lanes have already issued
+// cp.async copies of item i+1's row offsets, column indices, U_{k-1} rows and
+// own U_k rows (DOS) or original / compact ids (LDOS) into the other slot,
+// and lane 0 has loaded the CSR range of item i+2.  So only the gathers of
+// neighbour rows of U_k are on the warp's critical path.
 // ---------------------------------------------------------------------------
 template <int Q, int ROWB, int MODE>
 struct RoundLayout {
-  static constexpr int R = 32 / Q;                                // rows per round
-  static constexpr int RP = (((R + 4) * 8) + 15) / 16 * 16;      // row offsets (rounded out to 16 B)
+  static constexpr int R = 32 / Q;                                 // rows per round
+  static constexpr int RP = (((R + 3) * 8) + 15) / 16 * 16;       // row offsets from an even row
   static constexpr int COL = ((R * (kMediumDeg - 1) + 8) * 4 + 15) / 16 * 16;
   static constexpr int BLK = R * ROWB;
   static constexpr int IDS = ((R + 8) * 4 + 15) / 16 * 16;
@@ -543,38 +597,26 @@ struct RoundLayout {
   static constexpr int WARP = 2 * SLOT;  // two slots per warp
 };
 
-__device__ __forceinline__ void fence_proxy_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
 template <typename T, int Q, int MODE>
 __global__ void __launch_bounds__(kStepThreads, 3) k_cheb_light(const StepParams prm) {
   constexpr int V = VecT<T>::N;
   constexpr int TW = Q * V;
   constexpr int ROWB = TW * static_cast<int>(sizeof(T));
   using L = RoundLayout<Q, ROWB, MODE>;
+  using MD = ModeOf<MODE>;
   constexpr int R = L::R;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ uint64_t bars[kStepWarps][2];
   unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int grp = lane / Q, ql = lane % Q;
   unsigned char* wbuf = smem + warp * L::WARP;
-  uint64_t* bar = bars[warp];
-  if (lane == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
-    mbar_fence_init();
-  }
-  __syncwarp();
   const int64_t light0 = prm.n_mid;
-  const int64_t n_light = prm.n - light0;
-  const int64_t n_rounds = (n_light + R - 1) / R;
-  const int64_t wid = static_cast<int64_t>(blockIdx.x) * kStepWarps + warp;
+  const int64_t n_rounds = (prm.n - light0 + R - 1) / R;
   const int64_t nwarps = static_cast<int64_t>(gridDim.x) * kStepWarps;
-  double dd0 = 0.0, dd1 = 0.0;
+  SumFF dd0, dd1;
 
-  // (tile, round) cursor advanced without divisions
+  // item it = (tile, round) = (it / n_rounds, it % n_rounds); a warp takes
+  // items wid, wid + nwarps, ...
   struct Cursor {
     int64_t round;
     int tile;
@@ -590,33 +632,43 @@ __global__ void __launch_bounds__(kStepThreads, 3) k_cheb_light(const StepParams
     r0 = light0 + c.round * R;
     r1 = r0 + R < prm.n ? r0 + R : prm.n;
   };
-  // lane 0: issue the bulk copies of an item into slot s (e0, e1 = its CSR range)
+  // the warp's lanes issue the copies of an item into slot s (e0, e1 = its CSR range)
   auto issue = [&](const Cursor& c, int s, int64_t e0, int64_t e1) {
     int64_t r0, r1;
     rows_of(c, r0, r1);
     unsigned char* sl = wbuf + s * L::SLOT;
     const int64_t r0a = r0 & ~int64_t(1), ea = e0 & ~int64_t(3), r0i = r0 & ~int64_t(3);
-    const uint32_t rp_bytes = static_cast<uint32_t>(((r1 + 2 - r0a) & ~int64_t(1)) * 8);
-    const uint32_t col_bytes = static_cast<uint32_t>((((e1 + 3) & ~int64_t(3)) - ea) * 4);
-    const uint32_t blk_bytes = static_cast<uint32_t>((r1 - r0) * ROWB);
-    const uint32_t id_bytes = static_cast<uint32_t>((((r1 + 3) & ~int64_t(3)) - r0i) * 4);
-    uint32_t tx = rp_bytes + col_bytes + (prm.first ? 0u : blk_bytes) + (ModeOf<MODE>::own ? blk_bytes : 0u) +
-                  (ModeOf<MODE>::ldos ? 2 * id_bytes : 0u);
-    mbar_arrive_expect_tx(&bar[s], tx);
+    warp_copy16(sl + L::off_rp, reinterpret_cast<const unsigned char*>(prm.row_ptr + r0a), (r1 + 2 - r0a) >> 1,
+                lane);
+    warp_copy16(sl + L::off_col, reinterpret_cast<const unsigned char*>(prm.col + ea),
+                (((e1 + 3) & ~int64_t(3)) - ea) >> 2, lane);
     const size_t row_off = (static_cast<size_t>(c.tile) * prm.n + r0) * TW;
-    bulk_g2s(sl + L::off_rp, prm.row_ptr + r0a, rp_bytes, &bar[s]);
-    bulk_g2s(sl + L::off_col, prm.col + ea, col_bytes, &bar[s]);
-    if (!prm.first) bulk_g2s(sl + L::off_prev, reinterpret_cast<const T*>(prm.u_pn) + row_off, blk_bytes, &bar[s]);
-    if (ModeOf<MODE>::own)
-      bulk_g2s(sl + L::off_aux, reinterpret_cast<const T*>(prm.u_cur) + row_off, blk_bytes, &bar[s]);
-    if (ModeOf<MODE>::ldos) {
-      bulk_g2s(sl + L::off_ids, prm.orig + r0i, id_bytes, &bar[s]);
-      bulk_g2s(sl + L::off_ids + L::IDS, prm.compact + r0i, id_bytes, &bar[s]);
+    const int64_t blk = (r1 - r0) * (ROWB / 16);
+    if (!prm.first)
+      warp_copy16(sl + L::off_prev, reinterpret_cast<const unsigned char*>(reinterpret_cast<const T*>(prm.u_pn) + row_off),
+                  blk, lane);
+    if (MD::own)
+      warp_copy16(sl + L::off_aux, reinterpret_cast<const unsigned char*>(reinterpret_cast<const T*>(prm.u_cur) + row_off),
+                  blk, lane);
+    if (MD::ldos) {
+      const int64_t ids = (((r1 + 3) & ~int64_t(3)) - r0i) >> 2;
+      warp_copy16(sl + L::off_ids, reinterpret_cast<const unsigned char*>(prm.orig + r0i), ids, lane);
+      warp_copy16(sl + L::off_ids + L::IDS, reinterpret_cast<const unsigned char*>(prm.compact + r0i), ids, lane);
+    }
+  };
+  // CSR range of an item, loaded by lane 0 and broadcast (one iteration early)
+  auto range_of = [&](const Cursor& c, int64_t& e0, int64_t& e1) {
+    e0 = e1 = 0;
+    if (lane == 0 && c.tile < prm.tiles) {
+      int64_t r0, r1;
+      rows_of(c, r0, r1);
+      e0 = prm.row_ptr[r0];
+      e1 = prm.row_ptr[r1];
     }
   };
 
   // cur = this iteration's item, nx1 = the next, nx2 = the one after
-  Cursor cur{wid, 0};
+  Cursor cur{static_cast<int64_t>(blockIdx.x) * kStepWarps + warp, 0};
   if (n_rounds == 0) cur.tile = prm.tiles;
   while (cur.tile < prm.tiles && cur.round >= n_rounds) {
     cur.round -= n_rounds;
@@ -626,43 +678,28 @@ __global__ void __launch_bounds__(kStepThreads, 3) k_cheb_light(const StepParams
   if (n_rounds > 0) advance(nx1);
   Cursor nx2 = nx1;
   if (n_rounds > 0) advance(nx2);
-  int64_t nb0 = 0, nb1 = 0;  // lane 0: CSR range of nx1
-  int64_t nn0 = 0, nn1 = 0;  // lane 0: CSR range of nx2
-  if (lane == 0 && cur.tile < prm.tiles) {
-    int64_t r0, r1;
-    rows_of(cur, r0, r1);
-    issue(cur, 0, prm.row_ptr[r0], prm.row_ptr[r1]);
-    if (nx1.tile < prm.tiles) {
-      rows_of(nx1, r0, r1);
-      nb0 = prm.row_ptr[r0];
-      nb1 = prm.row_ptr[r1];
-    }
+  int64_t nb0, nb1;  // CSR range of nx1 (lane 0)
+  {
+    int64_t e0, e1;
+    range_of(cur, e0, e1);
+    range_of(nx1, nb0, nb1);
+    e0 = __shfl_sync(0xffffffffu, e0, 0);
+    e1 = __shfl_sync(0xffffffffu, e1, 0);
+    if (cur.tile < prm.tiles) issue(cur, 0, e0, e1);
+    cp_async_commit();
   }
   for (int it = 0; cur.tile < prm.tiles; ++it) {
     const int s = it & 1;
-    // issue nx1 (range loaded one iteration ago), load the range of nx2
-    if (lane == 0 && nx1.tile < prm.tiles) {
-      fence_proxy_async_smem();
-      issue(nx1, s ^ 1, nb0, nb1);
-      if (nx2.tile < prm.tiles) {
-        int64_t r0, r1;
-        rows_of(nx2, r0, r1);
-        nn0 = prm.row_ptr[r0];
-        nn1 = prm.row_ptr[r1];
-      }
+    // issue nx1 into the other slot (its range was loaded one iteration ago),
+    // and load the range of nx2; one group is committed per iteration
+    {
+      const int64_t e0 = __shfl_sync(0xffffffffu, nb0, 0), e1 = __shfl_sync(0xffffffffu, nb1, 0);
+      if (nx1.tile < prm.tiles) issue(nx1, s ^ 1, e0, e1);
+      cp_async_commit();
+      range_of(nx2, nb0, nb1);
     }
-    // wait for this item's slot (bounded; lane 0 decides for the warp)
-    int ok = 1;
-    if (lane == 0) ok = mbar_wait(&bar[s], static_cast<uint32_t>((it >> 1) & 1)) ? 1 : 0;
-    ok = __shfl_sync(0xffffffffu, ok, 0);
-    if (!ok) {
-      if (lane == 0) {
-        atomicExch(prm.err, kErrWaitTimeout);
-        // leave only after the copies issued for the next item have landed
-        if (nx1.tile < prm.tiles) mbar_wait(&bar[s ^ 1], static_cast<uint32_t>(((it + 1) >> 1) & 1));
-      }
-      break;
-    }
+    cp_async_wait<1>();  // this item's group has landed (only nx1's may be pending)
+    __syncwarp();
     const int tile = cur.tile;
     int64_t r0, r1;
     rows_of(cur, r0, r1);
@@ -674,43 +711,41 @@ __global__ void __launch_bounds__(kStepThreads, 3) k_cheb_light(const StepParams
     const uint4* ubase = reinterpret_cast<const uint4*>(prm.u_cur) + static_cast<size_t>(tile) * prm.n * Q;
     const bool active = r0 + grp < r1;
     int64_t beg = 0, end = 0;
+    if (active) {
+      beg = rp[grp];
+      end = rp[grp + 1];
+    }
+    float acc[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[v] = 0.f;
+    gather_list<T, Q, 1>(ubase, cidx + (beg - ea), static_cast<int>(end - beg), 0, ql, acc);
     float prev[V], own[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) prev[v] = own[v] = 0.f;
     uint32_t orig = 0;
     int32_t compact = 0;
     if (active) {
-      beg = rp[grp];
-      end = rp[grp + 1];
       if (!prm.first) unpack16<T>(*reinterpret_cast<const uint4*>(sl + L::off_prev + grp * ROWB + ql * 16), prev);
-      if (ModeOf<MODE>::own)
-        unpack16<T>(*reinterpret_cast<const uint4*>(sl + L::off_aux + grp * ROWB + ql * 16), own);
-      if (ModeOf<MODE>::ldos) {
+      if (MD::own) unpack16<T>(*reinterpret_cast<const uint4*>(sl + L::off_aux + grp * ROWB + ql * 16), own);
+      if (MD::ldos) {
         orig = static_cast<uint32_t>(reinterpret_cast<const int32_t*>(sl + L::off_ids)[r0 + grp - r0i]);
         compact = reinterpret_cast<const int32_t*>(sl + L::off_ids + L::IDS)[r0 + grp - r0i];
       }
     }
-    float acc[V];
-#pragma unroll
-    for (int v = 0; v < V; ++v) acc[v] = 0.f;
-    gather_list<T, Q, 1>(ubase, cidx + (beg - ea), static_cast<int>(end - beg), 0, ql, acc);
     step_epilogue<T, Q, MODE>(prm, active, r0 + grp, ql, tile, acc, prev, own, static_cast<float>(end - beg), orig,
                               compact, ql == 0, dd0, dd1);
     __syncwarp();  // the slot is read; it is refilled next iteration
     cur = nx1;
     nx1 = nx2;
     if (n_rounds > 0) advance(nx2);
-    if (lane == 0) {
-      nb0 = nn0;
-      nb1 = nn1;
-    }
   }
-  // the loop consumed every item it issued; nothing is left in flight
-  block_sum2<kStepWarps>(dd0, dd1);
+  cp_async_wait<0>();  // the trailing groups are empty; nothing is left in flight
+  double a0 = dd0.value(), a1 = dd1.value();
+  block_sum2<kStepWarps>(a0, a1);
   if (threadIdx.x == 0) {
     const size_t i = static_cast<size_t>(prm.light_part_off) + blockIdx.x;
-    prm.partial[i] = dd0;
-    if (!ModeOf<MODE>::ldos) prm.partial[prm.part_width + i] = dd1;
+    prm.partial[i] = a0;
+    if (!MD::ldos) prm.partial[prm.part_width + i] = a1;
   }
 }
 
@@ -791,15 +826,17 @@ int light_smem() {
   return kStepWarps * RoundLayout<Q, Q * 16, MODE>::WARP + 128;
 }
 
+// Raise a kernel's dynamic shared-memory limit on the current device.  The
+// attribute belongs to the device's context, so the raised limit is kept per
+// device (and only grows, so earlier plans stay launchable).
+int raise_smem_limit(const void* kernel, int* limits /* [64], per device */, int smem);
+
 template <typename T, int Q, int MODE>
 int light_config_q(int* smem, int* ctas_per_sm) {
   *smem = light_smem<T, Q, MODE>();
-  static int s_limit = 0;  // the limit only grows, so earlier plans stay launchable
-  if (*smem > s_limit) {
-    cudaError_t e = cudaFuncSetAttribute(k_cheb_light<T, Q, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, *smem);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute", __FILE__, __LINE__);
-    s_limit = *smem;
-  }
+  static int s_limit[64] = {};
+  const int st = raise_smem_limit(reinterpret_cast<const void*>(k_cheb_light<T, Q, MODE>), s_limit, *smem);
+  if (st != DOS_OK) return st;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_cheb_light<T, Q, MODE>, kStepThreads, *smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor", __FILE__, __LINE__);
   return DOS_OK;

@@ -172,15 +172,75 @@ __global__ void k_init_params(float* __restrict__ w, int64_t n, int64_t w_end, f
   }
 }
 
-// x[g] = [B * hist[g][0..B), d[g][1..K)]
+// x[g] = [B * hist[g][0..B), d[g][1..K)] and, with stats (mean d, mean d^2,
+// max d, N Nz per graph), [log(mean d), log(mean d^2)/2 - log(mean d),
+// log(max d), log(N Nz)] / 10
 __global__ void k_features(const double* __restrict__ hist, int B, const double* __restrict__ d, int ld_d, int K,
-                           int64_t n_graphs, float* __restrict__ x) {
-  const int F = B + K - 1;
+                           const double* __restrict__ stats, int64_t n_graphs, float* __restrict__ x) {
+  const int F = B + K - 1 + (stats ? 4 : 0);
   const int64_t total = n_graphs * F;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t g = i / F;
     const int f = static_cast<int>(i - g * F);
-    x[i] = f < B ? static_cast<float>(B * hist[g * B + f]) : static_cast<float>(d[g * ld_d + (f - B + 1)]);
+    double v;
+    if (f < B) {
+      v = B * hist[g * B + f];
+    } else if (f < B + K - 1) {
+      v = d[g * ld_d + (f - B + 1)];
+    } else {
+      const double* st = stats + 4 * g;
+      switch (f - (B + K - 1)) {
+        case 0: v = log(st[0]); break;
+        case 1: v = 0.5 * log(st[1]) - log(st[0]); break;
+        case 2: v = log(st[2]); break;
+        default: v = log(st[3]); break;
+      }
+      v /= 10.0;
+    }
+    x[i] = static_cast<float>(v);
+  }
+}
+
+// one block: sum and sum of squares of the degrees (exact in 64-bit
+// integers), the largest degree; out = [sum / n, sumsq / n, max, n * nz]
+__global__ void __launch_bounds__(1024) k_degree_stats(const int32_t* __restrict__ deg, int64_t n, int nz,
+                                                        double* __restrict__ out) {
+  __shared__ unsigned long long s1[32], s2[32];
+  __shared__ int smax[32];
+  unsigned long long a = 0, b = 0;
+  int mx = 0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const unsigned long long v = static_cast<unsigned long long>(deg[i]);
+    a += v;
+    b += v * v;
+    mx = max(mx, deg[i]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) {
+    s1[w] = a;
+    s2[w] = b;
+    smax[w] = mx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    a = s1[0];
+    b = s2[0];
+    mx = smax[0];
+    for (int k = 1; k < static_cast<int>(blockDim.x >> 5); ++k) {
+      a += s1[k];
+      b += s2[k];
+      mx = max(mx, smax[k]);
+    }
+    out[0] = static_cast<double>(a) / static_cast<double>(n);
+    out[1] = static_cast<double>(b) / static_cast<double>(n);
+    out[2] = static_cast<double>(mx);
+    out[3] = static_cast<double>(n) * static_cast<double>(nz);
   }
 }
 
@@ -430,15 +490,27 @@ int dos_mlp_train_step(dos_mlp_t hh, const float* x, const float* t, const int32
 
 }  // extern "C"
 
-extern "C" int dos_mlp_features(const double* hist, int n_bins, const double* d, int ld_d, int K, int64_t n_graphs,
-                                float* x_out, void* stream) {
+extern "C" int dos_mlp_features(const double* hist, int n_bins, const double* d, int ld_d, int K,
+                                const double* stats, int64_t n_graphs, float* x_out, void* stream) {
   clear_error();
   if (!hist || !d || !x_out) return fail(DOS_EINVAL, "dos_mlp_features: null pointer");
   if (n_bins < 1 || K < 1 || ld_d < K || n_graphs < 1 || n_bins + K - 1 > (1 << 20))
     return fail(DOS_EINVAL, "dos_mlp_features: bad sizes");
-  const int64_t total = n_graphs * (n_bins + K - 1);
+  const int64_t total = n_graphs * (n_bins + K - 1 + (stats ? 4 : 0));
   const unsigned blocks = static_cast<unsigned>(std::min<int64_t>((total + 255) / 256, 152 * 16));
-  k_features<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(hist, n_bins, d, ld_d, K, n_graphs, x_out);
+  k_features<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(hist, n_bins, d, ld_d, K, stats, n_graphs,
+                                                                    x_out);
+  NDOS_LAUNCHED();
+  return DOS_OK;
+}
+
+extern "C" int dos_graph_stats(dos_graph_t g, int Nz, double* stats_out, void* stream) {
+  clear_error();
+  const Graph* G = reinterpret_cast<const Graph*>(g);
+  if (!G || !stats_out) return fail(DOS_EINVAL, "dos_graph_stats: null argument");
+  if (G->n < 1) return fail(DOS_EINVAL, "dos_graph_stats: graph has no edges");
+  if (Nz < 1) return fail(DOS_EINVAL, "dos_graph_stats: Nz must be >= 1");
+  k_degree_stats<<<1, 1024, 0, static_cast<cudaStream_t>(stream)>>>(G->deg, G->n, Nz, stats_out);
   NDOS_LAUNCHED();
   return DOS_OK;
 }

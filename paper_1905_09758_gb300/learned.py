@@ -2,8 +2,9 @@
 
 Not part of the paper's method: a small network (``dos_mlp_*``) maps the
 Jackson histogram and the first ``m_in`` moments of a cheap KPM run on the
-twin-filtered operator P^T H P (§3.4) to that operator's density over
-``bins`` equal bins of [-1, 1]; the filtered spike at 0 and the r/N scale are
+twin-filtered operator P^T H P (§3.4), with the graph's degree statistics
+(mean, spread, largest degree) and noise level (N * Nz), to that operator's
+density over ``bins`` equal bins of [-1, 1]; the filtered spike at 0 and the r/N scale are
 added afterwards exactly as for the plain filtered series.  It is trained on
 pairs (cheap run, accurate run: ``m_ref`` moments, ``nz_ref`` probes,
 independent seed) computed by the library on graphs of the family it will be
@@ -30,6 +31,7 @@ class Reconstructor:
     m_in: int
     nz_in: int
     bins: int
+    stats: bool = True  # degree statistics and noise level among the inputs
 
     @property
     def sizes(self):
@@ -44,12 +46,14 @@ def filtered_operator(src, dst, n_nodes: int, stream=None):
     return g, nd.dos_motif_filter(g, stream=stream)
 
 
-def features(g: nd.Graph, f: nd.Filter | None, m_in: int, nz_in: int, seed: int, bins: int,
+def features(g: nd.Graph, f: nd.Filter | None, m_in: int, nz_in: int, seed: int, bins: int, stats: bool = True,
              stream=None) -> torch.Tensor:
-    """Feature row (1, bins + m_in - 1) of a graph from a cheap filtered run."""
+    """Feature row (1, bins + m_in - 1 [+ 4]) of a graph from a cheap filtered
+    run (and its degree statistics when ``stats``)."""
     d = nd.dos_moments(g, m_in, nz_in, seed, filter=f, stream=stream)
     h = nd.dos_density(d, bins, stream=stream)
-    return nd.dos_mlp_features(h.view(1, bins), d.view(1, m_in), m_in, stream=stream)
+    st = nd.dos_graph_stats(g, nz_in, stream=stream).view(1, 4) if stats else None
+    return nd.dos_mlp_features(h.view(1, bins), d.view(1, m_in), m_in, stats=st, stream=stream)
 
 
 def target(g: nd.Graph, f: nd.Filter | None, m_ref: int, nz_ref: int, seed: int, bins: int,
@@ -62,13 +66,13 @@ def target(g: nd.Graph, f: nd.Filter | None, m_ref: int, nz_ref: int, seed: int,
 
 
 def training_set(graphs, m_in: int = 50, nz_in: int = 8, m_ref: int = 500, nz_ref: int = 256, bins: int = 200,
-                 seed: int = 0, stream=None):
+                 seed: int = 0, stats: bool = True, stream=None):
     """(X, T) for an iterable of edge lists (src, dst, n_nodes): one row per graph.
     Graph k uses input seed seed + 2k and reference seed seed + 2k + 1."""
     xs, ts = [], []
     for k, (src, dst, n) in enumerate(graphs):
         g, f = filtered_operator(src, dst, n, stream=stream)
-        xs.append(features(g, f, m_in, nz_in, seed + 2 * k, bins, stream=stream))
+        xs.append(features(g, f, m_in, nz_in, seed + 2 * k, bins, stats=stats, stream=stream))
         ts.append(target(g, f, m_ref, nz_ref, seed + 2 * k + 1, bins, stream=stream))
     return torch.cat(xs).contiguous(), torch.cat(ts).contiguous()
 
@@ -76,7 +80,8 @@ def training_set(graphs, m_in: int = 50, nz_in: int = 8, m_ref: int = 500, nz_re
 def train(x: torch.Tensor, t: torch.Tensor, m_in: int, nz_in: int, hidden=(512, 512), steps: int = 8000,
           batch: int = 256, lr: float = 1e-3, lr_min: float = 1e-5, seed: int = 0, stream=None) -> Reconstructor:
     """Adam on minibatches drawn uniformly with replacement, learning rate on a
-    cosine schedule from lr to lr_min."""
+    cosine schedule from lr to lr_min.  Whether the rows carry the degree
+    statistics is read from their width."""
     bins = t.shape[1]
     net = nd.dos_mlp_create([x.shape[1], *hidden, bins], seed=seed)
     gen = torch.Generator().manual_seed(seed)
@@ -84,7 +89,7 @@ def train(x: torch.Tensor, t: torch.Tensor, m_in: int, nz_in: int, hidden=(512, 
     for s in range(steps):
         rate = lr_min + 0.5 * (lr - lr_min) * (1.0 + math.cos(math.pi * s / steps))
         nd.dos_mlp_train_step(net, x, t, rate, idx=idx[s], stream=stream)
-    return Reconstructor(net, m_in, nz_in, bins)
+    return Reconstructor(net, m_in, nz_in, bins, stats=x.shape[1] == bins + m_in - 1 + 4)
 
 
 def reconstruct(rec: Reconstructor, g: nd.Graph, f: nd.Filter | None, seed: int, count_isolated: bool = True,
@@ -92,7 +97,7 @@ def reconstruct(rec: Reconstructor, g: nd.Graph, f: nd.Filter | None, seed: int,
     """Spectral histogram (float64 CUDA, rec.bins) of the whole graph: the
     network's density of the filtered operator scaled by r / N_total, plus the
     eigenvalues the filter removed (and isolated nodes at 0) as point masses."""
-    x = features(g, f, rec.m_in, rec.nz_in, seed, rec.bins, stream=stream)
+    x = features(g, f, rec.m_in, rec.nz_in, seed, rec.bins, stats=rec.stats, stream=stream)
     p = nd.dos_mlp_forward(rec.net, x, stream=stream)
     scale, spikes = nd.filtered_scale_and_spikes(g, f, count_isolated)
     return nd.dos_hist_assemble(p, scale=scale, spikes=spikes, stream=stream)[0]

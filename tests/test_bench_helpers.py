@@ -33,3 +33,18 @@ def test_unit_probe_diagonal_is_the_exact_ldos():
     sample = np.array([0, 3, 77, ref.n - 1])
     got = bench._unit_probe_diagonal(a, sample, 25)
     assert np.abs(got - oracle.exact_ldos(lam, q, 25)[sample]).max() <= 1e-12
+
+
+def test_cpu_sample_times_the_oracle_on_worker_processes():
+    """The CPU baseline's sample: the oracle's CSR shared with spawned workers
+    that split the probe columns; one timing per repetition."""
+    spec = dict(bench.CPU_SAMPLE, N=20_000, Nz=3)
+    cs = bench.CpuSample(spec)
+    try:
+        times = cs.run(2, 2)
+        assert len(times) == 2 and all(t > 0 for t in times)
+        assert cs.cores == min(3, len(os.sched_getaffinity(0)))
+        assert cs.bytes_per_step() == bench.step_bytes(cs.n, cs.nnz, 3, False)
+        assert "N=20,000" in cs.describe(2)
+    finally:
+        cs.close()

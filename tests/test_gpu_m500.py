@@ -11,15 +11,17 @@
   with twin leaves at M = 500, Nz = 64, seed 2025, against the oracle run on
   probe-column subsets in worker processes (Eq. (11) sums over probes).
 
-LDOS tolerance at m = 500, derived as for m = 100 in test_gpu_parity.py:
-every step rounds each stored entry with relative error u = 2^-24 ~ 6e-8,
-and the Chebyshev recurrence carries an error made at step s into step m with
-a factor |U_{m-s}| <= m - s + 1; errors of independent sign accumulate like a
-random walk, sqrt(sum_s (m - s + 1)^2) u ~ u m^1.5 / sqrt(3) = 3.9e-4 at
-m = 500 before the 1/Nz average over probes.  That estimate is the asserted
-per-entry bound (an FP32 emulation of the recurrence on the 6.6k-node graph
-reaches 7.1e-5 at m = 499; the error grows about as m^2 along the lambda = 1
-eigenvector, 2.8e-6 at m = 100).
+LDOS tolerance at m = 500: every step rounds each stored entry with relative
+error u = 2^-24 ~ 6e-8, and the Chebyshev recurrence carries an error made
+at step s into step m with a factor |U_{m-s}(x)| <= m - s + 1, reached at the
+eigenvalues x = +-1 (lambda = 1 is in every graph's spectrum, lambda = -1 in
+every bipartite component's).  Along those eigenvectors the errors of one
+probe add up coherently, sum_s (m - s + 1) u ~ u m^2 / 2, and the 1/Nz
+average over independent probes divides that by sqrt(Nz):
+u m^2 / (2 sqrt(Nz)) = 9.3e-4 at m = 500, Nz = 64, the asserted per-entry
+bound.  (The hub graph's star is bipartite and reaches 6.2e-4; the Chung-Lu
+graph 6.6e-5, where an FP32 emulation of the recurrence gives 7.1e-5.  At
+m = 100 the same bound is 3.7e-5 for Nz = 64.)
 """
 import numpy as np
 import pytest
@@ -33,7 +35,7 @@ pytestmark = pytest.mark.gpu
 nd = pytest.importorskip("paper_1905_09758_gb300")
 
 TOL_D = 1e-5
-TOL_C500 = 2.0**-24 * 500**1.5 / np.sqrt(3.0)  # 3.9e-4
+TOL_C500 = 2.0**-24 * 500**2 / (2.0 * np.sqrt(64.0))  # 9.3e-4
 M, NZ = 500, 64
 
 
@@ -85,7 +87,8 @@ def test_dos_moments_m500(name, filtered):
     d_ref = oracle.kpm_doubled(ref, z, M) / (r * NZ)
     err = np.abs(d - d_ref)
     print(f"{name} filtered={filtered} M=500: max |d - d_oracle| = {err.max():.2e}")
-    assert abs(d[0] - 1.0) < 1e-12
+    if not filtered:  # d_0 = ||Z||^2 / (N Nz) = 1 for +-1 probes; projected probes give 1 only in expectation
+        assert abs(d[0] - 1.0) < 1e-12
     assert err.max() <= TOL_D
 
 

@@ -289,9 +289,9 @@ def test_learned_reconstruct_assembles_filtered_density():
     g, f = learned.filtered_operator(torch.from_numpy(s), torch.from_numpy(d), n)
     m_in, bins = 20, 40
     net = nd.dos_mlp_create([bins + m_in - 1, 16, bins], seed=1)
-    rec = learned.Reconstructor(net, m_in, 4, bins)
+    rec = learned.Reconstructor(net, m_in, 4, bins, stats=False)
     h = learned.reconstruct(rec, g, f, seed=9).cpu().numpy()
-    x = learned.features(g, f, m_in, 4, 9, bins)
+    x = learned.features(g, f, m_in, 4, 9, bins, stats=False)
     dd = nd.dos_moments(g, m_in, 4, 9, filter=f).cpu().numpy()
     # the GPU histogram equals the oracle's to ~1e-12, so the float32 features
     # agree to one rounding
@@ -304,3 +304,25 @@ def test_learned_reconstruct_assembles_filtered_density():
     want = (ref.n - removed) / n_tot * p + oracle.point_mass_histogram([0.0], [(removed + ref.n_isolated) / n_tot], bins)
     assert np.abs(h - want).max() <= 1e-12
     assert abs(h.sum() - 1.0) <= 1e-6
+
+
+def test_degree_stats_and_stat_features_match_oracle():
+    """dos_graph_stats equals the oracle's degree statistics exactly (integer
+    sums), and the feature rows with them agree with the oracle's definition
+    to float32 rounding."""
+    from paper_1905_09758_gb300 import learned
+
+    s, d, n = sg.add_twin_leaves(*sg.chung_lu(4000, 2.3, 9.0, 15), 80, 16)
+    n += 5
+    ref = oracle.build_csr(s, d, n)
+    g, f = learned.filtered_operator(torch.from_numpy(s), torch.from_numpy(d), n)
+    for nz in (1, 8, 64):
+        st = nd.dos_graph_stats(g, nz).cpu().numpy()
+        assert np.array_equal(st, oracle.graph_stats(ref.deg, nz)), (st, oracle.graph_stats(ref.deg, nz))
+    m_in, bins = 12, 30
+    x = learned.features(g, f, m_in, 8, 4, bins).cpu().numpy()[0]
+    assert x.shape == (bins + m_in - 1 + 4,)
+    dd = nd.dos_moments(g, m_in, 8, 4, filter=f).cpu().numpy()
+    x_ref = oracle.mlp_features(oracle.histogram(dd, bins)[None], dd[None], m_in,
+                                stats=[oracle.graph_stats(ref.deg, 8)])[0]
+    assert np.all(np.abs(x - x_ref) <= 2 * U * np.maximum(np.abs(x_ref), 1e-3))
