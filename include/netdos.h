@@ -719,11 +719,13 @@ int dos_get_plan(dos_graph_t g, int Nz, int prec, int* tile_width,
                  int* ctas_per_sm, int* tiles, int* grid_x);
 
 /* Failure detection, not in the paper. Status of the device-side error word of
- * the current device: the step kernels' waits on their shared-memory pipeline
- * are bounded (2 s); if one gives up, the kernel records it, leaves, and the
- * affected call's moments are NaN.  Synchronises `stream`, returns the word in
- * *status (0 = none; may be NULL) and clears it.  Returns DOS_ETIMEOUT if a
- * wait gave up, else DOS_OK. */
+ * the current device.  A kernel that gives up on a bounded wait records it
+ * there, and the moments of a call that saw a non-zero word are NaN.  The
+ * current step kernels stage their data with cp.async groups and wait with
+ * cp.async.wait_group only (no spin on a flag or an mbarrier), so no kernel
+ * of this library writes the word; it is kept for the ABI.  Synchronises
+ * `stream`, returns the word in *status (0 = none; may be NULL) and clears
+ * it.  Returns DOS_ETIMEOUT if the word was set, else DOS_OK. */
 int dos_device_status(void* stream, int* status);
 
 /* Instrumentation, not in the paper. Number of kernels this library has

@@ -142,7 +142,8 @@ static int g_force_ctas = 0;  // light-row CTAs per SM, 0 = as many as fit
 
 static int elem_size(int prec) { return prec == DOS_FP32 ? 4 : 2; }
 
-// error word written by the step kernels' bounded waits (one per device)
+// device error word (one per device): set by a kernel that gives up on a
+// bounded wait; the current step kernels have no such wait, so it stays 0
 __device__ int g_step_err;
 static std::mutex g_err_mu;
 static int* g_err_addr[64] = {};
@@ -328,13 +329,17 @@ static int run_steps(const Graph* G, const Filter* F, const Plan& plan, int M, i
   // LDOS output.  One tile and the moment-major layout: every step stores
   // its row of C_out directly.  Otherwise the steps store one row per tile
   // into a scratch of `ch` moments, and k_ldos_fold sums the tiles in a fixed
-  // order into the requested layout once a chunk of moments is complete.
+  // order into the requested layout once a chunk of moments is complete:
+  // after every step for the moment-major layout (the scratch, tiles x N
+  // floats, stays in L2 and its rows are written out coalesced), after up to
+  // 32 steps for the node-major one (each node's run of moments is then one
+  // contiguous write).
   const bool node_major = layout == 1;
   const bool fold = ldos && (plan.tiles > 1 || node_major);
   int ch = 1;
   if (fold && st == DOS_OK) {
     const double row = 4.0 * static_cast<double>(n) * plan.tiles;
-    ch = static_cast<int>(std::max(1.0, std::min(32.0, std::floor(256.0e6 / row))));
+    ch = node_major ? static_cast<int>(std::max(1.0, std::min(32.0, std::floor(256.0e6 / row)))) : 1;
     st = dalloc_t(&lpart, static_cast<size_t>(ch) * plan.tiles * n, s);
   }
   const auto fold_chunk = [&](int m0, int cnt) {

@@ -300,7 +300,7 @@ __device__ __forceinline__ void step_epilogue(const StepParams& prm, bool active
       // one plain store per (tile, node); several tiles are summed afterwards
       // in a fixed order (k_ldos_fold), so the result is reproducible
       const int64_t k = prm.ldos_by_position ? p : static_cast<int64_t>(compact);
-      prm.ldos[static_cast<size_t>(tile) * prm.ldos_tile_stride + k] = vsum * prm.inv_nz;
+      __stcs(prm.ldos + static_cast<size_t>(tile) * prm.ldos_tile_stride + k, vsum * prm.inv_nz);  // evict first
     }
   }
 }
@@ -446,126 +446,66 @@ __global__ void __launch_bounds__(kStepThreads) k_cheb_heavy(const StepParams pr
 
 // ---------------------------------------------------------------------------
 // Medium rows (kMediumDeg <= degree < kHeavyDeg): a warp per row, 32/Q
-// neighbour slots.  A warp's rows are cut into chunks of kMediumCols column
-// indices; while it gathers for one chunk, its lanes have already issued the
-// cp.async copy of the next chunk (of this row or of its next row) into the
-// other shared-memory slot, and lane 0 keeps the CSR ranges of its next two
-// rows loaded, so no CSR load is on the warp's critical path.  Grid (ctas, T).
+// neighbour slots; each block of 256 column indices is staged in the warp's
+// shared memory with coalesced loads before its gathers.  Grid (ctas, T).
 // ---------------------------------------------------------------------------
-constexpr int kMediumCols = 256;                    // column indices per chunk
-constexpr int kMediumSlot = (kMediumCols + 8) * 4;  // a chunk rounded out to 16-byte copies
+constexpr int kMediumCols = 256;  // staged indices per warp per block
 
 template <typename T, int Q, int MODE>
 __global__ void __launch_bounds__(kStepThreads) k_cheb_medium(const StepParams prm) {
   constexpr int V = VecT<T>::N;
   constexpr int TW = Q * V;
   constexpr int PS = 32 / Q;  // neighbour slots per row
-  using MD = ModeOf<MODE>;
-  __shared__ __align__(16) unsigned char s_col[kStepWarps][2][kMediumSlot];
+  __shared__ int32_t s_col[kStepWarps][kMediumCols];
   const int tile = blockIdx.y;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int slot = lane / Q, ql = lane % Q;
   const uint4* ubase = reinterpret_cast<const uint4*>(prm.u_cur) + static_cast<size_t>(tile) * prm.n * Q;
   SumD dd0, dd1;
+  const int64_t w0 = static_cast<int64_t>(blockIdx.x) * kStepWarps + warp;
   const int64_t nw = static_cast<int64_t>(gridDim.x) * kStepWarps;
-  const int64_t end_row = prm.n_mid;
-  // rows a (current), b (next) and c (after next) of this warp; lane 0 loads
-  // the CSR ranges, which are broadcast when a row moves up
-  int64_t pa = prm.n_heavy + static_cast<int64_t>(blockIdx.x) * kStepWarps + warp;
-  if (pa < end_row) {  // a warp without rows only joins the CTA reduction
-    int64_t pb = pa + nw, pc = pb + nw;
-    int64_t ba = 0, ea = 0, bb = 0, eb = 0, bc = 0, ec = 0;
-    if (lane == 0) {
-      ba = prm.row_ptr[pa];
-      ea = prm.row_ptr[pa + 1];
-      if (pb < end_row) {
-        bb = prm.row_ptr[pb];
-        eb = prm.row_ptr[pb + 1];
-      }
-      if (pc < end_row) {
-        bc = prm.row_ptr[pc];
-        ec = prm.row_ptr[pc + 1];
-      }
-    }
-    ba = __shfl_sync(0xffffffffu, ba, 0);
-    ea = __shfl_sync(0xffffffffu, ea, 0);
-    bb = __shfl_sync(0xffffffffu, bb, 0);
-    eb = __shfl_sync(0xffffffffu, eb, 0);
-    auto issue = [&](int sl, int64_t e0, int64_t e1) {
-      const int64_t ea4 = e0 & ~int64_t(3);
-      const int64_t hi = e0 + kMediumCols < e1 ? e0 + kMediumCols : e1;
-      warp_copy16(s_col[warp][sl], reinterpret_cast<const unsigned char*>(prm.col + ea4), (((hi + 3) & ~int64_t(3)) - ea4) >> 2,
-                  lane);
-    };
-    issue(0, ba, ea);
-    cp_async_commit();
-    int64_t ca = ba;  // start of the current chunk of row a
-    float acc[V], prev[V], own[V];
+  for (int64_t p = prm.n_heavy + w0; p < prm.n_mid; p += nw) {
+    const int64_t beg = prm.row_ptr[p], end = prm.row_ptr[p + 1];
+    const size_t off = (static_cast<size_t>(tile) * prm.n + p) * TW + ql * V;
+    float prev[V], own[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) prev[v] = own[v] = 0.f;
     uint32_t orig = 0;
     int32_t compact = 0;
-  #pragma unroll
-    for (int v = 0; v < V; ++v) acc[v] = prev[v] = own[v] = 0.f;
-    for (int it = 0;; ++it) {
-      const int s = it & 1;
-      const bool more = ca + kMediumCols < ea;  // row a has another chunk
-      if (more)
-        issue(s ^ 1, ca + kMediumCols, ea);
-      else if (pb < end_row)
-        issue(s ^ 1, bb, eb);
-      cp_async_commit();
-      if (ca == ba) {
-        // first chunk of row a: its epilogue operands, loaded now and used after the gathers
-        const size_t off = (static_cast<size_t>(tile) * prm.n + pa) * TW + ql * V;
-        if (!prm.first)
-          unpack16<T>(ld_stream(reinterpret_cast<const uint4*>(reinterpret_cast<const T*>(prm.u_pn) + off)), prev);
-        if (MD::own) unpack16<T>(ld_gather(reinterpret_cast<const uint4*>(reinterpret_cast<const T*>(prm.u_cur) + off)), own);
-        if (MD::ldos) {
-          orig = static_cast<uint32_t>(prm.orig[pa]);
-          compact = prm.compact[pa];
-        }
-      }
-      cp_async_wait<1>();
-      __syncwarp();
-      const int cnt = static_cast<int>(ea - ca < kMediumCols ? ea - ca : kMediumCols);
-      gather_list<T, Q, PS>(ubase, reinterpret_cast<const int32_t*>(s_col[warp][s]) + (ca - (ca & ~int64_t(3))), cnt,
-                            slot, ql, acc);
-      __syncwarp();  // the slot is read; it is refilled next iteration
-      if (more) {
-        ca += kMediumCols;
-        continue;
-      }
-      // last chunk of row a: sum the slots and finish the row
-  #pragma unroll
-      for (int o = Q; o < 32; o <<= 1)
-  #pragma unroll
-        for (int v = 0; v < V; ++v) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], o);
-      step_epilogue<T, Q, MODE>(prm, true, pa, ql, tile, acc, prev, own, static_cast<float>(ea - ba), orig, compact,
-                                lane == 0, dd0, dd1);
-  #pragma unroll
-      for (int v = 0; v < V; ++v) acc[v] = prev[v] = own[v] = 0.f;
-      if (pb >= end_row) break;
-      // rows move up: a <- b, b <- c, c <- the next row (range loaded by lane 0)
-      pa = pb;
-      ba = bb;
-      ea = eb;
-      ca = ba;
-      pb = pc;
-      bb = __shfl_sync(0xffffffffu, bc, 0);
-      eb = __shfl_sync(0xffffffffu, ec, 0);
-      pc = pb + nw;
-      if (lane == 0 && pc < end_row) {
-        bc = prm.row_ptr[pc];
-        ec = prm.row_ptr[pc + 1];
-      }
+    if (!prm.first) unpack16<T>(ld_stream(reinterpret_cast<const uint4*>(reinterpret_cast<const T*>(prm.u_pn) + off)), prev);
+    if (ModeOf<MODE>::own)
+      unpack16<T>(ld_gather(reinterpret_cast<const uint4*>(reinterpret_cast<const T*>(prm.u_cur) + off)), own);
+    if (ModeOf<MODE>::ldos) {
+      orig = static_cast<uint32_t>(prm.orig[p]);
+      compact = prm.compact[p];
     }
+    float acc[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[v] = 0.f;
+    for (int64_t e0 = beg; e0 < end; e0 += kMediumCols) {
+#pragma unroll
+      for (int i = 0; i < kMediumCols / 32; ++i) {
+        const int64_t e = e0 + lane + 32 * i;
+        s_col[warp][lane + 32 * i] = e < end ? ld_col(prm.col + e) : 0;
+      }
+      __syncwarp();
+      const int cnt = static_cast<int>(end - e0 < kMediumCols ? end - e0 : kMediumCols);
+      gather_list<T, Q, PS>(ubase, s_col[warp], cnt, slot, ql, acc);
+      __syncwarp();
+    }
+#pragma unroll
+    for (int o = Q; o < 32; o <<= 1)
+#pragma unroll
+      for (int v = 0; v < V; ++v) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], o);
+    step_epilogue<T, Q, MODE>(prm, true, p, ql, tile, acc, prev, own, static_cast<float>(end - beg), orig, compact,
+                              lane == 0, dd0, dd1);
   }
-  cp_async_wait<0>();
   double a0 = dd0.value(), a1 = dd1.value();
   block_sum2<kStepWarps>(a0, a1);
   if (threadIdx.x == 0) {
     const size_t i = static_cast<size_t>(prm.mid_part_off) + static_cast<size_t>(tile) * gridDim.x + blockIdx.x;
     prm.partial[i] = a0;
-    if (!MD::ldos) prm.partial[prm.part_width + i] = a1;
+    if (!ModeOf<MODE>::ldos) prm.partial[prm.part_width + i] = a1;
   }
 }
 

@@ -201,15 +201,18 @@ __global__ void k_features(const double* __restrict__ hist, int B, const double*
   }
 }
 
-// one block: sum and sum of squares of the degrees (exact in 64-bit
-// integers), the largest degree; out = [sum / n, sumsq / n, max, n * nz]
-__global__ void __launch_bounds__(1024) k_degree_stats(const int32_t* __restrict__ deg, int64_t n, int nz,
-                                                        double* __restrict__ out) {
+// degree statistics in two passes: every block reduces a grid-stride share
+// of the degrees to (sum, sum of squares, max) -- exact in 64-bit integers,
+// so the order of the additions does not matter -- and one block combines
+// the blocks' triples into out = [sum / n, sumsq / n, max, n * nz]
+__global__ void __launch_bounds__(1024) k_degree_partials(const int32_t* __restrict__ deg, int64_t n,
+                                                          unsigned long long* __restrict__ part) {
   __shared__ unsigned long long s1[32], s2[32];
   __shared__ int smax[32];
   unsigned long long a = 0, b = 0;
   int mx = 0;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const unsigned long long v = static_cast<unsigned long long>(deg[i]);
     a += v;
     b += v * v;
@@ -229,19 +232,30 @@ __global__ void __launch_bounds__(1024) k_degree_stats(const int32_t* __restrict
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    a = s1[0];
-    b = s2[0];
-    mx = smax[0];
     for (int k = 1; k < static_cast<int>(blockDim.x >> 5); ++k) {
-      a += s1[k];
-      b += s2[k];
-      mx = max(mx, smax[k]);
+      s1[0] += s1[k];
+      s2[0] += s2[k];
+      smax[0] = max(smax[0], smax[k]);
     }
-    out[0] = static_cast<double>(a) / static_cast<double>(n);
-    out[1] = static_cast<double>(b) / static_cast<double>(n);
-    out[2] = static_cast<double>(mx);
-    out[3] = static_cast<double>(n) * static_cast<double>(nz);
+    part[3 * blockIdx.x] = s1[0];
+    part[3 * blockIdx.x + 1] = s2[0];
+    part[3 * blockIdx.x + 2] = static_cast<unsigned long long>(smax[0]);
   }
+}
+
+__global__ void k_degree_stats(const unsigned long long* __restrict__ part, int blocks, int64_t n, int nz,
+                               double* __restrict__ out) {
+  if (threadIdx.x != 0) return;
+  unsigned long long a = 0, b = 0, mx = 0;
+  for (int k = 0; k < blocks; ++k) {
+    a += part[3 * k];
+    b += part[3 * k + 1];
+    mx = part[3 * k + 2] > mx ? part[3 * k + 2] : mx;
+  }
+  out[0] = static_cast<double>(a) / static_cast<double>(n);
+  out[1] = static_cast<double>(b) / static_cast<double>(n);
+  out[2] = static_cast<double>(mx);
+  out[3] = static_cast<double>(n) * static_cast<double>(nz);
 }
 
 // warp per graph: t[g][b] = max(h, 0) / sum max(h, 0), uniform if the sum is 0
@@ -510,7 +524,14 @@ extern "C" int dos_graph_stats(dos_graph_t g, int Nz, double* stats_out, void* s
   if (!G || !stats_out) return fail(DOS_EINVAL, "dos_graph_stats: null argument");
   if (G->n < 1) return fail(DOS_EINVAL, "dos_graph_stats: graph has no edges");
   if (Nz < 1) return fail(DOS_EINVAL, "dos_graph_stats: Nz must be >= 1");
-  k_degree_stats<<<1, 1024, 0, static_cast<cudaStream_t>(stream)>>>(G->deg, G->n, Nz, stats_out);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int blocks = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((G->n + 1023) / 1024, 2LL * num_sms())));
+  Temps t(s);
+  unsigned long long* part = nullptr;
+  NDOS_CHECK(t.get(&part, static_cast<size_t>(3) * blocks));
+  k_degree_partials<<<blocks, 1024, 0, s>>>(G->deg, G->n, part);
+  NDOS_LAUNCHED();
+  k_degree_stats<<<1, 32, 0, s>>>(part, blocks, G->n, Nz, stats_out);
   NDOS_LAUNCHED();
   return DOS_OK;
 }
