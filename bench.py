@@ -1444,6 +1444,153 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+# A plain gather kernel that measures this GPU's row-gather ceilings, the
+# reference for what bounds the Chebyshev step: rows of 32-256 bytes gathered
+# with 16-byte loads (8 in flight per lane) from a 67 MB (L2-resident) and a
+# 4.3 GB table, indices uniform or drawn with the Chung-Lu endpoint law of the
+# degree-sorted order, at 4 and 8 CTAs of 256 threads per SM, and for the
+# large table under each L2 fetch granularity.  Every index is in range and
+# nothing waits.
+GATHER_CEILING_CU = r"""
+#include <cstdio>
+#include <cstdlib>
+#include <cstdint>
+#include <cmath>
+#include <cuda_runtime.h>
+
+#define CK(x) do { cudaError_t e = (x); if (e != cudaSuccess) { printf("CUDA %s at %d: %s\n", #x, __LINE__, cudaGetErrorString(e)); exit(1);} } while (0)
+
+__device__ __forceinline__ uint64_t mix(uint64_t z) {
+  z += 0x9e3779b97f4a7c15ull;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+__global__ void k_idx(int32_t* idx, int64_t L, int64_t n_rows, int skew) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < L; i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t h = mix((uint64_t)i * 7919ull + 17ull);
+    double u = (double)(h >> 11) * (1.0 / 9007199254740992.0);
+    int64_t r;
+    if (!skew) {
+      r = (int64_t)(u * (double)n_rows);
+    } else {
+      const double a = cbrt(10.0), b = cbrt((double)n_rows + 10.0);
+      double x = u * (b - a) + a;
+      r = (int64_t)(x * x * x - 10.0);
+    }
+    if (r < 0) r = 0;
+    if (r >= n_rows) r = n_rows - 1;
+    idx[i] = (int32_t)r;
+  }
+}
+
+template <int Q>
+__global__ void __launch_bounds__(256) k_gather(const uint4* __restrict__ tab, const int32_t* __restrict__ idx,
+                                                int64_t L, float* out) {
+  constexpr int G = 32 / Q;
+  const int lane = threadIdx.x & 31, ql = lane % Q, grp = lane / Q;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  float acc = 0.f;
+  // each warp takes chunks of 8*G consecutive gathers
+  for (int64_t c = warp * 8 * G; c < L; c += nwarps * 8 * G) {
+    uint4 r[8];
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+      const int64_t i = c + v * G + grp;
+      r[v] = i < L ? __ldg(tab + (size_t)idx[i] * Q + ql) : make_uint4(0, 0, 0, 0);
+    }
+#pragma unroll
+    for (int v = 0; v < 8; ++v)
+      acc += __uint_as_float(r[v].x) + __uint_as_float(r[v].y) + __uint_as_float(r[v].z) + __uint_as_float(r[v].w);
+  }
+  out[blockIdx.x * (int64_t)blockDim.x + threadIdx.x] = acc;
+}
+
+template <int Q>
+float run(const uint4* tab, const int32_t* idx, int64_t L, float* out, int grid) {
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  k_gather<Q><<<grid, 256>>>(tab, idx, L, out);
+  CK(cudaGetLastError());
+  CK(cudaDeviceSynchronize());
+  float best = 1e30f;
+  for (int rep = 0; rep < 5; ++rep) {
+    CK(cudaEventRecord(a));
+    k_gather<Q><<<grid, 256>>>(tab, idx, L, out);
+    CK(cudaEventRecord(b));
+    CK(cudaEventSynchronize(b));
+    float ms;
+    CK(cudaEventElapsedTime(&ms, a, b));
+    if (ms < best) best = ms;
+  }
+  CK(cudaEventDestroy(a));
+  CK(cudaEventDestroy(b));
+  return best;
+}
+
+int main(int argc, char** argv) {
+  int sms = 0;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0));
+  const size_t tab_max = 4ull << 30;  // 4 GiB table
+  const int64_t L = 256ll << 20;      // 256 Mi gathers
+  uint4* tab;
+  int32_t* idx;
+  float* out;
+  CK(cudaMalloc(&tab, tab_max));
+  CK(cudaMemset(tab, 0, tab_max));
+  CK(cudaMalloc(&idx, L * 4));
+  CK(cudaMalloc(&out, (size_t)sms * 16 * 256 * 4));
+  const size_t sizes[] = {64ull << 20, 4ull << 30};
+  const int fetch[] = {0, 32, 64, 128};
+  for (int fi = 0; fi < 4; ++fi) {
+    if (fetch[fi]) CK(cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, fetch[fi]));
+    size_t cur = 0;
+    CK(cudaDeviceGetLimit(&cur, cudaLimitMaxL2FetchGranularity));
+    for (size_t tb : sizes) {
+      if (tb < (1ull << 30) && fi > 0) continue;
+      for (int skew = 0; skew < 2; ++skew) {
+        for (int rb = 32; rb <= 256; rb *= 2) {
+          const int64_t n_rows = (int64_t)(tb / rb);
+          k_idx<<<sms * 8, 256>>>(idx, L, n_rows, skew);
+          CK(cudaGetLastError());
+          for (int cps = 4; cps <= 8; cps *= 2) {
+            const int grid = sms * cps;
+            float ms = 0;
+            switch (rb) {
+              case 32: ms = run<2>(tab, idx, L, out, grid); break;
+              case 64: ms = run<4>(tab, idx, L, out, grid); break;
+              case 128: ms = run<8>(tab, idx, L, out, grid); break;
+              default: ms = run<16>(tab, idx, L, out, grid); break;
+            }
+            printf("fetch=%zu table=%6.0fMB skew=%d rb=%3d ctas/sm=%d: %.3f ms  %.1f Mrows/ms  %.2f TB/s rows\n", cur,
+                   tb / 1e6, skew, rb, cps, ms, L / ms / 1e6, (double)L * rb / ms / 1e9);
+          }
+        }
+      }
+    }
+  }
+  return 0;
+}
+"""
+
+
+def gather_ceiling():
+    """Compile and run GATHER_CEILING_CU (nvcc, sm_103a); print its lines."""
+    import shutil
+    import tempfile
+
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    with tempfile.TemporaryDirectory() as d:
+        cu, exe = os.path.join(d, "gather_ceiling.cu"), os.path.join(d, "gather_ceiling")
+        with open(cu, "w") as f:
+            f.write(GATHER_CEILING_CU)
+        subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-o", exe, cu], check=True)
+        subprocess.run([exe], check=True)
+
+
 def profile_step(args):
     """The headline step alone, for ncu launch lists and counter captures: the
     workload's CSR build, filter, M = 200 KPM and density, and the M = 50
@@ -1522,6 +1669,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--gather-ceiling", action="store_true",
+                    help="measure this GPU's random row-gather ceilings with a plain gather kernel and exit")
     ap.add_argument("--profile-step", action="store_true",
                     help="run only the headline step (untrained network, no timing), for ncu captures")
     ap.add_argument("--profile-nodes", type=int, default=0,
@@ -1543,9 +1692,11 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--ref-steps-per-sample", type=int, default=2)
     args = ap.parse_args()
-    if args.warmup < 3 and args.impl == "ours" and not (args.profile_step or args.side_kernels):
+    if args.warmup < 3 and args.impl == "ours" and not (args.profile_step or args.side_kernels or args.gather_ceiling):
         ap.error("--warmup must be >= 3")
-    if args.profile_step:
+    if args.gather_ceiling:
+        gather_ceiling()
+    elif args.profile_step:
         profile_step(args)
     elif args.side_kernels:
         side_kernels()

@@ -86,42 +86,56 @@ __global__ void k_fill_f32(float* __restrict__ p, int64_t n, int64_t stride, flo
 
 // LDOS output of a chunk of moments [m0, m0 + cnt) from the step scratch
 // part[(m % ch) * tiles + t][p] (one row per tile, indexed by the position p
-// of the degree-sorted order, so the steps' stores are coalesced): for every
-// compact node k the tiles' values at p = pos[k] are summed in tile order and
-// written moment-major (out[m * n + k]) or node-major (out[k * M + m], through
-// a 32 x 32 shared-memory transpose so the writes stay coalesced).
-// Block (32, 8).
-template <bool NODE_MAJOR>
-__global__ void __launch_bounds__(256) k_ldos_fold(const float* __restrict__ part, const int32_t* __restrict__ pos,
-                                                   int tiles, int ch, int64_t n, int m0, int cnt, int M,
-                                                   float* __restrict__ out) {
+// of the degree-sorted order, so the steps' stores are coalesced); the
+// tiles' values are summed in tile order.
+// Moment-major (out[m * n + k]): a thread per (moment, position), reading
+// the scratch rows in position order and writing at the node's compact id
+// k = compact[p].
+__global__ void __launch_bounds__(256) k_ldos_fold_mm(const float* __restrict__ part,
+                                                      const int32_t* __restrict__ compact, int tiles, int ch,
+                                                      int64_t n, int m0, int cnt, float* __restrict__ out) {
+  const int64_t total = static_cast<int64_t>(cnt) * n;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int r = static_cast<int>(e / n);
+    const int64_t p = e - static_cast<int64_t>(r) * n;
+    const int m = m0 + r;
+    const float* src = part + static_cast<size_t>(m % ch) * tiles * n + p;
+    float v = 0.f;
+    for (int t = 0; t < tiles; ++t) v += src[static_cast<size_t>(t) * n];
+    out[static_cast<size_t>(m) * n + compact[p]] = v;
+  }
+}
+
+// Node-major (out[k * M + m]): for every compact node k the value at
+// p = pos[k], through a 32 x 32 shared-memory transpose so that each node's
+// run of moments is one contiguous write.  Block (32, 8).
+__global__ void __launch_bounds__(256) k_ldos_fold_nm(const float* __restrict__ part, const int32_t* __restrict__ pos,
+                                                      int tiles, int ch, int64_t n, int m0, int cnt, int M,
+                                                      float* __restrict__ out) {
   __shared__ float tile_s[32][33];
   const int tx = threadIdx.x, ty = threadIdx.y;
   for (int64_t k0 = static_cast<int64_t>(blockIdx.x) * 32; k0 < n; k0 += static_cast<int64_t>(gridDim.x) * 32) {
     for (int r0 = 0; r0 < cnt; r0 += 32) {
       for (int r = ty; r < 32; r += 8) {
         const int64_t k = k0 + tx;
-        const int m = m0 + r0 + r;
         float v = 0.f;
         if (k < n && r0 + r < cnt) {
+          const int m = m0 + r0 + r;
           const float* src = part + static_cast<size_t>(m % ch) * tiles * n + pos[k];
           for (int t = 0; t < tiles; ++t) v += src[static_cast<size_t>(t) * n];
-          if (!NODE_MAJOR) out[static_cast<size_t>(m) * n + k] = v;
         }
         tile_s[r][tx] = v;
       }
-      if (NODE_MAJOR) {
-        __syncthreads();
-        for (int j = ty; j < 32; j += 8) {
-          const int64_t k = k0 + j;
-          if (k < n && r0 + tx < cnt) out[static_cast<size_t>(k) * M + m0 + r0 + tx] = tile_s[tx][j];
-        }
-        __syncthreads();
+      __syncthreads();
+      for (int j = ty; j < 32; j += 8) {
+        const int64_t k = k0 + j;
+        if (k < n && r0 + tx < cnt) out[static_cast<size_t>(k) * M + m0 + r0 + tx] = tile_s[tx][j];
       }
+      __syncthreads();
     }
   }
 }
-
 
 static std::mutex g_smem_mu;
 
@@ -328,7 +342,7 @@ static int run_steps(const Graph* G, const Filter* F, const Plan& plan, int M, i
 
   // LDOS output.  One tile and the moment-major layout: every step stores
   // its row of C_out directly.  Otherwise the steps store one row per tile
-  // into a scratch of `ch` moments, and k_ldos_fold sums the tiles in a fixed
+  // into a scratch of `ch` moments, and k_ldos_fold_* sum the tiles in a fixed
   // order into the requested layout once a chunk of moments is complete:
   // after every step for the moment-major layout (the scratch, tiles x N
   // floats, stays in L2 and its rows are written out coalesced), after up to
@@ -343,11 +357,13 @@ static int run_steps(const Graph* G, const Filter* F, const Plan& plan, int M, i
     st = dalloc_t(&lpart, static_cast<size_t>(ch) * plan.tiles * n, s);
   }
   const auto fold_chunk = [&](int m0, int cnt) {
-    const unsigned blocks = static_cast<unsigned>(std::min<int64_t>((n + 31) / 32, 16LL * num_sms()));
-    if (node_major)
-      k_ldos_fold<true><<<blocks, dim3(32, 8), 0, s>>>(lpart, G->compact_to_p, plan.tiles, ch, n, m0, cnt, M, C_out);
-    else
-      k_ldos_fold<false><<<blocks, dim3(32, 8), 0, s>>>(lpart, G->compact_to_p, plan.tiles, ch, n, m0, cnt, M, C_out);
+    if (node_major) {
+      const unsigned blocks = static_cast<unsigned>(std::min<int64_t>((n + 31) / 32, 16LL * num_sms()));
+      k_ldos_fold_nm<<<blocks, dim3(32, 8), 0, s>>>(lpart, G->compact_to_p, plan.tiles, ch, n, m0, cnt, M, C_out);
+    } else {
+      const unsigned blocks = static_cast<unsigned>(std::min<int64_t>((cnt * n + 255) / 256, 8LL * num_sms()));
+      k_ldos_fold_mm<<<blocks, 256, 0, s>>>(lpart, G->p_compact, plan.tiles, ch, n, m0, cnt, C_out);
+    }
     count_launch();
     cu(cudaGetLastError(), "k_ldos_fold");
   };
