@@ -100,6 +100,22 @@ def max_over_ranks(dist, values, device):
     return [float(v) for v in t.tolist()]
 
 
+def combine_moments(dist, d, device):
+    """Probe-sharded form of one problem: every rank ran the same graph with
+    its own independent probes (its own seed, Nz each); the trace estimator
+    of Eq. (11) averages over probes, so the estimate from all world * Nz
+    probes is the mean of the ranks' normalised moments -- one sum of M
+    doubles over the ranks, the path's only exchange.  Identity without a
+    process group."""
+    import torch
+
+    t = torch.as_tensor(d, dtype=torch.float64, device=device).clone()
+    if dist is None:
+        return t
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return t / dist.get_world_size()
+
+
 def whole_job_gbs(world: int, bytes_per_rank: float, seconds: float) -> float:
     """Whole-job GB/s: every rank moved bytes_per_rank in `seconds` (max over ranks)."""
     return world * bytes_per_rank / seconds / 1e9
@@ -110,9 +126,11 @@ STEP_SOURCES = ("paper_1905_09758_gb300/csrc/kpm_kernels.cuh", "paper_1905_09758
 TRAFFIC_PROFILE = "profiles/step_traffic_chung_lu_1M.md"
 HEADLINE_SOURCES = STEP_SOURCES
 HEADLINE_PROFILE = "profiles/step_traffic_chung_lu_60M.md"
-# measured with a plain gather kernel on GB300 (profiles/random_gather_ceiling.md)
-RANDOM_ACCESS_NOTE = ("random row gathers from a block far larger than L2 top out at ~37-44 M rows/ms whatever the "
-                      "row width up to 128 B (DRAM access rate, not bytes); the 60M-node step gathers ~2e9 rows")
+# measured with a plain gather kernel on GB300 (bench.py --gather-ceiling, profiles/random_gather_ceiling.md):
+# 64-byte rows gathered from a 4.3 GB table with the Chung-Lu endpoint law of a degree-sorted order
+GATHER_CEILING_MROWS_PER_MS = 47.0
+RANDOM_ACCESS_NOTE = ("random row gathers from a block far larger than L2 top out at ~37-47 M rows/ms whatever the "
+                      "row width up to 128 B (DRAM access rate, not bytes); the step gathers one row per nonzero")
 
 
 def step_source_hash(sources=STEP_SOURCES) -> str:
@@ -319,6 +337,14 @@ def run_ours(args):
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     del src_h, dst_h
 
+    # probe-sharded single problem: the ranks' filtered moments (independent seeds) combined
+    g_c = nd.dos_build_csr(src_d, dst_d, n_nodes)
+    f_c = nd.dos_motif_filter(g_c)
+    d_c = combine_moments(dist, nd.dos_moments(g_c, w["M_kpm"], nz, seed, filter=f_c), dev)
+    combined = {"ranks": world, "probes": world * nz,
+                "d2": round(float(d_c[2]), 6) if d_c.numel() > 2 else None,
+                "exchange_bytes": 8 * int(d_c.numel()) if world > 1 else 0}
+    del g_c, f_c, d_c
     tl1 = None if args.no_time_to_l1 else time_to_l1_c5(src_d, dst_d, n_nodes, seed, rec)
     del src_d, dst_d
     torch.cuda.empty_cache()
@@ -385,6 +411,9 @@ def run_ours(args):
             "launches": step_launches,
             "share_of_step": round(step_ms_total / ms, 4) if ms > 0 else None,
             "random_access_bound": RANDOM_ACCESS_NOTE,
+            "gathers_per_launch": nnz,
+            "gather_rate_mrows_per_ms": round(nnz / avg_launch_ms / 1e6, 1),
+            "gather_ceiling_mrows_per_ms": GATHER_CEILING_MROWS_PER_MS,
         },
         "e2e": {
             "value": round(whole_job_gbs(world, bytes_step, e2e_s), 2),
@@ -402,6 +431,7 @@ def run_ours(args):
             "ms_per_fused_step": round(avg_launch_ms, 4),
         },
         "setup": {"train_s": round(setup_train_s, 1), "network": train_info, "small_family_network": small_info},
+        "probe_sharded": combined,
     }
     if tl1 is not None:
         out["time_to_l1"] = tl1

@@ -32,6 +32,47 @@ def _rank_main(rank, world, port, out):
         dist.destroy_process_group()
 
 
+def _combine_main(rank, world, port, out):
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle
+    import synthgraphs as sg
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        # each rank: the oracle's moments of the same graph with its own probes (seed 100 + rank)
+        s, d, n = sg.erdos_renyi(300, 0.03, 4)
+        ref = oracle.build_csr(s, d, n)
+        z = oracle.probes(100 + rank, ref.old_id, 6)
+        mine = oracle.kpm_doubled(ref, z, 20) / (ref.n * 6)
+        out[rank] = bench.combine_moments(dist, mine, torch.device("cpu")).numpy().tolist()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_probe_sharded_moments_world_2():
+    """Two ranks with independent probes combine into the estimate of all 12
+    probes: the single-process oracle run on the two probe blocks side by side."""
+    import numpy as np
+
+    sys.path.insert(0, ROOT)
+    import oracle
+    import synthgraphs as sg
+
+    port = _free_port()
+    with mp.Manager() as man:
+        out = man.dict()
+        mp.spawn(_combine_main, args=(2, port, out), nprocs=2, join=True)
+        res = dict(out)
+    s, d, n = sg.erdos_renyi(300, 0.03, 4)
+    ref = oracle.build_csr(s, d, n)
+    z = np.concatenate([oracle.probes(100, ref.old_id, 6), oracle.probes(101, ref.old_id, 6)], axis=1)
+    want = oracle.kpm_doubled(ref, z, 20) / (ref.n * 12)
+    assert res[0] == res[1]
+    assert np.abs(np.array(res[0]) - want).max() < 1e-14
+
+
 def test_max_over_ranks_world_2():
     port = _free_port()
     with mp.Manager() as man:
