@@ -382,6 +382,7 @@ def run_ours(args):
     peak, peak_kind = load_peaks()
     avg_launch_ms = step_ms_total / max(1, step_launches)
     achieved = b_launch / (avg_launch_ms * 1e-3) / 1e9
+    traffic = measured_traffic(HEADLINE_PROFILE, HEADLINE_SOURCES)
     out = {
         "metric": METRIC,
         "value": round(value, 2),
@@ -405,7 +406,11 @@ def run_ours(args):
             "peak_kind": f"{peak_kind} hbm_gbs",
             "unit": "GB/s",
             "frac": round(achieved / peak, 4),
-            "traffic": measured_traffic(HEADLINE_PROFILE, HEADLINE_SOURCES),
+            "traffic": traffic,
+            # the DRAM traffic of a launch (ncu) over its live average duration: what the DRAM
+            # actually moves, random 64-byte row gathers costing ~2x their bytes
+            "traffic_gbs": round(traffic / (avg_launch_ms * 1e-3) / 1e9, 1) if traffic else None,
+            "traffic_frac": round(traffic / (avg_launch_ms * 1e-3) / 1e9 / peak, 4) if traffic else None,
             "bytes_per_launch": round(b_launch),
             "avg_launch_ms": round(avg_launch_ms, 4),
             "launches": step_launches,
@@ -504,6 +509,7 @@ def section_c2(args, dist, dev, rank, world) -> dict:
     per_launch_bytes = bytes_step / fused_steps
     avg_launch_ms = step_ms_total / max(1, step_launches)
     achieved = per_launch_bytes / (avg_launch_ms * 1e-3) / 1e9
+    c2_traffic = measured_traffic(TRAFFIC_PROFILE, STEP_SOURCES)
     del c_buf, c_host
     return {
         "config": dict(C2, n_compact=n, nnz=nnz, plan=plan),
@@ -518,7 +524,8 @@ def section_c2(args, dist, dev, rank, world) -> dict:
             "peak_kind": f"{peak_kind} hbm_gbs",
             "unit": "GB/s",
             "frac": round(achieved / peak, 4),
-            "traffic": measured_traffic(TRAFFIC_PROFILE, STEP_SOURCES),
+            "traffic": c2_traffic,
+            "traffic_gbs": round(c2_traffic / (avg_launch_ms * 1e-3) / 1e9, 1) if c2_traffic else None,
             "bytes_per_launch": round(per_launch_bytes),
             "avg_launch_ms": round(avg_launch_ms, 5),
             "launches": step_launches,
