@@ -1174,7 +1174,8 @@ def learned_leg(g, h_ref, seed: int, timed_reps: int = 3) -> dict:
 # ---------------------------------------------------------------------------
 # the headline network's training family: large Chung-Lu graphs drawn on the device
 LARGE_LEARN = {"train_graphs": 2000, "family": "Chung-Lu on the device, N log-uniform [1e4, 1e6], gamma U[2.1, 3.0], "
-               "mean degree U[5, 40]", "M_in": 50, "Nz_in": 10, "M_ref": 500, "Nz_ref": 64, "hidden": [512, 512],
+               "mean degree U[5, 40]", "M_in": 50, "M_in_more": [20, 30], "Nz_in": 10, "M_ref": 500, "Nz_ref": 64,
+               "hidden": [512, 512],
                "steps": 16000, "batch": 256, "lr": 2e-3, "seed": 23, "inputs": "Jackson histogram, d_1..d_49, "
                "degree statistics (mean, spread, largest) and log(N Nz)"}
 HEADLINE_REF = {"M": 500, "Nz": 32}
@@ -1191,14 +1192,16 @@ def train_large_family():
     sl = LARGE_LEARN
     t0 = time.perf_counter()
     graphs = (sg.chung_lu_device_member(sl["seed"] * 1_000_003 + k) for k in range(sl["train_graphs"]))
-    x, t = learned.training_set(graphs, sl["M_in"], sl["Nz_in"], sl["M_ref"], sl["Nz_ref"], BINS, seed=sl["seed"] * 7919)
+    m_ins = [sl["M_in"], *sl["M_in_more"]]
+    xs, t = learned.training_sets(graphs, m_ins, sl["Nz_in"], sl["M_ref"], sl["Nz_ref"], BINS, seed=sl["seed"] * 7919)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    rec = learned.train(x, t, sl["M_in"], sl["Nz_in"], hidden=sl["hidden"], steps=sl["steps"], batch=sl["batch"],
-                        lr=sl["lr"], seed=sl["seed"])
+    recs = {m: learned.train(xs[m], t, m, sl["Nz_in"], hidden=sl["hidden"], steps=sl["steps"], batch=sl["batch"],
+                             lr=sl["lr"], seed=sl["seed"]) for m in m_ins}
     torch.cuda.synchronize()
     t2 = time.perf_counter()
-    return rec, dict(sl, data_s=round(t1 - t0, 1), train_s=round(t2 - t1, 1))
+    _TRAINED["large_more"] = {m: recs[m] for m in sl["M_in_more"]}
+    return recs[sl["M_in"]], dict(sl, data_s=round(t1 - t0, 1), train_s=round(t2 - t1, 1))
 
 
 def time_to_l1_c5(src_d, dst_d, n_nodes, seed, rec, target=1e-2, reps: int = 2) -> dict:
@@ -1252,6 +1255,9 @@ def time_to_l1_c5(src_d, dst_d, n_nodes, seed, rec, target=1e-2, reps: int = 2) 
 
     t, l1 = timed(lrn(rec))
     rows.append({"variant": "learned (large family)", "M": rec.m_in, "Nz": rec.nz_in, "seconds": t, "l1": l1})
+    for m_in, r in sorted(_TRAINED.get("large_more", {}).items(), reverse=True):
+        t, l1 = timed(lrn(r))
+        rows.append({"variant": "learned (large family)", "M": r.m_in, "Nz": r.nz_in, "seconds": t, "l1": l1})
     small = _TRAINED.get("rec")
     if small is not None:
         t, l1 = timed(lrn(small))

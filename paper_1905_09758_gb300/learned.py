@@ -77,6 +77,30 @@ def training_set(graphs, m_in: int = 50, nz_in: int = 8, m_ref: int = 500, nz_re
     return torch.cat(xs).contiguous(), torch.cat(ts).contiguous()
 
 
+def training_sets(graphs, m_ins, nz_in: int = 8, m_ref: int = 500, nz_ref: int = 256, bins: int = 200, seed: int = 0,
+                  stats: bool = True, stream=None):
+    """({m_in: X}, T) for several input sizes at once: one cheap run of
+    max(m_ins) moments per graph gives the first m_in moments of each (the
+    doubled recurrence's first moments do not depend on how many follow), and
+    each X gets the Jackson histogram of its own first m_in moments.  Graph k
+    uses input seed seed + 2k and reference seed seed + 2k + 1, as
+    training_set."""
+    m_ins = sorted(set(int(m) for m in m_ins))
+    xs = {m: [] for m in m_ins}
+    ts = []
+    m_max = m_ins[-1]
+    for k, (src, dst, n) in enumerate(graphs):
+        g, f = filtered_operator(src, dst, n, stream=stream)
+        d = nd.dos_moments(g, m_max, nz_in, seed + 2 * k, filter=f, stream=stream)
+        st = nd.dos_graph_stats(g, nz_in, stream=stream).view(1, 4) if stats else None
+        for m in m_ins:
+            dm = d[:m].contiguous()
+            h = nd.dos_density(dm, bins, stream=stream)
+            xs[m].append(nd.dos_mlp_features(h.view(1, bins), dm.view(1, m), m, stats=st, stream=stream))
+        ts.append(target(g, f, m_ref, nz_ref, seed + 2 * k + 1, bins, stream=stream))
+    return {m: torch.cat(v).contiguous() for m, v in xs.items()}, torch.cat(ts).contiguous()
+
+
 def train(x: torch.Tensor, t: torch.Tensor, m_in: int, nz_in: int, hidden=(512, 512), steps: int = 8000,
           batch: int = 256, lr: float = 1e-3, lr_min: float = 1e-5, seed: int = 0, stream=None) -> Reconstructor:
     """Adam on minibatches drawn uniformly with replacement, learning rate on a

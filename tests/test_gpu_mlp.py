@@ -326,3 +326,18 @@ def test_degree_stats_and_stat_features_match_oracle():
     x_ref = oracle.mlp_features(oracle.histogram(dd, bins)[None], dd[None], m_in,
                                 stats=[oracle.graph_stats(ref.deg, 8)])[0]
     assert np.all(np.abs(x - x_ref) <= 2 * U * np.maximum(np.abs(x_ref), 1e-3))
+
+
+def test_training_sets_share_one_cheap_run():
+    """learned.training_sets: the rows for each input size equal the features
+    of a run with exactly that many moments (the doubled recurrence's first
+    moments do not depend on how many follow), and the targets equal
+    training_set's."""
+    from paper_1905_09758_gb300 import learned
+
+    graphs = [sg.add_twin_leaves(*sg.chung_lu(1500, 2.5, 8.0, 40 + k), 30, 50 + k) for k in range(3)]
+    xs, t = learned.training_sets(graphs, [8, 13], nz_in=4, m_ref=40, nz_ref=16, bins=30, seed=9)
+    for m in (8, 13):
+        x1, t1 = learned.training_set(graphs, m, 4, 40, 16, 30, seed=9)
+        assert torch.equal(xs[m], x1), m
+        assert torch.equal(t, t1)
