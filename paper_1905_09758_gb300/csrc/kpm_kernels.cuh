@@ -23,7 +23,7 @@
 // (k_cheb_medium); light rows go to a persistent kernel in which every warp
 // takes rounds of R = 32 / Q consecutive rows, Q lanes per row, each lane one
 // 16-byte chunk of the row's tile (t = Q * VEC probes), and stages the next
-// round's contiguous data in shared memory with bulk copies (k_cheb_light).
+// round's contiguous data in shared memory with cp.async (k_cheb_light).
 #pragma once
 
 #include <type_traits>
