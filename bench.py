@@ -1634,6 +1634,120 @@ def gather_ceiling():
         subprocess.run([exe], check=True)
 
 
+def bfs_order(src, dst, n: int):
+    """Cuthill-McKee-style numbering (device tensors): breadth-first from the
+    largest-degree node, each level in the order its nodes are first reached
+    from the previous level; nodes of other components follow in id order.
+    Returns rank[node]."""
+    import torch
+
+    s = torch.cat([src, dst])
+    d = torch.cat([dst, src])
+    keep = s != d
+    s, d = s[keep], d[keep]
+    order = torch.argsort(s)
+    d = d[order]
+    deg = torch.bincount(s, minlength=n)
+    del s, order
+    row = torch.zeros(n + 1, dtype=torch.int64, device=src.device)
+    row[1:] = torch.cumsum(deg, 0)
+    rank = torch.full((n,), -1, dtype=torch.int64, device=src.device)
+    front = torch.argmax(deg).view(1)
+    rank[front] = 0
+    nxt = 1
+    while front.numel() > 0:
+        beg, cnt = row[front], deg[front]
+        total = int(cnt.sum())
+        if total == 0:
+            break
+        base = torch.repeat_interleave(beg - (torch.cumsum(cnt, 0) - cnt), cnt)
+        nb = d[base + torch.arange(total, device=src.device)]
+        nb = nb[rank[nb] < 0]
+        if nb.numel() == 0:
+            break
+        uniq, inv = torch.unique(nb, return_inverse=True)
+        first = torch.full((uniq.numel(),), nb.numel(), dtype=torch.int64, device=src.device)
+        first.scatter_reduce_(0, inv, torch.arange(nb.numel(), device=src.device), reduce="amin")
+        front = uniq[torch.argsort(first)]
+        rank[front] = nxt + torch.arange(front.numel(), device=src.device)
+        nxt += front.numel()
+    rest = torch.nonzero(rank < 0).view(-1)
+    rank[rest] = nxt + torch.arange(rest.numel(), device=src.device)
+    return rank
+
+
+def row_order_locality(m_moments: int = 21, nz: int = 10, reps: int = 3):
+    """Fused-step time of dos_moments (FP32, Nz = 10: one 64-byte tile, as on
+    the headline graph) under several numberings of the same graphs, with the
+    default degree-descending row order and with DOS_ORDER_BY_CLASS.  Graphs:
+    a Chung-Lu graph of the headline family at N = 8M (an expander: no
+    numbering gives its neighbour lists locality), a 3D torus (degree 6) and a
+    2D lattice with random local edges (varying degree).  Numberings: the
+    generator's, a random permutation, and breadth-first (bfs_order).  Prints
+    one JSON line per run."""
+    import torch
+
+    import paper_1905_09758_gb300 as nd
+    import synthgraphs as sg
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(7)
+
+    def torus3d(side: int):
+        i = torch.arange(side ** 3, device=dev)
+        x, y, z = i % side, (i // side) % side, i // (side * side)
+        nbr = [((x + 1) % side) + side * y + side * side * z, x + side * ((y + 1) % side) + side * side * z,
+               x + side * y + side * side * ((z + 1) % side)]
+        return i.repeat(3), torch.cat(nbr), side ** 3
+
+    def local_lattice(side: int, mean_deg: float, reach: int):
+        n = side * side
+        m = int(n * mean_deg / 2)
+        u = torch.randint(0, n, (m,), device=dev, generator=gen)
+        dx = torch.randint(-reach, reach + 1, (m,), device=dev, generator=gen)
+        dy = torch.randint(-reach, reach + 1, (m,), device=dev, generator=gen)
+        x, y = u % side + dx, u // side + dy
+        ok = (x >= 0) & (x < side) & (y >= 0) & (y < side)
+        return u[ok], (y * side + x)[ok], n
+
+    graphs = {
+        "chung_lu_8M": lambda: sg.chung_lu_device(8_000_000, WORKLOAD["gamma"], WORKLOAD["mean_degree"], 77),
+        "torus3d_200": lambda: torus3d(200),
+        "lattice2d_local_2828": lambda: local_lattice(2828, 16.0, 6),
+    }
+    for gname, make in graphs.items():
+        src, dst, n = make()
+        numberings = {"generator": None,
+                      "random": torch.randperm(n, device=dev, generator=gen),
+                      "bfs": bfs_order(src, dst, n)}
+        for num, perm in numberings.items():
+            s, t = (src, dst) if perm is None else (perm[src], perm[dst])
+            for order in ("degree", "class"):
+                g = nd.dos_build_csr(s, t, n, order=order)
+                info = g.info()
+                best = float("inf")
+                nd.dos_profile_enable(True)
+                for r in range(reps + 1):
+                    nd.dos_profile_read(reset=True)
+                    nd.dos_moments(g, m_moments, nz, 3)
+                    torch.cuda.synchronize()
+                    ms, k = nd.dos_profile_read(reset=True)
+                    if r > 0:
+                        best = min(best, ms / max(1, k))
+                nd.dos_profile_enable(False)
+                b = step_bytes(info["n"], info["nnz"], nz, False)
+                print(json.dumps({"graph": gname, "numbering": num, "row_order": order, "n": info["n"],
+                                  "nnz": info["nnz"], "ms_per_step": round(best, 4),
+                                  "M_rows_per_ms": round(info["nnz"] / best / 1e6, 1),
+                                  "alg_gbs": round(b / best / 1e6, 1)}), flush=True)
+                del g
+            del s, t
+        del src, dst, numberings
+        torch.cuda.empty_cache()
+
+
 def profile_step(args):
     """The headline step alone, for ncu launch lists and counter captures: the
     workload's CSR build, filter, M = 200 KPM and density, and the M = 50
@@ -1720,6 +1834,8 @@ def main():
                     help="with --profile-step: nodes of the Chung-Lu graph (0 = the workload's 60M)")
     ap.add_argument("--profile-workload", choices=["chung_lu_60M", "chung_lu_1M"], default="chung_lu_60M",
                     help="with --profile-step: the headline step, or one step of the chung_lu_1M section")
+    ap.add_argument("--row-order", action="store_true",
+                    help="measure the fused step under several node numberings and row orders and exit")
     ap.add_argument("--side-kernels", action="store_true",
                     help="run only a short Lanczos / LDOS-of-A / contraction sequence (for ncu) and exit")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -1735,10 +1851,13 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--ref-steps-per-sample", type=int, default=2)
     args = ap.parse_args()
-    if args.warmup < 3 and args.impl == "ours" and not (args.profile_step or args.side_kernels or args.gather_ceiling):
+    if args.warmup < 3 and args.impl == "ours" and not (args.profile_step or args.side_kernels or args.gather_ceiling
+                                                         or args.row_order):
         ap.error("--warmup must be >= 3")
     if args.gather_ceiling:
         gather_ceiling()
+    elif args.row_order:
+        row_order_locality()
     elif args.profile_step:
         profile_step(args)
     elif args.side_kernels:

@@ -61,7 +61,9 @@ enum dos_kernel { DOS_KERNEL_NONE = 0, DOS_KERNEL_JACKSON = 1 };
 
 /* Flags of dos_build_csr. */
 enum dos_build_flags {
-  DOS_INPUT_HOST = 1 /* src/dst are host pointers; the library copies them */
+  DOS_INPUT_HOST = 1,    /* src/dst are host pointers; the library copies them */
+  DOS_ORDER_BY_CLASS = 2 /* the kernels' row order keeps the node numbering
+                            inside each degree class (see dos_build_csr) */
 };
 
 /* Instrumentation, not in the paper. Library version as MAJOR*10000 +
@@ -83,8 +85,16 @@ const char* dos_last_error(void);
  *   out        receives the graph handle (device memory owned by the library).
  * Column indices are int32 and row offsets int64, so nnz (2 x undirected
  * edges) may exceed 2^31; n_edges <= 2^40.
+ * Row order of the step kernels (a relabelling; moments and densities do not
+ * depend on it beyond FP rounding, LDOS rows are returned by compact id):
+ * by default degree-descending, so rows processed together have similar
+ * degrees.  With DOS_ORDER_BY_CLASS only the three degree classes (>= 2048,
+ * >= 64, the rest) are separated and each keeps the node numbering: for
+ * graphs numbered so that neighbours have nearby ids (meshes, road networks,
+ * a bandwidth-reducing order), whose gathers then stay in L2.
  * Errors: DOS_EINVAL (negative sizes, endpoint out of range -- detected on
- * the device and reported after a stream sync), DOS_ENOMEM, DOS_ECUDA.
+ * the device and reported after a stream sync, unknown flags), DOS_ENOMEM,
+ * DOS_ECUDA.
  * Synchronises `stream` (the node count is needed on the host).
  */
 int dos_build_csr(const int64_t* src, const int64_t* dst, int64_t n_edges,

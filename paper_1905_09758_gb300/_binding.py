@@ -21,6 +21,7 @@ PREC = {"fp32": 0, "bf16": 1, "fp16": 2}
 KERNEL = {"none": 0, "jackson": 1}
 LAYOUT = {"moment": 0, "node": 1}
 DOS_INPUT_HOST = 1
+DOS_ORDER_BY_CLASS = 2
 MOTIF = {"open": 1, "closed": 2, "pendant": 4, "parallel": 8}
 OPERATOR = {"normalized_adjacency": 0, "adjacency": 1, "laplacian": 2, "normalized_laplacian": 3}
 
@@ -245,14 +246,18 @@ def dos_version() -> int:
     return lib().dos_version()
 
 
-def dos_build_csr(src: torch.Tensor, dst: torch.Tensor, n_nodes: int, stream=None) -> Graph:
-    """Edge list (int64 tensors, CUDA or host) -> Graph.  Host tensors are copied by the library."""
+def dos_build_csr(src: torch.Tensor, dst: torch.Tensor, n_nodes: int, stream=None, order: str = "degree") -> Graph:
+    """Edge list (int64 tensors, CUDA or host) -> Graph.  Host tensors are copied by the library.
+    order "degree": the step kernels' rows by descending degree; "class": by
+    degree class only, keeping the node numbering inside a class."""
+    if order not in ("degree", "class"):
+        raise ValueError("order must be 'degree' or 'class'")
     if src.dtype != torch.int64 or dst.dtype != torch.int64 or src.shape != dst.shape:
         raise ValueError("src and dst must be int64 tensors of equal shape")
     src, dst = src.contiguous(), dst.contiguous()
     if src.is_cuda != dst.is_cuda:
         raise ValueError("src and dst must be on the same device")
-    flags = 0 if src.is_cuda else DOS_INPUT_HOST
+    flags = (0 if src.is_cuda else DOS_INPUT_HOST) | (DOS_ORDER_BY_CLASS if order == "class" else 0)
     out = C.c_void_p()
     _check(lib().dos_build_csr(_ptr(src), _ptr(dst), src.numel(), int(n_nodes), flags, _stream(stream),
                                C.byref(out)))

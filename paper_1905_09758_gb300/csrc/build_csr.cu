@@ -1,6 +1,6 @@
 // dos_build_csr: undirected edge list -> CSR of A (compact ids), degrees,
-// D^{-1/2} (§2.1), and the degree-sorted relabelling used by the Chebyshev
-// kernels.  Sorting and prefix sums use CUB's device primitives; every other
+// D^{-1/2} (§2.1), and the degree-sorted (or degree-class) relabelling used
+// by the Chebyshev kernels.  Sorting and prefix sums use CUB's device primitives; every other
 // step is a kernel of this file.
 #include <cub/device/device_radix_sort.cuh>
 #include <cub/device/device_scan.cuh>
@@ -94,6 +94,18 @@ __global__ void k_deg_sort_key(const int32_t* __restrict__ deg, int64_t n, uint3
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
     key[k] = 0x7fffffffu - static_cast<uint32_t>(deg[k]);
+    idx[k] = static_cast<int32_t>(k);
+  }
+}
+
+// Class order (DOS_ORDER_BY_CLASS): heavy, medium, light; the stable sort
+// keeps compact-id order inside a class.
+__global__ void k_class_sort_key(const int32_t* __restrict__ deg, int64_t n, uint32_t* __restrict__ key,
+                                 int32_t* __restrict__ idx) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t d = deg[k];
+    key[k] = d >= kHeavyDeg ? 0u : (d >= kMediumDeg ? 1u : 2u);
     idx[k] = static_cast<int32_t>(k);
   }
 }
@@ -381,12 +393,17 @@ static int build_csr_impl(const int64_t* src_in, const int64_t* dst_in, int64_t 
       uint32_t *dk = nullptr, *dk_alt = nullptr;
       NDOS_CHECK(t.get(&dk, n));
       NDOS_CHECK(t.get(&dk_alt, n));
-      k_deg_sort_key<<<grid_for(n), kThreads, 0, s>>>(G->deg, n, dk, idx);
+      const bool by_class = (flags & DOS_ORDER_BY_CLASS) != 0;
+      if (by_class)
+        k_class_sort_key<<<grid_for(n), kThreads, 0, s>>>(G->deg, n, dk, idx);
+      else
+        k_deg_sort_key<<<grid_for(n), kThreads, 0, s>>>(G->deg, n, dk, idx);
       NDOS_LAUNCHED();
+      const int end_bit = by_class ? 2 : 31;
       cub::DoubleBuffer<uint32_t> kb(dk, dk_alt);
-      NDOS_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, bytes, kb, vb, n, 0, 31, s));
+      NDOS_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, bytes, kb, vb, n, 0, end_bit, s));
       NDOS_CHECK(t.get(reinterpret_cast<char**>(&tmp), bytes));
-      NDOS_CUDA(cub::DeviceRadixSort::SortPairs(tmp, bytes, kb, vb, n, 0, 31, s));
+      NDOS_CUDA(cub::DeviceRadixSort::SortPairs(tmp, bytes, kb, vb, n, 0, end_bit, s));
     }
     count_launch();
     NDOS_CUDA(cudaMemcpyAsync(G->p_compact, vb.Current(), sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
@@ -433,7 +450,9 @@ static int build_graph(const int64_t* src, const int64_t* dst, int64_t n_edges, 
   if (n_nodes > 0x7fffffffLL) return fail(DOS_EOVERFLOW, w + ": n_nodes exceeds 2^31 - 1");
   if (n_edges > (1LL << 40)) return fail(DOS_EOVERFLOW, w + ": n_edges exceeds 2^40");
   if (n_edges > 0 && (!src || !dst)) return fail(DOS_EINVAL, w + ": null edge arrays");
-  if (flags & ~static_cast<uint32_t>(DOS_INPUT_HOST)) return fail(DOS_EINVAL, w + ": unknown flags");
+  if (flags & ~static_cast<uint32_t>(DOS_INPUT_HOST | DOS_ORDER_BY_CLASS)) return fail(DOS_EINVAL, w + ": unknown flags");
+  if ((flags & DOS_ORDER_BY_CLASS) && node_offset)
+    return fail(DOS_EINVAL, w + ": DOS_ORDER_BY_CLASS is for single graphs (a batch is grouped by graph)");
   Graph* G = new Graph();
   cudaGetDevice(&G->device);
   int st = build_csr_impl(src, dst, n_edges, n_nodes, flags, node_offset, n_graphs, static_cast<cudaStream_t>(stream),

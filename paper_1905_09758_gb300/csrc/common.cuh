@@ -94,7 +94,9 @@ struct Temps {
 //  * the CSR in compact-id order (the exported, bit-exact one), and
 //  * a degree-sorted relabelling used by the Chebyshev kernels.  Rows are
 //    ordered by degree (descending, ties by compact id), so heavy rows are a
-//    prefix (load balancing) and the most-gathered rows share cache lines.
+//    prefix (load balancing) and the most-gathered rows share cache lines;
+//    with DOS_ORDER_BY_CLASS only by degree class (heavy, medium, light),
+//    compact-id order inside a class, which keeps a numbering's locality.
 //    The spectrum is invariant under the relabelling.
 struct Graph {
   int64_t n = 0, nnz = 0, n_isolated = 0, n_original = 0;

@@ -19,7 +19,8 @@
 // Rows are relabelled by degree class: heavy rows (degree >= kHeavyDeg)
 // first, then medium (>= kMediumDeg), then light rows, degree-descending
 // inside a class (a batch of graphs groups the medium and light rows graph by
-// graph).  Heavy rows get a CTA each (k_cheb_heavy), medium rows a warp each
+// graph; DOS_ORDER_BY_CLASS keeps the node numbering inside a class).  Heavy
+// rows get a CTA each (k_cheb_heavy), medium rows a warp each
 // (k_cheb_medium); light rows go to a persistent kernel in which every warp
 // takes rounds of R = 32 / Q consecutive rows, Q lanes per row, each lane one
 // 16-byte chunk of the row's tile (t = Q * VEC probes), and stages the next

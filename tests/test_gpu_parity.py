@@ -430,3 +430,47 @@ def test_ldos_layouts_equal_and_reproducible(t, nz):
     z = oracle.probes(seed, ref.old_id, nz)
     _, cref = oracle.kpm_direct(ref, z, m, ldos=True)
     assert np.abs(c_nm - cref).max() <= TOL_C
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+def test_class_row_order_matches_oracle(name):
+    """DOS_ORDER_BY_CLASS only relabels the kernels' rows (degree classes kept
+    apart, node numbering inside a class): the exported CSR, DOS and LDOS
+    moments and the twin filter match the oracle as with the default order,
+    and the filtered moments of the two orders agree."""
+    src, dst, n = GRAPHS[name]
+    ref = oracle.build_csr(src, dst, n)
+    g = nd.dos_build_csr(torch.from_numpy(src).cuda(), torch.from_numpy(dst).cuda(), n, order="class")
+    ex = {k: v.cpu().numpy() for k, v in nd.dos_graph_export(g).items()}
+    assert np.array_equal(ex["row_ptr"], ref.row_ptr) and np.array_equal(ex["col"], ref.col)
+    d = nd.dos_moments(g, 60, 20, 11).cpu().numpy()
+    assert np.abs(d - _dos_ref(ref, 11, 20, 60)).max() <= TOL_D
+    c, dl = nd.ldos_moments(g, 40, 20, 3)
+    z = oracle.probes(3, ref.old_id, 20)
+    mu, cref = oracle.kpm_direct(ref, z, 40, ldos=True)
+    assert np.abs(c.cpu().numpy().T - cref).max() <= TOL_C
+    assert np.abs(dl.cpu().numpy() - mu / (ref.n * 20)).max() <= TOL_D
+    f = nd.dos_motif_filter(g)
+    cid_ref, removed = oracle.twin_classes(ref)
+    assert np.array_equal(nd.dos_filter_export(f).cpu().numpy(), cid_ref)
+    g_deg = _gpu_graph(src, dst, n)
+    d_cls = nd.dos_moments(g, 40, 16, 9, filter=f).cpu().numpy()
+    d_deg = nd.dos_moments(g_deg, 40, 16, 9, filter=nd.dos_motif_filter(g_deg)).cpu().numpy()
+    assert np.abs(d_cls - d_deg).max() <= 2 * TOL_D
+
+
+def test_class_row_order_flag_checks():
+    import ctypes
+
+    s = torch.tensor([0, 1], dtype=torch.int64, device="cuda")
+    t = torch.tensor([1, 2], dtype=torch.int64, device="cuda")
+    out = ctypes.c_void_p()
+    off = (ctypes.c_int64 * 2)(0, 3)
+    st = nd.lib().dos_build_csr_batched(ctypes.c_void_p(s.data_ptr()), ctypes.c_void_p(t.data_ptr()), 2, off, 1,
+                                        nd.DOS_ORDER_BY_CLASS, None, ctypes.byref(out))
+    assert st == nd.DOS_EINVAL and not out.value
+    st = nd.lib().dos_build_csr(ctypes.c_void_p(s.data_ptr()), ctypes.c_void_p(t.data_ptr()), 2, 3, 8, None,
+                                ctypes.byref(out))
+    assert st == nd.DOS_EINVAL and not out.value
+    with pytest.raises(ValueError):
+        nd.dos_build_csr(s, t, 3, order="bfs")
