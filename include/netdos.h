@@ -61,7 +61,9 @@ enum dos_kernel { DOS_KERNEL_NONE = 0, DOS_KERNEL_JACKSON = 1 };
 
 /* Flags of dos_build_csr. */
 enum dos_build_flags {
-  DOS_INPUT_HOST = 1,    /* src/dst are host pointers; the library copies them */
+  DOS_INPUT_HOST = 1,    /* src/dst are host pointers: page-locked ones are read
+                            in place through their device mapping, others are
+                            copied to device temporaries */
   DOS_ORDER_BY_CLASS = 2 /* the kernels' row order keeps the node numbering
                             inside each degree class (see dos_build_csr) */
 };

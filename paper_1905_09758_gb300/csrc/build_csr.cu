@@ -251,7 +251,21 @@ static int build_csr_impl(const int64_t* src_in, const int64_t* dst_in, int64_t 
   Temps t(s);
   const int64_t* src = src_in;
   const int64_t* dst = dst_in;
+  // host input: page-locked buffers are read in place by k_make_keys through
+  // their device mapping (no 16-byte-per-edge device copy); pageable ones are
+  // copied to temporaries first
+  bool mapped = false;
   if ((flags & DOS_INPUT_HOST) && n_edges > 0) {
+    cudaPointerAttributes as{}, ad{};
+    if (cudaPointerGetAttributes(&as, src_in) == cudaSuccess && cudaPointerGetAttributes(&ad, dst_in) == cudaSuccess &&
+        as.type == cudaMemoryTypeHost && ad.type == cudaMemoryTypeHost && as.devicePointer && ad.devicePointer) {
+      src = static_cast<const int64_t*>(as.devicePointer);
+      dst = static_cast<const int64_t*>(ad.devicePointer);
+      mapped = true;
+    }
+    cudaGetLastError();  // an unregistered pointer is not an error here
+  }
+  if ((flags & DOS_INPUT_HOST) && n_edges > 0 && !mapped) {
     int64_t *ds = nullptr, *dd = nullptr;
     NDOS_CHECK(t.get(&ds, n_edges));
     NDOS_CHECK(t.get(&dd, n_edges));

@@ -96,6 +96,21 @@ def test_csr_from_host_buffers_and_edge_cases():
     assert g1.info()["nnz"] == 0
 
 
+@pytest.mark.parametrize("name", ["cl_twins", "hub"])
+def test_csr_from_pinned_host_buffers(name):
+    """Page-locked host edge lists are read in place (no device copy): the CSR
+    is still bit-exact, also from a slice that starts inside the buffer."""
+    src, dst, n = GRAPHS[name]
+    ref = oracle.build_csr(src, dst, n)
+    s = torch.from_numpy(np.concatenate([[7], src]).astype(np.int64)).pin_memory()
+    d = torch.from_numpy(np.concatenate([[7], dst]).astype(np.int64)).pin_memory()
+    g = nd.dos_build_csr(s[1:], d[1:], n)
+    ex = nd.dos_graph_export(g)
+    assert np.array_equal(ex["row_ptr"].cpu().numpy(), ref.row_ptr)
+    assert np.array_equal(ex["col"].cpu().numpy(), ref.col)
+    assert np.array_equal(ex["old_id"].cpu().numpy(), ref.old_id)
+
+
 def test_invalid_ids_are_rejected():
     with pytest.raises(nd.DosError) as e:
         _gpu_graph(np.array([0, 7]), np.array([1, 2]), 5)
