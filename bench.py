@@ -1174,7 +1174,7 @@ def learned_leg(g, h_ref, seed: int, timed_reps: int = 3) -> dict:
 # ---------------------------------------------------------------------------
 # the headline network's training family: large Chung-Lu graphs drawn on the device
 LARGE_LEARN = {"train_graphs": 2000, "family": "Chung-Lu on the device, N log-uniform [1e4, 1e6], gamma U[2.1, 3.0], "
-               "mean degree U[5, 40]", "M_in": 50, "M_in_more": [20, 30], "Nz_in": 10, "M_ref": 500, "Nz_ref": 64,
+               "mean degree U[5, 40]", "M_in": 50, "M_in_more": [10, 14, 20, 30], "Nz_in": 10, "M_ref": 500, "Nz_ref": 64,
                "hidden": [512, 512],
                "steps": 16000, "batch": 256, "lr": 2e-3, "seed": 23, "inputs": "Jackson histogram, d_1..d_49, "
                "degree statistics (mean, spread, largest) and log(N Nz)"}
