@@ -87,8 +87,9 @@ const char* dos_last_error(void);
  *   out        receives the graph handle (device memory owned by the library).
  * Column indices are int32 and row offsets int64, so nnz (2 x undirected
  * edges) may exceed 2^31; n_edges <= 2^40.
- * Row order of the step kernels (a relabelling; moments and densities do not
- * depend on it beyond FP rounding, LDOS rows are returned by compact id):
+ * Row order of the step kernels (a project addition, not in the paper; a
+ * relabelling, so moments and densities do not depend on it beyond FP
+ * rounding, and LDOS rows are returned by compact id):
  * by default degree-descending, so rows processed together have similar
  * degrees.  With DOS_ORDER_BY_CLASS only the three degree classes (>= 2048,
  * >= 64, the rest) are separated and each keeps the node numbering: for
