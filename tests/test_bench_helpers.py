@@ -48,3 +48,39 @@ def test_cpu_sample_times_the_oracle_on_worker_processes():
         assert "N=20,000" in cs.describe(2)
     finally:
         cs.close()
+
+
+def test_bfs_order_is_a_breadth_first_numbering():
+    """bench.bfs_order (the --row-order measurement's breadth-first numbering):
+    a permutation in which ranks grow with the BFS level from the largest-degree
+    node, every reached node is numbered after a neighbour on the previous
+    level, and nodes of other components follow."""
+    import scipy.sparse.csgraph as csg
+    import torch
+
+    s1, d1, n1 = sg.grid2d(9, 7)
+    s2, d2, n2 = sg.erdos_renyi(40, 0.1, 2)
+    src = np.concatenate([s1, s2 + n1])
+    dst = np.concatenate([d1, d2 + n1])
+    n = n1 + n2 + 3  # three isolated nodes
+    rank = bench.bfs_order(torch.from_numpy(src), torch.from_numpy(dst), n).numpy()
+    assert np.array_equal(np.sort(rank), np.arange(n))
+    import scipy.sparse as sp
+
+    a = sp.coo_matrix((np.ones(2 * src.size), (np.concatenate([src, dst]), np.concatenate([dst, src]))),
+                      shape=(n, n)).tocsr()
+    a.data[:] = 1.0
+    deg = np.diff(a.indptr)
+    root = int(np.argmax(deg))
+    assert rank[root] == 0
+    level = csg.shortest_path(a, unweighted=True, indices=root)
+    reached = np.isfinite(level)
+    lv = level[reached]
+    order = np.argsort(rank[reached])
+    assert np.all(np.diff(lv[order]) >= 0)  # levels never decrease along the numbering
+    assert rank[reached].max() < rank[~reached].min()
+    for v in np.nonzero(reached)[0]:
+        if v == root:
+            continue
+        nb = a.indices[a.indptr[v]:a.indptr[v + 1]]
+        assert np.any(level[nb] == level[v] - 1)
