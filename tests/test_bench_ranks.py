@@ -61,7 +61,7 @@ def test_probe_sharded_moments_world_2():
     import synthgraphs as sg
 
     port = _free_port()
-    with mp.Manager() as man:
+    with mp.get_context("spawn").Manager() as man:
         out = man.dict()
         mp.spawn(_combine_main, args=(2, port, out), nprocs=2, join=True)
         res = dict(out)
@@ -75,7 +75,7 @@ def test_probe_sharded_moments_world_2():
 
 def test_max_over_ranks_world_2():
     port = _free_port()
-    with mp.Manager() as man:
+    with mp.get_context("spawn").Manager() as man:
         out = man.dict()
         mp.spawn(_rank_main, args=(2, port, out), nprocs=2, join=True)
         res = dict(out)
