@@ -651,6 +651,16 @@ int dos_mlp_param_count(dos_mlp_t net, int64_t* count);
  * moments and step count. */
 int dos_mlp_get_params(dos_mlp_t net, float* out, void* stream);
 int dos_mlp_set_params(dos_mlp_t net, const float* in, void* stream);
+/* Project addition (learned reconstruction): checkpoint and resume of
+ * training.  get_state copies the parameters and Adam's first and second
+ * moments (each a device buffer of dos_mlp_param_count floats, or NULL to
+ * skip it) and the number of Adam steps taken; set_state loads all of them,
+ * so that training continues exactly as if it had not been interrupted.
+ * Errors: DOS_EINVAL (null handle or buffer, step outside [0, 2^31 - 1]). */
+int dos_mlp_get_state(dos_mlp_t net, float* params, float* m, float* v,
+                      int64_t* step, void* stream);
+int dos_mlp_set_state(dos_mlp_t net, const float* params, const float* m,
+                      const float* v, int64_t step, void* stream);
 
 /* Project addition (learned reconstruction). probs[rows][sizes[n_layers]] =
  * softmax(network(x)), x[rows][sizes[0]]. Errors: DOS_EINVAL (rows < 1, null

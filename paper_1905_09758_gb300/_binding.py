@@ -83,6 +83,8 @@ _SIGNATURES = {
     "dos_mlp_param_count": ([_vp, _P64], _i32),
     "dos_mlp_get_params": ([_vp, _vp, _vp], _i32),
     "dos_mlp_set_params": ([_vp, _vp, _vp], _i32),
+    "dos_mlp_get_state": ([_vp, _vp, _vp, _vp, C.POINTER(_i64), _vp], _i32),
+    "dos_mlp_set_state": ([_vp, _vp, _vp, _vp, _i64, _vp], _i32),
     "dos_mlp_forward": ([_vp, _vp, _i32, _vp, _vp], _i32),
     "dos_mlp_loss_grad": ([_vp, _vp, _vp, _i32, _vp, _vp, _vp], _i32),
     "dos_mlp_train_step": ([_vp, _vp, _vp, _vp, _i32, C.c_float, _vp, _vp], _i32),
@@ -551,6 +553,28 @@ def dos_mlp_get_params(net: Mlp, out: torch.Tensor | None = None, stream=None) -
 def dos_mlp_set_params(net: Mlp, params: torch.Tensor, stream=None):
     _need_cuda(params, torch.float32, "params", dos_mlp_param_count(net))
     _check(lib().dos_mlp_set_params(net.handle, _ptr(params), _stream(stream)))
+
+
+def dos_mlp_get_state(net: Mlp, stream=None) -> dict:
+    """Training state: {"params", "m", "v"} (float32 CUDA tensors) and "step"."""
+    n = dos_mlp_param_count(net)
+    st = {k: torch.empty(n, dtype=torch.float32, device=_dev()) for k in ("params", "m", "v")}
+    step = C.c_int64()
+    _check(lib().dos_mlp_get_state(net.handle, _ptr(st["params"]), _ptr(st["m"]), _ptr(st["v"]), C.byref(step),
+                                   _stream(stream)))
+    st["step"] = step.value
+    return st
+
+
+def dos_mlp_set_state(net: Mlp, state: dict, stream=None):
+    """Load a state from dos_mlp_get_state (tensors on any device)."""
+    n = dos_mlp_param_count(net)
+    t = {k: torch.as_tensor(state[k], dtype=torch.float32).to(_dev()).contiguous() for k in ("params", "m", "v")}
+    for k, v in t.items():
+        _need_cuda(v, torch.float32, k, n)
+    _check(lib().dos_mlp_set_state(net.handle, _ptr(t["params"]), _ptr(t["m"]), _ptr(t["v"]), int(state["step"]),
+                                   _stream(stream)))
+    torch.cuda.synchronize()  # the copies have read t before it is released
 
 
 def dos_mlp_forward(net: Mlp, x: torch.Tensor, probs: torch.Tensor | None = None, stream=None) -> torch.Tensor:

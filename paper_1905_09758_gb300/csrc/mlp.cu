@@ -461,6 +461,34 @@ int dos_mlp_set_params(dos_mlp_t hh, const float* in, void* stream) {
   return DOS_OK;
 }
 
+int dos_mlp_get_state(dos_mlp_t hh, float* params, float* m, float* v, int64_t* step, void* stream) {
+  clear_error();
+  if (!hh) return fail(DOS_EINVAL, "dos_mlp_get_state: null handle");
+  Mlp* h = reinterpret_cast<Mlp*>(hh);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t bytes = sizeof(float) * h->count;
+  if (params) NDOS_CUDA(cudaMemcpyAsync(params, h->params, bytes, cudaMemcpyDeviceToDevice, s));
+  if (m) NDOS_CUDA(cudaMemcpyAsync(m, h->m, bytes, cudaMemcpyDeviceToDevice, s));
+  if (v) NDOS_CUDA(cudaMemcpyAsync(v, h->v, bytes, cudaMemcpyDeviceToDevice, s));
+  if (step) *step = h->step;
+  return DOS_OK;
+}
+
+int dos_mlp_set_state(dos_mlp_t hh, const float* params, const float* m, const float* v, int64_t step,
+                      void* stream) {
+  clear_error();
+  if (!hh || !params || !m || !v) return fail(DOS_EINVAL, "dos_mlp_set_state: null argument");
+  if (step < 0 || step > 0x7fffffffLL) return fail(DOS_EINVAL, "dos_mlp_set_state: step out of range");
+  Mlp* h = reinterpret_cast<Mlp*>(hh);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t bytes = sizeof(float) * h->count;
+  NDOS_CUDA(cudaMemcpyAsync(h->params, params, bytes, cudaMemcpyDeviceToDevice, s));
+  NDOS_CUDA(cudaMemcpyAsync(h->m, m, bytes, cudaMemcpyDeviceToDevice, s));
+  NDOS_CUDA(cudaMemcpyAsync(h->v, v, bytes, cudaMemcpyDeviceToDevice, s));
+  h->step = static_cast<int>(step);
+  return DOS_OK;
+}
+
 int dos_mlp_forward(dos_mlp_t hh, const float* x, int rows, float* probs, void* stream) {
   clear_error();
   if (!hh || !x || !probs || rows < 1) return fail(DOS_EINVAL, "dos_mlp_forward: bad argument");

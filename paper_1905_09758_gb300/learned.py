@@ -18,6 +18,7 @@ from __future__ import annotations
 import math
 from dataclasses import dataclass
 
+import numpy as np
 import torch
 
 from . import _binding as nd
@@ -102,18 +103,56 @@ def training_sets(graphs, m_ins, nz_in: int = 8, m_ref: int = 500, nz_ref: int =
 
 
 def train(x: torch.Tensor, t: torch.Tensor, m_in: int, nz_in: int, hidden=(512, 512), steps: int = 8000,
-          batch: int = 256, lr: float = 1e-3, lr_min: float = 1e-5, seed: int = 0, stream=None) -> Reconstructor:
+          batch: int = 256, lr: float = 1e-3, lr_min: float = 1e-5, seed: int = 0, stream=None,
+          resume: Reconstructor | None = None, stop: int | None = None) -> Reconstructor:
     """Adam on minibatches drawn uniformly with replacement, learning rate on a
-    cosine schedule from lr to lr_min.  Whether the rows carry the degree
-    statistics is read from their width."""
+    cosine schedule from lr to lr_min over `steps` steps.  Whether the rows
+    carry the degree statistics is read from their width.  `stop` ends the run
+    after that many schedule steps; `resume` (a network saved part-way through
+    the same schedule, see save / load) continues it from the Adam step it
+    had reached, so an interrupted run ends where an uninterrupted one would."""
     bins = t.shape[1]
-    net = nd.dos_mlp_create([x.shape[1], *hidden, bins], seed=seed)
     gen = torch.Generator().manual_seed(seed)
     idx = torch.randint(0, x.shape[0], (steps, batch), generator=gen, dtype=torch.int32).to(x.device)
-    for s in range(steps):
+    if resume is not None:
+        net = resume.net
+        start = nd.dos_mlp_get_state(net)["step"]
+    else:
+        net = nd.dos_mlp_create([x.shape[1], *hidden, bins], seed=seed)
+        start = 0
+    for s in range(start, steps if stop is None else min(stop, steps)):
         rate = lr_min + 0.5 * (lr - lr_min) * (1.0 + math.cos(math.pi * s / steps))
         nd.dos_mlp_train_step(net, x, t, rate, idx=idx[s], stream=stream)
     return Reconstructor(net, m_in, nz_in, bins, stats=x.shape[1] == bins + m_in - 1 + 4)
+
+
+def save(rec: Reconstructor, path, with_optimizer: bool = True) -> None:
+    """Write a network and the settings of its features to `path` (numpy
+    .npz): layer sizes, m_in, nz_in, bins, whether the degree statistics are
+    inputs, the parameters and, with_optimizer, Adam's moments and step count
+    (what train(resume=...) needs to continue)."""
+    st = nd.dos_mlp_get_state(rec.net)
+    arrays = {"sizes": np.asarray(rec.sizes, np.int64),
+              "meta": np.asarray([rec.m_in, rec.nz_in, rec.bins, int(rec.stats)], np.int64),
+              "params": st["params"].cpu().numpy()}
+    if with_optimizer:
+        arrays.update(m=st["m"].cpu().numpy(), v=st["v"].cpu().numpy(), step=np.asarray(st["step"], np.int64))
+    np.savez(path, **arrays)
+
+
+def load(path) -> Reconstructor:
+    """A network written by save, on the current CUDA device."""
+    with np.load(path) as z:
+        net = nd.dos_mlp_create([int(v) for v in z["sizes"]])
+        params = torch.from_numpy(z["params"])
+        if "m" in z:
+            nd.dos_mlp_set_state(net, {"params": params, "m": torch.from_numpy(z["m"]), "v": torch.from_numpy(z["v"]),
+                                       "step": int(z["step"])})
+        else:
+            nd.dos_mlp_set_params(net, params.to(torch.device("cuda", torch.cuda.current_device())))
+            torch.cuda.synchronize()
+        m_in, nz_in, bins, stats = (int(v) for v in z["meta"])
+    return Reconstructor(net, m_in, nz_in, bins, stats=bool(stats))
 
 
 def reconstruct(rec: Reconstructor, g: nd.Graph, f: nd.Filter | None, seed: int, count_isolated: bool = True,

@@ -341,3 +341,35 @@ def test_training_sets_share_one_cheap_run():
         x1, t1 = learned.training_set(graphs, m, 4, 40, 16, 30, seed=9)
         assert torch.equal(xs[m], x1), m
         assert torch.equal(t, t1)
+
+
+def test_checkpoint_and_resume_training(tmp_path):
+    """learned.save / load with Adam's state (dos_mlp_get_state / set_state):
+    a run interrupted after 30 of 50 steps, written to disk, read back into a
+    new handle and resumed ends bit for bit where the uninterrupted run ends;
+    a parameters-only file reproduces the forward pass."""
+    from paper_1905_09758_gb300 import learned
+
+    g = torch.Generator().manual_seed(5)
+    bins, m_in = 12, 6
+    x = torch.randn(64, bins + m_in - 1, generator=g).cuda()
+    t = torch.rand(64, bins, generator=g)
+    t = (t / t.sum(1, keepdim=True)).cuda()
+    kw = dict(hidden=(32, 24), steps=50, batch=16, lr=1e-2, seed=3)
+    full = learned.train(x, t, m_in, 4, **kw)
+    part = learned.train(x, t, m_in, 4, stop=30, **kw)
+    assert nd.dos_mlp_get_state(part.net)["step"] == 30
+    learned.save(part, tmp_path / "ck.npz")
+    back = learned.load(tmp_path / "ck.npz")
+    assert (back.m_in, back.nz_in, back.bins, back.stats, back.sizes) == (m_in, 4, bins, False, part.sizes)
+    done = learned.train(x, t, m_in, 4, resume=back, **kw)
+    a, b = nd.dos_mlp_get_state(full.net), nd.dos_mlp_get_state(done.net)
+    assert a["step"] == b["step"] == 50
+    for k in ("params", "m", "v"):
+        assert torch.equal(a[k], b[k]), k
+    learned.save(full, tmp_path / "p.npz", with_optimizer=False)
+    only = learned.load(tmp_path / "p.npz")
+    assert nd.dos_mlp_get_state(only.net)["step"] == 0
+    assert torch.equal(nd.dos_mlp_forward(only.net, x[:5]), nd.dos_mlp_forward(full.net, x[:5]))
+    with pytest.raises(nd.DosError):
+        nd.dos_mlp_set_state(only.net, {"params": a["params"], "m": a["m"], "v": a["v"], "step": -1})
