@@ -755,6 +755,14 @@ int dos_device_status(void* stream, int* status);
  * launched since load (all threads). */
 int64_t dos_launch_count(void);
 
+/* Test hook, not in the paper (failure detection without a GPU fault).
+ * after >= 0: the library's device allocations succeed `after` more times and
+ * the next one fails as an out-of-memory cudaMalloc would (the call that made
+ * it returns DOS_ENOMEM, "injected allocation failure" in dos_last_error);
+ * the hook then disarms itself.  after < 0 disarms it.  Process-wide; device
+ * memory that torch or the caller allocates is not affected. */
+int dos_test_fail_alloc(int64_t after);
+
 /* Instrumentation, not in the paper. Enable (1) / disable (0) CUDA-event
  * timing of the Chebyshev step kernels. While enabled, every step launch is
  * bracketed by events on its own stream. */

@@ -83,6 +83,7 @@ _SIGNATURES = {
     "dos_mlp_param_count": ([_vp, _P64], _i32),
     "dos_mlp_get_params": ([_vp, _vp, _vp], _i32),
     "dos_mlp_set_params": ([_vp, _vp, _vp], _i32),
+    "dos_test_fail_alloc": ([_i64], _i32),
     "dos_mlp_get_state": ([_vp, _vp, _vp, _vp, C.POINTER(_i64), _vp], _i32),
     "dos_mlp_set_state": ([_vp, _vp, _vp, _vp, _i64, _vp], _i32),
     "dos_mlp_forward": ([_vp, _vp, _i32, _vp, _vp], _i32),
@@ -464,6 +465,12 @@ def dos_device_status(stream=None) -> int:
 
 def dos_launch_count() -> int:
     return int(lib().dos_launch_count())
+
+
+def dos_test_fail_alloc(after: int):
+    """Make the library's device allocation after `after` more successful ones
+    fail with DOS_ENOMEM (once); a negative value disarms."""
+    _check(lib().dos_test_fail_alloc(int(after)))
 
 
 def dos_profile_enable(on: bool = True):

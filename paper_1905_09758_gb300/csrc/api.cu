@@ -4,9 +4,21 @@
 #include <mutex>
 #include <vector>
 
+#include "alloc_hook.h"
 #include "common.cuh"
 
 namespace netdos {
+
+// allocations left before the injected failure (-1: disarmed)
+static std::atomic<int64_t> g_fail_after{-1};
+
+bool alloc_fault_injected() {
+  int64_t v = g_fail_after.load(std::memory_order_relaxed);
+  while (v >= 0) {
+    if (g_fail_after.compare_exchange_weak(v, v - 1)) return v == 0;
+  }
+  return false;
+}
 
 static thread_local std::string t_last_error;
 std::atomic<int64_t> g_launches{0};
@@ -30,6 +42,7 @@ int cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
 int dalloc(void** p, size_t bytes, cudaStream_t s) {
   *p = nullptr;
   if (bytes == 0) bytes = 16;
+  if (alloc_fault_injected()) return fail(DOS_ENOMEM, "injected allocation failure (dos_test_fail_alloc)");
   cudaError_t e = cudaMallocAsync(p, bytes, s);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -96,6 +109,11 @@ int dos_version(void) { return 100; }
 const char* dos_last_error(void) { return t_last_error.c_str(); }
 
 int64_t dos_launch_count(void) { return g_launches.load(); }
+
+int dos_test_fail_alloc(int64_t after) {
+  g_fail_after.store(after >= 0 ? after : -1);
+  return DOS_OK;
+}
 
 int dos_profile_enable(int on) {
   std::lock_guard<std::mutex> lk(g_prof_mu);

@@ -18,6 +18,7 @@
 #include <cmath>
 #include <mutex>
 
+#include "alloc_hook.h"
 #include "kpm_kernels.cuh"
 
 namespace netdos {
@@ -163,6 +164,7 @@ int capture_stream(cudaStream_t* out) {
 
 template <typename T>
 int alloc_t(T** p, size_t count) {
+  if (alloc_fault_injected()) return fail(DOS_ENOMEM, "injected allocation failure (dos_test_fail_alloc)");
   cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), (count ? count : 1) * sizeof(T));
   if (e != cudaSuccess) {
     cudaGetLastError();

@@ -9,6 +9,7 @@
 #include <string>
 #include <vector>
 
+#include "alloc_hook.h"
 #include "common.cuh"
 
 namespace netdos {
@@ -209,6 +210,7 @@ __global__ void k_low_word(const uint64_t* __restrict__ keys, int64_t nnz, int32
 template <typename T>
 int persistent_alloc(T** p, size_t count) {
   *p = nullptr;
+  if (alloc_fault_injected()) return fail(DOS_ENOMEM, "injected allocation failure (dos_test_fail_alloc)");
   cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), (count ? count : 1) * sizeof(T));
   if (e != cudaSuccess) {
     cudaGetLastError();

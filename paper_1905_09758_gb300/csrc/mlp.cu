@@ -16,6 +16,7 @@
 #include <utility>
 #include <vector>
 
+#include "alloc_hook.h"
 #include "common.cuh"
 
 namespace netdos {
@@ -305,6 +306,7 @@ static int ensure(Mlp* h, int rows) {
   const int L = static_cast<int>(h->sizes.size()) - 1;
   h->z.assign(L + 1, nullptr);
   h->a.assign(L + 1, nullptr);
+  if (alloc_fault_injected()) return fail(DOS_ENOMEM, "injected allocation failure (dos_test_fail_alloc)");
   for (int l = 1; l <= L; ++l) {
     NDOS_CUDA(cudaMalloc(reinterpret_cast<void**>(&h->z[l]), sizeof(float) * rows * h->sizes[l]));
     NDOS_CUDA(cudaMalloc(reinterpret_cast<void**>(&h->a[l]), sizeof(float) * rows * h->sizes[l]));
@@ -399,6 +401,10 @@ int dos_mlp_create(int n_layers, const int* sizes, uint64_t seed, dos_mlp_t* out
   }
   float** bufs[] = {&h->params, &h->grads, &h->m, &h->v};
   for (float** b : bufs) {
+    if (alloc_fault_injected()) {
+      dos_mlp_destroy(reinterpret_cast<dos_mlp_t>(h));
+      return fail(DOS_ENOMEM, "injected allocation failure (dos_test_fail_alloc)");
+    }
     cudaError_t e = cudaMalloc(reinterpret_cast<void**>(b), sizeof(float) * h->count);
     if (e != cudaSuccess) {
       dos_mlp_destroy(reinterpret_cast<dos_mlp_t>(h));

@@ -31,6 +31,7 @@
 #include <utility>
 #include <vector>
 
+#include "alloc_hook.h"
 #include "common.cuh"
 
 namespace netdos {
@@ -467,6 +468,7 @@ static int motif_filter_impl(const Graph* G, uint32_t motifs, cudaStream_t s, Fi
   // query would otherwise pay a cudaMalloc each time); dos_filter_destroy
   // synchronises the device before it returns them
   auto palloc = [s](int32_t** p, int64_t count) -> int {
+    if (alloc_fault_injected()) return fail(DOS_ENOMEM, "injected allocation failure (dos_test_fail_alloc)");
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(p), sizeof(int32_t) * (count > 0 ? count : 1), s);
     if (e != cudaSuccess) {
       cudaGetLastError();
